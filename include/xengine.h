@@ -1,0 +1,150 @@
+/*
+ * xengine.h -- C ABI of the GB300 X-engine (FX correlator, cross-multiply
+ * and integrate stage) of Niu et al., arXiv:1904.07778.
+ *
+ * What the library computes (Sec. 2, System Design; Sec. 2.2, X-engine):
+ * for every frequency channel c and every pair of inputs j <= i,
+ *
+ *     V[c][i][j] = sum over pushed spectra t of  x_i(c,t) * conj(x_j(c,t))
+ *
+ * i.e. all cross- and auto-correlations of the same frequency (the CMAC
+ * "multiply and accumulation" of Sec. 2), integrated over a caller-chosen
+ * number of blocks ("integrated for some pre-specified duration", Sec. 2).
+ * Results are exact integers (int64); the GPU result is bit-identical to
+ * the plain definition above.
+ *
+ * Conventions shared by every call:
+ *  - Status: every int-returning call returns CORR_OK (0) or a negative
+ *    CORR_E* code; nothing throws across the ABI.  corr_strerror() names it.
+ *  - Output order: baseline index b(i,j) = i*(i+1)/2 + j for i >= j (lower
+ *    triangle incl. autos; the upper triangle is the conjugate).  A
+ *    visibility array is int64 vis[n_chans][n_baselines][2], [..][0] = Re,
+ *    [..][1] = Im.  The paper's delay-test visibility V = I1* . I2 (Sec. 3,
+ *    Eq. 5) conjugates the first input; that quantity is this library's
+ *    V[i=2][j=1] = x_2 conj(x_1).
+ *  - Pointers: any buffer argument may be host memory (pageable or pinned)
+ *    or device memory of the current CUDA device; the library detects which.
+ *    The caller owns every buffer it passes.
+ *  - Streams: all device work of a context runs on the stream given to
+ *    corr_create (a cudaStream_t passed as void*), or on a private stream if
+ *    NULL was given.  Calls on one context are not thread-safe; use one
+ *    context per thread.
+ */
+#ifndef XENGINE_H
+#define XENGINE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define CORR_OK 0
+#define CORR_EINVAL (-1)    /* bad argument: shape, bits, layout, size, pointer   */
+#define CORR_ENOMEM (-2)    /* device or host allocation failed                  */
+#define CORR_EBUSY (-3)     /* request does not fit the memory budget now         */
+#define CORR_ERANGE (-4)    /* an 8-bit sample equal to -128 was pushed           */
+#define CORR_ESEQ (-5)      /* block sequence number is a gap or a duplicate      */
+#define CORR_ETIMEDOUT (-6) /* a bounded device-side wait expired                 */
+#define CORR_ECUDA (-7)     /* a CUDA runtime call failed                         */
+#define CORR_ESTATE (-8)    /* call not valid in the context's current state      */
+
+/* ---- sample layouts of a pushed block -------------------------------- */
+/* [time][channel][input]: the F-engine payload order of Sec. 2.3 (packets
+ * hold "[time, (fixed) channel, (run) input channel]").                    */
+#define CORR_L_TCI 0
+/* [time][input][channel]: spectra grouped by receiver input, before the
+ * corner turn of Sec. 2.1 ("Transpose" block: [input, frequency] ->
+ * [frequency, input]); the library performs the corner turn on the GPU.    */
+#define CORR_L_TIC 1
+/* [channel][input][time]: already corner-turned and time-contiguous.       */
+#define CORR_L_CIT 2
+
+/* ---- create flags ---------------------------------------------------- */
+/* 4-bit samples: the real part is in the LOW nibble (default: high nibble).
+ * Sec. 2.1 only says two 4-bit numbers are re-packed into one byte.        */
+#define CORR_F_LO_IS_REAL 0x1u
+
+/* Pass as seq to corr_push to skip the sequence check.                    */
+#define CORR_SEQ_ANY UINT64_MAX
+
+typedef struct corr_ctx corr_ctx; /* opaque, owned by the library */
+
+/*
+ * corr_create -- make a correlator context for one array.
+ *   n_inputs : number of inputs N (receiver channels; 2 per dual-pol dish,
+ *              Sec. 1), 1 <= N <= 1024.
+ *   n_chans  : frequency channels C held by this context (the F/N channels a
+ *              GPU node processes, Sec. 2), C >= 1.
+ *   n_time   : spectra per pushed block T, T >= 1.
+ *   bits     : 4 -> one byte per complex sample, two 4-bit two's-complement
+ *              numbers (the equaliser output of Sec. 2.1, values -7..7; code
+ *              0x8 decodes to -8);  8 -> two int8 bytes (re, im) per sample,
+ *              symmetric range -127..127 (-128 is rejected, CORR_ERANGE).
+ *   layout   : CORR_L_TCI, CORR_L_TIC or CORR_L_CIT.
+ *   flags    : CORR_F_* bits.
+ *   stream   : cudaStream_t to run on, or NULL for a private stream.
+ *   out      : receives the context.
+ * Allocates the context's device state (accumulators, staging, corner-turn
+ * buffers) on the current device.  Returns CORR_EINVAL for a bad shape,
+ * CORR_ENOMEM when an allocation fails, CORR_ECUDA when no usable device.
+ */
+int corr_create(int n_inputs, int n_chans, int n_time, int bits, int layout, unsigned flags,
+                void* stream, corr_ctx** out);
+
+/*
+ * corr_push -- add one block of T spectra to the running integration.
+ *   block  : packed samples in the context's layout, host or device memory.
+ *   nbytes : must equal N * C * T * bits / 4, else CORR_EINVAL.
+ *   seq    : block sequence number; the first push after create or a reset
+ *            may carry any value, each later push must carry previous + 1
+ *            (the packet-counter gap check of Sec. 2.3).  A gap or duplicate
+ *            returns CORR_ESEQ and the block is NOT integrated.
+ *            CORR_SEQ_ANY disables the check for this push.
+ * Asynchronous and stream-ordered.  A device block is read in place and
+ * must stay unchanged until corr_sync or corr_dump returns; a host block is
+ * copied to device staging (pinned memory makes the copy asynchronous and
+ * double-buffered against compute) and must stay unchanged until the same
+ * point.  8-bit samples equal to -128 are detected on the device and
+ * reported as CORR_ERANGE by the next corr_sync / corr_dump.
+ */
+int corr_push(corr_ctx* ctx, const void* block, size_t nbytes, uint64_t seq);
+
+/*
+ * corr_dump -- copy the integrated visibilities out.
+ *   vis   : int64 [C][N(N+1)/2][2], host or device memory; may be NULL to
+ *           only reset.
+ *   reset : nonzero -> the integration restarts from zero afterwards.
+ * Waits for all pushed work.  Returns the first deferred device error
+ * (CORR_ERANGE, CORR_ETIMEDOUT) if one occurred since the last check.
+ */
+int corr_dump(corr_ctx* ctx, int64_t* vis, int reset);
+
+/*
+ * corr_normalise -- correlation coefficients of the current integration:
+ * rho_ij = V_ij / sqrt(V_ii * V_jj) computed in FP64 on the GPU as
+ * double(V_ij) / sqrt(double(V_ii) * double(V_jj)); rho = 0 where
+ * V_ii * V_jj == 0.  (Not defined by the paper; provided for monitoring.)
+ *   rho : double [C][N(N+1)/2][2], host or device memory.
+ * Does not reset the integration.
+ */
+int corr_normalise(corr_ctx* ctx, double* rho);
+
+/* corr_sync -- wait for all pushed work; returns any deferred device error. */
+int corr_sync(corr_ctx* ctx);
+
+/* corr_destroy -- free the context (waits for its work first).  NULL is ok. */
+int corr_destroy(corr_ctx* ctx);
+
+/* corr_strerror -- static description of a status code. */
+const char* corr_strerror(int status);
+
+/* corr_n_baselines -- N(N+1)/2, or 0 for N < 1. */
+int64_t corr_n_baselines(int n_inputs);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* XENGINE_H */
