@@ -1,0 +1,176 @@
+"""Python binding of the X-engine C ABI (include/xengine.h).
+
+Argument marshalling only: every step of the data path runs in the CUDA
+kernels of ``libxengine.so``.  There is no CPU fallback -- importing this
+module raises if the library has not been built.
+
+Functions carry the C names (``corr_create``, ``corr_push``, ...) and take
+plain integers/pointers; ``Correlator`` wraps them for numpy arrays and torch
+tensors (host or device).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libxengine.so")
+
+CORR_OK, CORR_EINVAL, CORR_ENOMEM, CORR_EBUSY = 0, -1, -2, -3
+CORR_ERANGE, CORR_ESEQ, CORR_ETIMEDOUT, CORR_ECUDA, CORR_ESTATE = -4, -5, -6, -7, -8
+CORR_L_TCI, CORR_L_TIC, CORR_L_CIT = 0, 1, 2
+CORR_F_LO_IS_REAL = 1
+CORR_SEQ_ANY = (1 << 64) - 1
+_CUDA_STREAM_LEGACY = 0x1  # cudaStreamLegacy
+
+EXPORTS = ["corr_create", "corr_push", "corr_dump", "corr_normalise", "corr_sync",
+           "corr_destroy", "corr_strerror", "corr_n_baselines"]
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libxengine.so is not built (run paper_1904_07778_gb300.build.build()); "
+                      "the X-engine has no CPU fallback")
+
+_lib = ctypes.CDLL(LIB_PATH)
+_P, _I, _U, _SZ, _U64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint, ctypes.c_size_t, ctypes.c_uint64
+_lib.corr_create.argtypes = [_I, _I, _I, _I, _I, _U, _P, ctypes.POINTER(_P)]
+_lib.corr_push.argtypes = [_P, _P, _SZ, _U64]
+_lib.corr_dump.argtypes = [_P, _P, _I]
+_lib.corr_normalise.argtypes = [_P, _P]
+_lib.corr_sync.argtypes = [_P]
+_lib.corr_destroy.argtypes = [_P]
+_lib.corr_strerror.argtypes = [_I]
+_lib.corr_strerror.restype = ctypes.c_char_p
+_lib.corr_n_baselines.argtypes = [_I]
+_lib.corr_n_baselines.restype = ctypes.c_int64
+for _f in ("corr_create", "corr_push", "corr_dump", "corr_normalise", "corr_sync", "corr_destroy"):
+    getattr(_lib, _f).restype = _I
+
+
+class CorrError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__("%s: %s (%d)" % (where, corr_strerror(status), status))
+        self.status = status
+
+
+def corr_strerror(status: int) -> str:
+    return _lib.corr_strerror(status).decode()
+
+
+def corr_n_baselines(n_inputs: int) -> int:
+    return int(_lib.corr_n_baselines(n_inputs))
+
+
+def corr_create(n_inputs, n_chans, n_time, bits=4, layout=CORR_L_TCI, flags=0, stream=0):
+    ctx = _P()
+    st = _lib.corr_create(n_inputs, n_chans, n_time, bits, layout, flags,
+                          _P(stream) if stream else None, ctypes.byref(ctx))
+    if st != CORR_OK:
+        raise CorrError(st, "corr_create")
+    return ctx
+
+
+def corr_push(ctx, block_ptr: int, nbytes: int, seq: int = CORR_SEQ_ANY) -> int:
+    return _lib.corr_push(ctx, _P(block_ptr), nbytes, seq)
+
+
+def corr_dump(ctx, vis_ptr: int, reset: int = 1) -> int:
+    return _lib.corr_dump(ctx, _P(vis_ptr) if vis_ptr else None, reset)
+
+
+def corr_normalise(ctx, rho_ptr: int) -> int:
+    return _lib.corr_normalise(ctx, _P(rho_ptr))
+
+
+def corr_sync(ctx) -> int:
+    return _lib.corr_sync(ctx)
+
+
+def corr_destroy(ctx) -> int:
+    return _lib.corr_destroy(ctx)
+
+
+def _ptr_and_size(buf):
+    """(address, nbytes) of a numpy array or torch tensor (host or device)."""
+    if isinstance(buf, np.ndarray):
+        if not buf.flags.c_contiguous:
+            raise ValueError("buffer must be contiguous")
+        return buf.ctypes.data, buf.nbytes
+    if hasattr(buf, "data_ptr"):
+        if not buf.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return buf.data_ptr(), buf.numel() * buf.element_size()
+    raise TypeError("expected a numpy array or a torch tensor")
+
+
+class Correlator:
+    """One X-engine context: push blocks, dump integrated visibilities."""
+
+    def __init__(self, n_inputs, n_chans, n_time, bits=4, layout=CORR_L_TCI, lo_is_real=False,
+                 stream=None):
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+            if stream == 0:
+                stream = _CUDA_STREAM_LEGACY  # torch's default stream is the legacy stream
+        self.n_inputs, self.n_chans, self.n_time, self.bits = n_inputs, n_chans, n_time, bits
+        self.layout = layout
+        self.n_baselines = corr_n_baselines(n_inputs)
+        self.block_bytes = n_inputs * n_chans * n_time * bits // 4
+        self._ctx = corr_create(n_inputs, n_chans, n_time, bits, layout,
+                                CORR_F_LO_IS_REAL if lo_is_real else 0, stream)
+
+    def push(self, block, seq=CORR_SEQ_ANY, check=True):
+        p, n = _ptr_and_size(block)
+        st = corr_push(self._ctx, p, n, seq)
+        if check and st != CORR_OK:
+            raise CorrError(st, "corr_push")
+        return st
+
+    def dump_into(self, vis, reset=True):
+        p, n = _ptr_and_size(vis)
+        if n != self.n_chans * self.n_baselines * 16:
+            raise ValueError("vis must hold n_chans * n_baselines * 2 int64")
+        st = corr_dump(self._ctx, p, 1 if reset else 0)
+        if st != CORR_OK:
+            raise CorrError(st, "corr_dump")
+        return vis
+
+    def dump(self, reset=True):
+        vis = np.empty((self.n_chans, self.n_baselines, 2), dtype=np.int64)
+        return self.dump_into(vis, reset)
+
+    def normalise_into(self, rho):
+        p, n = _ptr_and_size(rho)
+        if n != self.n_chans * self.n_baselines * 16:
+            raise ValueError("rho must hold n_chans * n_baselines * 2 float64")
+        st = corr_normalise(self._ctx, p)
+        if st != CORR_OK:
+            raise CorrError(st, "corr_normalise")
+        return rho
+
+    def normalise(self):
+        return self.normalise_into(np.empty((self.n_chans, self.n_baselines, 2), dtype=np.float64))
+
+    def sync(self):
+        st = corr_sync(self._ctx)
+        if st != CORR_OK:
+            raise CorrError(st, "corr_sync")
+
+    def close(self):
+        if self._ctx:
+            corr_destroy(self._ctx)
+            self._ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

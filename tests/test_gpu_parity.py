@@ -1,0 +1,162 @@
+"""Parity of the CUDA X-engine with the oracle, element by element, through
+the C ABI.  Integer results must be bit-exact; FP64 correlation
+coefficients within 1e-12 relative."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+from paper_1904_07778_gb300 import synth  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def xe():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1904_07778_gb300 import build
+    build.build()
+    from paper_1904_07778_gb300 import xengine
+    return xengine
+
+
+def _run(xe, blocks, N, C, T, layout, lo_is_real=False, device_input=True):
+    with xe.Correlator(N, C, T, bits=4, layout=layout, lo_is_real=lo_is_real) as cor:
+        for b in blocks:
+            if device_input:
+                cor.push(torch.from_numpy(b).cuda())
+            else:
+                cor.push(b)
+        return cor.dump()
+
+
+def _oracle(blocks, N, C, T, layout, lo_is_real=False, chans=None):
+    out = None
+    for b in blocks:
+        out = oracle.correlate(b, N, C, T, bits=4, layout=layout, hi_is_real=not lo_is_real,
+                               chans=chans, out=out)
+    return out
+
+
+SHAPES = [
+    # (N, C, T): stacked small arrays, one / several 128-row blocks, ragged tails
+    (1, 3, 1), (1, 5, 130), (2, 7, 17), (3, 4, 257), (16, 9, 128), (31, 5, 200),
+    (32, 6, 1024), (33, 3, 300), (48, 2, 129), (64, 3, 384), (65, 2, 100),
+    (100, 2, 513), (192, 2, 256), (257, 1, 160),
+]
+
+
+@pytest.mark.parametrize("N,C,T", SHAPES)
+@pytest.mark.parametrize("layout", [0, 1, 2])
+def test_random_codes_bit_exact(xe, N, C, T, layout):
+    """Uniform random bytes (every 4-bit code incl. -8), every layout."""
+    blk = synth.random_bytes(N * 1000 + C * 10 + T + layout, N * C * T)
+    got = _run(xe, [blk], N, C, T, layout)
+    assert np.array_equal(got, _oracle([blk], N, C, T, layout))
+
+
+@pytest.mark.parametrize("lo", [False, True])
+def test_nibble_order(xe, lo):
+    N, C, T = 8, 4, 64
+    blk = synth.random_bytes(77, N * C * T)
+    got = _run(xe, [blk], N, C, T, 0, lo_is_real=lo)
+    assert np.array_equal(got, _oracle([blk], N, C, T, 0, lo_is_real=lo))
+
+
+def test_extreme_codes(xe):
+    """All -8 (the largest products) and all +7, several blocks integrated."""
+    N, C, T = 40, 3, 1024
+    a = np.full(N * C * T, 0x88, np.uint8)
+    b = np.full(N * C * T, 0x77, np.uint8)
+    c = np.full(N * C * T, 0x78, np.uint8)
+    got = _run(xe, [a, b, c], N, C, T, 2)
+    assert np.array_equal(got, _oracle([a, b, c], N, C, T, 2))
+
+
+def test_host_and_device_pointers(xe):
+    N, C, T = 24, 8, 256
+    blks = [synth.block("gauss", s, N, C, T, layout=0) for s in range(3)]
+    want = _oracle(blks, N, C, T, 0)
+    assert np.array_equal(_run(xe, blks, N, C, T, 0, device_input=False), want)
+    pinned = [torch.from_numpy(b).pin_memory() for b in blks]
+    with xe.Correlator(N, C, T, layout=0) as cor:
+        for p in pinned:
+            cor.push(p)
+        vis = torch.empty((C, N * (N + 1) // 2, 2), dtype=torch.int64, device="cuda")
+        cor.dump_into(vis)
+        assert np.array_equal(vis.cpu().numpy(), want)
+
+
+def test_dump_reset_and_sequence(xe):
+    N, C, T = 12, 5, 96
+    blks = [synth.random_bytes(s, N * C * T) for s in range(4)]
+    with xe.Correlator(N, C, T, layout=2) as cor:
+        cor.push(blks[0], seq=10)
+        cor.push(blks[1], seq=11)
+        assert cor.push(blks[3], seq=13, check=False) == xe.CORR_ESEQ   # gap: not integrated
+        assert cor.push(blks[1], seq=11, check=False) == xe.CORR_ESEQ   # duplicate
+        v = cor.dump(reset=False)
+        assert np.array_equal(v, _oracle(blks[:2], N, C, T, 2))
+        cor.push(blks[2], seq=12)
+        v = cor.dump(reset=True)
+        assert np.array_equal(v, _oracle(blks[:3], N, C, T, 2))
+        assert not cor.dump(reset=True).any()          # nothing pushed since the reset
+        cor.push(blks[3], seq=99)                        # any seq after a reset
+        assert np.array_equal(cor.dump(), _oracle(blks[3:], N, C, T, 2))
+        with pytest.raises(xe.CorrError):
+            cor.push(blks[0][:-1])                       # wrong size
+
+
+def test_long_block_chunked(xe):
+    """T above the per-accumulation limit (65536 spectra) is split exactly."""
+    N, C, T = 4, 2, 70000
+    blk = np.full(N * C * T, 0x88, np.uint8)  # worst-case magnitudes
+    blk[::7] = 0x7F
+    got = _run(xe, [blk], N, C, T, 2)
+    assert np.array_equal(got, _oracle([blk], N, C, T, 2))
+
+
+def test_normalise(xe):
+    N, C, T = 20, 4, 512
+    blk = synth.block("sky", 3, N, C, T, layout=0)
+    blk[:N] = 0  # input bytes of t=0, c=0: keep autos positive but exercise small values
+    with xe.Correlator(N, C, T, layout=0) as cor:
+        cor.push(blk)
+        rho = cor.normalise()
+        vis = cor.dump()
+    want, _ = oracle.normalise(vis, N)
+    assert np.array_equal(vis, _oracle([blk], N, C, T, 0))
+    assert np.allclose(rho, want, rtol=1e-12, atol=0)
+
+
+def test_dish_array_full_size(xe):
+    """32 inputs, 256 channels, 1024 spectra, payload order: full parity."""
+    N, C, T = 32, 256, 1024
+    blk = synth.block("gauss", 0, N, C, T, layout=0)
+    got = _run(xe, [blk], N, C, T, 0)
+    assert np.array_equal(got, _oracle([blk], N, C, T, 0))
+
+
+def test_cylinder_array_full_size_sampled(xe):
+    """192 inputs, 1024 channels, 8192 spectra, [t][i][c] order (corner turn
+    on the GPU): generated on the device; sampled channels against the
+    oracle; all channels against invariants that hold at any size."""
+    N, C, T = 192, 1024, 8192
+    dblk = synth.block_device("sky", 2, N, C, T, layout=1, device="cuda")
+    with xe.Correlator(N, C, T, layout=1) as cor:
+        cor.push(dblk)
+        vis = cor.dump()
+    blk = dblk.cpu().numpy()
+    chans = np.random.default_rng(5).choice(C, size=12, replace=False)
+    chans = np.concatenate([[0, C - 1], chans])
+    want = oracle.correlate(blk, N, C, T, layout=1, chans=chans)
+    assert np.array_equal(vis[chans], want)
+    # total power of every channel: sum_i V_ii = sum_t sum_i |x_i|^2
+    x = dblk.view(T, N, C)
+    hi = ((x >> 4).to(torch.int32) ^ 8) - 8
+    lo = ((x & 15).to(torch.int32) ^ 8) - 8
+    p = (hi * hi + lo * lo).sum(dim=(0, 1)).cpu().numpy()
+    ii = np.array([i * (i + 1) // 2 + i for i in range(N)])
+    assert np.array_equal(vis[:, ii, 0].sum(axis=1), p)
+    assert (vis[:, ii, 1] == 0).all() and (vis[:, ii, 0] >= 0).all()
