@@ -1,0 +1,385 @@
+#!/usr/bin/env python3
+"""X-engine benchmark: correlator throughput on one or more GB300s.
+
+One step = one block of synthetic channelised voltages through the whole hot
+path, via the C ABI: corr_push (4-bit unpack, corner turn, tensor-core
+cross-multiply, integration into int64) and corr_dump (visibilities out).
+
+Default workload: the Tianlai cylinder array size -- 192 inputs (96 dual-pol
+receivers), 1024 channels, 8192 spectra per block, 4-bit complex samples in
+[time][input][channel] order so the corner turn runs on the GPU, common sky
+signal plus receiver noise.  Metric: correlator ops/s, 8 integer ops per
+complex multiply-accumulate over the N(N+1)/2 baselines incl. autos, plus the
+multiple of real time at 250 MSPS (a C-channel spectrum = 2C real samples).
+
+``--impl reference`` times the plain CPU oracle on the host cores instead,
+on a bounded sample of the same workload.
+
+Multi-GPU (torchrun, one rank per GPU): channels are independent, so each
+rank integrates its own block with no collective on the data path (weak
+scaling); timings are reduced with a max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "cylinder192": dict(
+        desc="cylinder array: 192 inputs x 1024 channels x 8192 spectra/block, 4-bit complex, "
+             "[time][input][channel] order (corner turn on GPU), sky+noise model",
+        N=192, C=1024, T=8192, layout=1, kind="sky"),
+    "cylinder192s": dict(
+        desc="cylinder array, 128-channel slice: 192 inputs x 128 channels x 8192 spectra/block, "
+             "4-bit complex, [time][input][channel] order, sky+noise model (profiling size)",
+        N=192, C=128, T=8192, layout=1, kind="sky"),
+    "dish32": dict(
+        desc="dish array: 32 inputs x 1024 channels x 4096 spectra/block, 4-bit complex, "
+             "[time][channel][input] payload order, sky+noise model",
+        N=32, C=1024, T=4096, layout=0, kind="sky"),
+}
+METRIC = "X-engine correlator Tops/s at 192 inputs (8 int ops per complex MAC, lower triangle incl. autos)"
+PAPER_TOPS = 1.2  # xGPU on one GTX 690 core, >= 96 dual-pol stations (Sec. 2.2); context only
+REAL_TIME_RATE = 125e6  # spectra x channels per second per input at 250 MSPS real sampling
+
+
+def ops_per_block(w):
+    return 8 * w["N"] * (w["N"] + 1) // 2 * w["C"] * w["T"]
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return dict(hbm=d["hbm_gbs"], bf16=d["bf16_tflops"],
+                    bf16_sus=d.get("bf16_tflops_sustained", d["bf16_tflops"]), src="measured")
+    return dict(hbm=6800.0, bf16=1900.0, bf16_sus=1700.0, src="fallback")
+
+
+def kernel_traffic(name, launch_units):
+    """DRAM bytes per launch from a committed ncu summary, if the kernel's
+    source is unchanged since the capture; scaled to this launch's units."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        d = json.load(open(path)).get(name)
+        src = open(os.path.join(ROOT, d["source"]), "rb").read()
+        if hashlib.sha256(src).hexdigest() != d["source_sha256"]:
+            return None
+        return d["dram_bytes"] * launch_units / d["units"]
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                self.rows.append(f)
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.th.join(timeout=5)
+        if not self.rows:
+            return None
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[5 + k] == "Active"})
+        pw = [float(r[3]) for r in self.rows if r[3].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows),
+                "power_w_median": statistics.median(pw) if pw else None}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("gloo")
+    return world, rank, local
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def cpu_oracle_run(w, seconds, seed=0):
+    """A bounded sample (channels x spectra) of workload w sized to take about
+    `seconds` of oracle time on all host cores; returns the sample block."""
+    import oracle
+    from paper_1904_07778_gb300 import synth
+    cores = os.cpu_count() or 1
+    n, T = w["N"], w["T"]
+    per_spectrum = n * (n + 1) // 2  # complex MACs per channel per spectrum
+    nch = max(1, min(w["C"], cores))
+    t_cal = min(T, 128)
+    blk = synth.block(w["kind"], seed, n, nch, t_cal, layout=w["layout"])
+    t0 = time.perf_counter()
+    oracle.correlate(blk, n, nch, t_cal, layout=w["layout"], threads=cores)
+    rate = per_spectrum * nch * t_cal / max(time.perf_counter() - t0, 1e-6)  # CMAC/s
+    target = rate * seconds
+    if target >= per_spectrum * T * nch:
+        ts = T
+        nch = int(min(w["C"], max(nch, (target // (per_spectrum * T)) // nch * nch)))
+    else:
+        ts = int(max(16, min(T, target // (per_spectrum * nch))))
+    blk = synth.block(w["kind"], seed + 1, n, nch, ts, layout=w["layout"])
+    return blk, nch, ts, cores
+
+
+def time_oracle(blk, w, nch, ts, cores):
+    import oracle
+    t0 = time.perf_counter()
+    oracle.correlate(blk, w["N"], nch, ts, layout=w["layout"], threads=cores)
+    return time.perf_counter() - t0
+
+
+def run_reference(args, w, world, rank):
+    if rank != 0:
+        return 0
+    budget = max(0.05, min(2.0, 120.0 / max(1, args.steps + args.warmup)))
+    blk, nch, ts, cores = cpu_oracle_run(w, budget)
+    for _ in range(args.warmup):
+        time_oracle(blk, w, nch, ts, cores)
+    el = [time_oracle(blk, w, nch, ts, cores) for _ in range(args.steps)]
+    ops = 8 * w["N"] * (w["N"] + 1) // 2 * nch * ts
+    tot = sum(el)
+    v = ops * args.steps / tot / 1e12
+    sample = "%d of %d channels x %d of %d spectra per step" % (nch, w["C"], ts, w["T"])
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Tops/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic",
+            "config": {"workload": w["desc"], "sample": sample},
+            "cpu_baseline": {"value": v, "unit": "Tops/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": "Tops/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args, w, world, rank, local):
+    import torch
+    from paper_1904_07778_gb300 import build, synth
+    build.build()
+    from paper_1904_07778_gb300.xengine import Correlator
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    N, C, T = w["N"], w["C"], w["T"]
+    nb = N * (N + 1) // 2
+    with torch.cuda.stream(stream):
+        # two different blocks (2 x 1.5 GiB for the default workload, both far
+        # larger than the 129 MB L2): alternate so no step reuses cached input
+        blocks = [synth.block_device(w["kind"], 1000 * rank + s, N, C, T, w["layout"], dev)
+                  for s in range(2)]
+        vis = torch.empty((C, nb, 2), dtype=torch.int64, device=dev)
+    stream.synchronize()
+    cor = Correlator(N, C, T, bits=4, layout=w["layout"], stream=stream.cuda_stream)
+
+    def step(k):
+        cor.push(blocks[k & 1])
+        cor.dump_into(vis, reset=True)
+
+    for k in range(args.warmup):
+        step(k)
+    cor.set_timing(True)
+    s0 = cor.stats()
+    sampler = ClockSampler(local) if not args.no_clocks else None
+    barrier(world)
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    w0 = time.perf_counter()
+    e0.record(stream)
+    for k in range(args.steps):
+        step(k)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - w0
+    clocks = sampler.stop() if sampler else None
+    barrier(world)
+    ms = e0.elapsed_time(e1)
+    ms_max = max_over_ranks(ms, world)
+    s1 = cor.stats()
+    cor.set_timing(False)
+
+    # end to end through the public API with host buffers: pinned input
+    # blocks copied in and the visibilities read back every step
+    e2e = None
+    if not args.no_e2e:
+        hb = [torch.empty(blocks[0].numel(), dtype=torch.uint8, pin_memory=True) for _ in range(2)]
+        for h, b in zip(hb, blocks):
+            h.copy_(b)
+        hv = torch.empty((C, nb, 2), dtype=torch.int64, pin_memory=True)
+
+        def step_host(k):
+            cor.push(hb[k & 1])
+            cor.dump_into(hv, reset=True)
+
+        for k in range(max(2, args.warmup // 4)):
+            step_host(k)
+        ke = max(3, min(args.steps, args.e2e_steps))
+        barrier(world)
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        t0 = time.perf_counter()
+        for k in range(ke):
+            step_host(k)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        e2e_wall = time.perf_counter() - t0
+        e2e_ms = max_over_ranks(1e3 * e2e_wall / ke, world)
+        e2e = {"value": world * ops_per_block(w) / (e2e_ms * 1e-3) / 1e12, "unit": "Tops/s",
+               "h2d_bytes_per_step": blocks[0].numel(), "d2h_bytes_per_step": vis.numel() * 8,
+               "ms_per_step": e2e_ms, "steps": ke}
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        blk, nch, ts, cores = cpu_oracle_run(w, args.cpu_seconds)
+        dt = time_oracle(blk, w, nch, ts, cores)
+        cpu = {"value": 8 * N * (N + 1) // 2 * nch * ts / dt / 1e12, "unit": "Tops/s",
+               "cores": cores, "kind": "oracle",
+               "sample": "%d of %d channels x %d of %d spectra (%.1f s)" % (nch, C, ts, T, dt)}
+
+    if rank != 0:
+        cor.close()
+        return 0
+    pk = peaks()
+    d = {k: s1[k] - s0[k] for k in s1}
+    herk_avg = d["herk_ms"] / max(1, d["timed_herk"])
+    turn_avg = d["turn_ms"] / max(1, d["timed_turn"])
+    herk_ops = ops_per_block(w)  # one herk launch per block at T <= 65536
+    fp8_sus = 2 * pk["bf16_sus"]  # fp8 dense = 2 x bf16 (nominal ratio)
+    herk = {"kernel": "herk4_kernel", "bound": "tensor", "unit": "TFLOP/s",
+            "achieved": herk_ops / (herk_avg * 1e-3) / 1e12, "peak": fp8_sus,
+            "avg_launch_ms": herk_avg, "launches": d["timed_herk"],
+            "peak_note": "fp8 dense = 2 x %s bf16 sustained (%.1f TF/s)" % (pk["src"], pk["bf16_sus"]),
+            "traffic": kernel_traffic("herk4_kernel", C)}
+    herk["frac"] = herk["achieved"] / herk["peak"]
+    kernels = [herk]
+    if w["layout"] != 2:
+        tb = 2 * N * C * T
+        turn = {"kernel": "turn_kernel", "bound": "hbm", "unit": "GB/s",
+                "achieved": tb / (turn_avg * 1e-3) / 1e9, "peak": pk["hbm"], "avg_launch_ms": turn_avg,
+                "launches": d["timed_turn"], "peak_note": "%s HBM copy" % pk["src"],
+                "traffic": kernel_traffic("turn_kernel", N * C * T)}
+        turn["frac"] = turn["achieved"] / turn["peak"]
+        kernels.append(turn)
+    dom = max(kernels, key=lambda k: k["avg_launch_ms"] * k["launches"])
+    roof = {k: dom[k] for k in ("bound", "achieved", "peak", "unit", "frac", "traffic")}
+    roof["kernel"] = dom["kernel"]
+    ms_step = ms_max / args.steps
+    value = world * ops_per_block(w) / (ms_step * 1e-3) / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": "Tops/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": value / PAPER_TOPS, "dtype": "u8",
+        "data": "synthetic (seeded sky+noise model, device-generated)",
+        "config": {"workload": w["desc"], "n_inputs": N, "n_chans": C, "n_time": T,
+                   "bits": 4, "layout": ["tci", "tic", "cit"][w["layout"]],
+                   "l2": "inputs larger than L2 (two alternating 1.5 GiB blocks)",
+                   "parallelism": "replica per GPU, channels independent" if world > 1 else "1 GPU"},
+        "x_real_time": world * C * T / REAL_TIME_RATE / (ms_step * 1e-3),
+        "wall_ms_per_step": 1e3 * wall / args.steps,
+        "gpu_launches": (d["herk_launches"] + d["turn_launches"] + d["norm_launches"]),
+        "roofline": roof, "kernels": kernels,
+        "phase_ms_per_step": {"turn": d["turn_ms"] / args.steps, "herk": d["herk_ms"] / args.steps,
+                              "dump_copy": d["dump_ms"] / args.steps},
+        "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,
+        "vs_baseline_note": "value / 1.2 Tops/s (xGPU, one GTX 690 core, Sec. 2.2): context only",
+    }
+    print(json.dumps(line), flush=True)
+    cor.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="cylinder192")
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    w = WORKLOADS[args.workload]
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        rc = run_reference(args, w, world, rank)
+    else:
+        rc = run_gpu(args, w, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return rc
+
+
+if __name__ == "__main__":
+    sys.exit(main())

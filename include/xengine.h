@@ -144,6 +144,35 @@ const char* corr_strerror(int status);
 /* corr_n_baselines -- N(N+1)/2, or 0 for N < 1. */
 int64_t corr_n_baselines(int n_inputs);
 
+/*
+ * Run-time counters of a context, in the spirit of the per-thread key/value
+ * status buffer of the paper's pipeline manager (Sec. 2.2, Hashpipe status).
+ * Device times are summed over launches since the context was created and
+ * are only collected while timing is on (corr_set_timing): each timed
+ * kernel or copy is bracketed by CUDA events on the context's stream.
+ */
+typedef struct corr_stats {
+  uint64_t blocks;          /* blocks integrated                              */
+  uint64_t seq_rejects;     /* pushes rejected with CORR_ESEQ                 */
+  uint64_t dumps;           /* corr_dump calls                                */
+  uint64_t turn_launches;   /* corner-turn kernels launched                   */
+  uint64_t herk_launches;   /* cross-multiply kernels launched                */
+  uint64_t norm_launches;   /* normalisation kernels launched                 */
+  double turn_ms;           /* device time in corner-turn kernels (timed)     */
+  double herk_ms;           /* device time in cross-multiply kernels (timed)  */
+  double copy_in_ms;        /* device time of host-to-device block copies     */
+  double dump_ms;           /* device time of visibility copies out           */
+  double norm_ms;           /* device time in normalisation kernels           */
+  uint64_t timed_turn;      /* launches included in turn_ms                   */
+  uint64_t timed_herk;      /* launches included in herk_ms                   */
+} corr_stats;
+
+/* corr_set_timing -- turn per-phase device timing on (1) or off (0). */
+int corr_set_timing(corr_ctx* ctx, int on);
+
+/* corr_get_stats -- wait for the context's work and fill *out. */
+int corr_get_stats(corr_ctx* ctx, corr_stats* out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -4,6 +4,7 @@
 #include <cstddef>
 #include <cstdint>
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 namespace xe {
@@ -14,18 +15,19 @@ enum : int {
   kStRange = 2,     // an 8-bit sample equal to -128 was seen
 };
 
-// One tile-row task of the Hermitian rank-k update.  The real Gram matrix of
-// a channel is G = Y Y^T with Y the (2N x T) matrix whose row 2i holds Re x_i
-// and row 2i+1 holds Im x_i.  A task owns output rows [128 rb, 128 rb + 128)
-// of G against column blocks [128 cb0, 128 cb1) (cb1 <= rb + 1, at most four
-// blocks), for channel chan0.  When 2N < 128, several channels are stacked in
-// one 128-row tile (rows_per_chan = 2N rounded up to a power of two) and the
-// task covers channels chan0 .. chan0 + 128 / rows_per_chan - 1.
+// One task of the Hermitian rank-k update.  The real Gram matrix of a
+// channel is G = Y Y^T with Y the (2N x T) matrix whose row 2i holds Re x_i
+// and row 2i+1 holds Im x_i; it is cut into 128 x 128 blocks.  A task owns
+// the rows of block rb against one or two column blocks cb[0], cb[1]
+// (cb[1] = -1 for one): the MMA is 128 x 128 or 128 x 256.  Because G is
+// symmetric, block (rb, c) with c > rb stands for block (c, rb) of the lower
+// triangle and is written transposed.  When 2N <= 64, several channels are
+// stacked in one 128-row block (rows_per_chan = 2N rounded up to a power of
+// two) and the task covers channels chan0 .. chan0 + 128 / rows_per_chan - 1.
 struct HerkTask {
   int chan0;
   int rb;
-  int cb0;
-  int cb1;
+  int cb[2];
 };
 
 struct HerkArgs {
@@ -50,10 +52,21 @@ struct HerkArgs {
 constexpr int kMaxChunk4 = 65536;
 
 int herk4_max_smem();
-cudaError_t herk4_launch(const HerkArgs& a, int n_tasks, cudaStream_t s);
+// tmap == nullptr selects the kernel that loads with plain global loads (any
+// alignment); otherwise tmap describes x as a 3-D byte tensor
+// {time (row_stride apart: inner), input, channel} for the TMA kernel.
+cudaError_t herk4_launch(const HerkArgs& a, const CUtensorMap* tmap, int n_tasks, cudaStream_t s);
 
-// Corner turn of byte samples: in[t][g][k] -> out[k][g][t] (out row = T bytes).
-cudaError_t turn_launch(const uint8_t* in, uint8_t* out, int T, int G, int K, cudaStream_t s);
+// Build the tensor map of a [channel][input][time] byte array with rows of
+// row_stride bytes (a multiple of 16, base 16-byte aligned).  Box: 128
+// spectra x box_inputs x box_chans.  Returns false if the driver rejects it.
+bool make_sample_tmap(CUtensorMap* m, const uint8_t* x, int n_time, long long row_stride,
+                      int n_inputs, int n_chans, int box_inputs, int box_chans);
+
+// Corner turn of byte samples: in[t][g][k] -> out[k][g][t], output rows of
+// out_stride >= T bytes.
+cudaError_t turn_launch(const uint8_t* in, uint8_t* out, int T, int G, int K, long long out_stride,
+                        cudaStream_t s);
 
 // FP64 correlation coefficients from int64 visibilities.
 cudaError_t normalise_launch(const int64_t* acc, double* rho, int n_inputs, int n_chans,

@@ -8,10 +8,37 @@
 #include <new>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "xe_internal.h"
 #include "xengine.h"
 
 using namespace xe;
+
+namespace xe {
+
+bool make_sample_tmap(CUtensorMap* m, const uint8_t* x, int n_time, long long row_stride,
+                      int n_inputs, int n_chans, int box_inputs, int box_chans) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+      return false;
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const cuuint64_t dims[3] = {(cuuint64_t)n_time, (cuuint64_t)n_inputs, (cuuint64_t)n_chans};
+  const cuuint64_t strides[2] = {(cuuint64_t)row_stride, (cuuint64_t)row_stride * n_inputs};
+  const cuuint32_t box[3] = {128u, (cuuint32_t)box_inputs, (cuuint32_t)box_chans};
+  const cuuint32_t estr[3] = {1u, 1u, 1u};
+  return encode(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<uint8_t*>(x), dims, strides, box,
+                estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace xe
 
 struct corr_ctx {
   int n_inputs = 0, n_chans = 0, n_time = 0, bits = 4, layout = 0;
@@ -29,6 +56,7 @@ struct corr_ctx {
   cudaEvent_t stage_ready[2] = {nullptr, nullptr};
   int stage_next = 0;
   uint8_t* turned = nullptr;  // corner-turned copy of the block, [c][i][t]
+  long long turned_stride = 0;  // bytes per (channel, input) row of `turned`
   HerkTask* tasks = nullptr;
   int n_tasks = 0;
   int rows_per_chan = 0;
@@ -38,9 +66,74 @@ struct corr_ctx {
   double* rho_tmp = nullptr;
   bool seq_started = false;
   uint64_t next_seq = 0;
+  // run-time counters and optional per-phase event timing
+  corr_stats stats{};
+  bool timing = false;
+  struct Timed {
+    int phase;
+    cudaEvent_t begin, end;
+  };
+  std::vector<Timed> pending;
+  std::vector<cudaEvent_t> pool;
 };
 
 namespace {
+
+enum Phase { kTurn, kHerk, kCopyIn, kDump, kNorm };
+
+cudaEvent_t take_event(corr_ctx* x) {
+  if (!x->pool.empty()) {
+    cudaEvent_t e = x->pool.back();
+    x->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+// Start timing a phase on stream s (no-op while timing is off).
+cudaEvent_t phase_begin(corr_ctx* x, cudaStream_t s) {
+  if (!x->timing) return nullptr;
+  cudaEvent_t e = take_event(x);
+  if (e && cudaEventRecord(e, s) != cudaSuccess) {
+    x->pool.push_back(e);
+    return nullptr;
+  }
+  return e;
+}
+
+void phase_end(corr_ctx* x, int phase, cudaEvent_t begin, cudaStream_t s) {
+  if (!begin) return;
+  cudaEvent_t e = take_event(x);
+  if (!e || cudaEventRecord(e, s) != cudaSuccess) {
+    x->pool.push_back(begin);
+    if (e) x->pool.push_back(e);
+    return;
+  }
+  x->pending.push_back({phase, begin, e});
+}
+
+// Fold completed phase timings into the counters (streams must be idle).
+void collect_timings(corr_ctx* x) {
+  for (auto& t : x->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, t.begin, t.end) == cudaSuccess) {
+      switch (t.phase) {
+        case kTurn: x->stats.turn_ms += ms; ++x->stats.timed_turn; break;
+        case kHerk: x->stats.herk_ms += ms; ++x->stats.timed_herk; break;
+        case kCopyIn: x->stats.copy_in_ms += ms; break;
+        case kDump: x->stats.dump_ms += ms; break;
+        default: x->stats.norm_ms += ms; break;
+      }
+    } else {
+      cudaGetLastError();
+    }
+    x->pool.push_back(t.begin);
+    x->pool.push_back(t.end);
+  }
+  x->pending.clear();
+}
 
 int cuda_fail(cudaError_t e) {
   (void)e;
@@ -56,8 +149,12 @@ bool is_device_ptr(const void* p) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
-// Tasks of the lower-triangle tiling of the real Gram matrix (see
-// HerkTask), ordered by decreasing work so that large tasks start first.
+// Tasks of the real Gram matrix: every 128 x 128 block (r, c), c <= r, of
+// the lower triangle exactly once.  Row block r takes the column blocks
+// r, r+1, ..., r + (nrb-1)/2 (mod nrb) -- for even nrb, r + nrb/2 goes to
+// the smaller of the two -- so the work is spread evenly over the row
+// blocks, and pairs of them form 128 x 256 MMAs.  Ordered by decreasing
+// work.
 std::vector<HerkTask> plan_tasks(int n, int c, int* rows_per_chan) {
   std::vector<HerkTask> t;
   const int rows = 2 * n;
@@ -66,27 +163,22 @@ std::vector<HerkTask> plan_tasks(int n, int c, int* rows_per_chan) {
     while (rpc < rows) rpc <<= 1;
     *rows_per_chan = rpc;
     const int per = 128 / rpc;
-    for (int c0 = 0; c0 < c; c0 += per) t.push_back({c0, 0, 0, 1});
+    for (int c0 = 0; c0 < c; c0 += per) t.push_back({c0, 0, {0, -1}});
     return t;
   }
   *rows_per_chan = 0;
   const int nrb = (rows + 127) / 128;
   for (int ch = 0; ch < c; ++ch)
-    for (int rb = 0; rb < nrb; ++rb) {
-      int cb = 0;
-      while (cb <= rb) {
-        if (rb - cb + 1 <= 4) {
-          t.push_back({ch, rb, cb, rb + 1});
-          cb = rb + 1;
-        } else {
-          t.push_back({ch, rb, cb, cb + 3});
-          cb += 3;
-        }
-      }
+    for (int r = 0; r < nrb; ++r) {
+      std::vector<int> cols;
+      for (int d = 0; 2 * d < nrb; ++d)
+        if (2 * d != nrb || r < nrb / 2) cols.push_back((r + d) % nrb);
+      if (nrb % 2 == 0 && r < nrb / 2 && 2 * (nrb / 2) == nrb) cols.push_back(r + nrb / 2);
+      for (size_t k = 0; k < cols.size(); k += 2)
+        t.push_back({ch, r, {cols[k], k + 1 < cols.size() ? cols[k + 1] : -1}});
     }
   std::stable_sort(t.begin(), t.end(), [](const HerkTask& x, const HerkTask& y) {
-    const int wx = x.cb1 - x.cb0, wy = y.cb1 - y.cb0;
-    return wx > wy;
+    return (x.cb[1] >= 0) > (y.cb[1] >= 0);
   });
   return t;
 }
@@ -105,6 +197,11 @@ void free_ctx(corr_ctx* x) {
   cudaFree(x->tasks);
   cudaFree(x->d_status);
   cudaFree(x->rho_tmp);
+  for (auto& t : x->pending) {
+    cudaEventDestroy(t.begin);
+    cudaEventDestroy(t.end);
+  }
+  for (auto e : x->pool) cudaEventDestroy(e);
   if (x->h_status) cudaFreeHost(x->h_status);
   if (x->copy_stream) cudaStreamDestroy(x->copy_stream);
   if (x->own_stream && x->stream) cudaStreamDestroy(x->stream);
@@ -183,7 +280,9 @@ int corr_create(int n_inputs, int n_chans, int n_time, int bits, int layout, uns
     if (cudaStreamCreateWithFlags(&x->copy_stream, cudaStreamNonBlocking) != cudaSuccess) { st = CORR_ECUDA; break; }
     x->acc_bytes = (size_t)corr_n_baselines(n_inputs) * n_chans * 2 * sizeof(int64_t);
     if (cudaMalloc(&x->acc, x->acc_bytes) != cudaSuccess) { st = CORR_ENOMEM; break; }
-    if (layout != CORR_L_CIT && cudaMalloc(&x->turned, block_bytes) != cudaSuccess) { st = CORR_ENOMEM; break; }
+    x->turned_stride = ((long long)n_time + 15) / 16 * 16;
+    if (layout != CORR_L_CIT &&
+        cudaMalloc(&x->turned, (size_t)x->turned_stride * n_inputs * n_chans) != cudaSuccess) { st = CORR_ENOMEM; break; }
     if (cudaMalloc(&x->d_status, sizeof(int)) != cudaSuccess) { st = CORR_ENOMEM; break; }
     if (cudaMemset(x->d_status, 0, sizeof(int)) != cudaSuccess) { st = CORR_ECUDA; break; }
     if (cudaMallocHost(&x->h_status, sizeof(int)) != cudaSuccess) { st = CORR_ENOMEM; break; }
@@ -200,7 +299,7 @@ int corr_create(int n_inputs, int n_chans, int n_time, int bits, int layout, uns
     if (cudaMalloc(&x->tasks, tasks.size() * sizeof(HerkTask)) != cudaSuccess) { st = CORR_ENOMEM; break; }
     if (cudaMemcpy(x->tasks, tasks.data(), tasks.size() * sizeof(HerkTask), cudaMemcpyHostToDevice) != cudaSuccess) { st = CORR_ECUDA; break; }
     x->smem_bytes = herk4_max_smem();
-    if (x->smem_bytes < 2 * 4 * 128 * 128 + 1024) { st = CORR_ECUDA; break; }
+    if (x->smem_bytes < 2 * 3 * (16384 + 8192) + 1024) { st = CORR_ECUDA; break; }
   } while (0);
   if (st != CORR_OK) {
     free_ctx(x);
@@ -214,7 +313,10 @@ int corr_push(corr_ctx* x, const void* block, size_t nbytes, uint64_t seq) {
   if (!x || !block) return CORR_EINVAL;
   if (nbytes != x->block_bytes) return CORR_EINVAL;
   if (seq != CORR_SEQ_ANY) {
-    if (x->seq_started && seq != x->next_seq) return CORR_ESEQ;
+    if (x->seq_started && seq != x->next_seq) {
+      ++x->stats.seq_rejects;
+      return CORR_ESEQ;
+    }
     x->seq_started = true;
     x->next_seq = seq + 1;
   }
@@ -225,25 +327,33 @@ int corr_push(corr_ctx* x, const void* block, size_t nbytes, uint64_t seq) {
     x->stage_next ^= 1;
     if (!x->stage[slot] && cudaMalloc(&x->stage[slot], x->block_bytes) != cudaSuccess)
       return CORR_ENOMEM;
-    if (cudaStreamWaitEvent(x->copy_stream, x->stage_free[slot], 0) != cudaSuccess ||
-        cudaMemcpyAsync(x->stage[slot], block, nbytes, cudaMemcpyHostToDevice, x->copy_stream) !=
-            cudaSuccess ||
-        cudaEventRecord(x->stage_ready[slot], x->copy_stream) != cudaSuccess ||
+    if (cudaStreamWaitEvent(x->copy_stream, x->stage_free[slot], 0) != cudaSuccess)
+      return CORR_ECUDA;
+    cudaEvent_t tc = phase_begin(x, x->copy_stream);
+    if (cudaMemcpyAsync(x->stage[slot], block, nbytes, cudaMemcpyHostToDevice, x->copy_stream) !=
+        cudaSuccess)
+      return CORR_ECUDA;
+    phase_end(x, kCopyIn, tc, x->copy_stream);
+    if (cudaEventRecord(x->stage_ready[slot], x->copy_stream) != cudaSuccess ||
         cudaStreamWaitEvent(x->stream, x->stage_ready[slot], 0) != cudaSuccess)
       return CORR_ECUDA;
     src = x->stage[slot];
   }
   const int N = x->n_inputs, C = x->n_chans, T = x->n_time;
-  if (x->layout == CORR_L_TCI) {
-    // [t][c][i] -> [c][i][t]: one transpose of a T x (C N) byte matrix
-    cudaError_t e = turn_launch(src, x->turned, T, 1, C * N, x->stream);
+  long long row_stride = T;
+  if (x->layout != CORR_L_CIT) {
+    // [t][c][i] -> [c][i][t] is one transpose of a T x (C N) byte matrix;
+    // [t][i][c] -> [c][i][t] is N transposes of T x C.
+    cudaEvent_t tt = phase_begin(x, x->stream);
+    cudaError_t e =
+        x->layout == CORR_L_TCI
+            ? turn_launch(src, x->turned, T, 1, C * N, x->turned_stride, x->stream)
+            : turn_launch(src, x->turned, T, N, C, x->turned_stride, x->stream);
     if (e != cudaSuccess) return cuda_fail(e);
+    phase_end(x, kTurn, tt, x->stream);
+    ++x->stats.turn_launches;
     src = x->turned;
-  } else if (x->layout == CORR_L_TIC) {
-    // [t][i][c] -> [c][i][t]
-    cudaError_t e = turn_launch(src, x->turned, T, N, C, x->stream);
-    if (e != cudaSuccess) return cuda_fail(e);
-    src = x->turned;
+    row_stride = x->turned_stride;
   }
   HerkArgs a;
   memset(&a, 0, sizeof(a));
@@ -251,22 +361,33 @@ int corr_push(corr_ctx* x, const void* block, size_t nbytes, uint64_t seq) {
   a.acc = x->acc;
   a.tasks = x->tasks;
   a.status = x->d_status;
-  a.chan_stride = (long long)N * T;
-  a.row_stride = T;
+  a.chan_stride = (long long)N * row_stride;
+  a.row_stride = row_stride;
   a.n_inputs = N;
   a.n_chans = C;
   a.rows_per_chan = x->rows_per_chan;
   a.lo_is_real = (x->flags & CORR_F_LO_IS_REAL) ? 1 : 0;
   a.smem_bytes = x->smem_bytes;
+  // The TMA kernel needs 16-byte aligned rows; otherwise plain loads.
+  CUtensorMap tmap;
+  const bool aligned = row_stride % 16 == 0 && reinterpret_cast<uintptr_t>(src) % 16 == 0;
+  const int box_in = x->rows_per_chan ? x->rows_per_chan / 2 : 64;
+  const int box_ch = x->rows_per_chan ? 128 / x->rows_per_chan : 1;
+  const bool use_tma =
+      aligned && make_sample_tmap(&tmap, src, T, row_stride, N, C, box_in, box_ch);
   for (int t0 = 0; t0 < T; t0 += kMaxChunk4) {
     a.t0 = t0;
     a.tn = std::min(kMaxChunk4, T - t0);
     a.accumulate = x->acc_live ? 1 : 0;
-    a.vec_ok = (T % 16 == 0) && (t0 % 16 == 0) && (reinterpret_cast<uintptr_t>(src) % 16 == 0);
-    cudaError_t e = herk4_launch(a, x->n_tasks, x->stream);
+    a.vec_ok = aligned ? 1 : 0;
+    cudaEvent_t th = phase_begin(x, x->stream);
+    cudaError_t e = herk4_launch(a, use_tma ? &tmap : nullptr, x->n_tasks, x->stream);
     if (e != cudaSuccess) return cuda_fail(e);
+    phase_end(x, kHerk, th, x->stream);
+    ++x->stats.herk_launches;
     x->acc_live = true;
   }
+  ++x->stats.blocks;
   if (slot >= 0 && cudaEventRecord(x->stage_free[slot], x->stream) != cudaSuccess)
     return CORR_ECUDA;
   return CORR_OK;
@@ -283,8 +404,10 @@ int corr_dump(corr_ctx* x, int64_t* vis, int reset) {
   if (vis) {
     const bool dev = is_device_ptr(vis);
     if (x->acc_live) {
+      cudaEvent_t td = phase_begin(x, x->stream);
       if (cudaMemcpyAsync(vis, x->acc, x->acc_bytes, cudaMemcpyDefault, x->stream) != cudaSuccess)
         return CORR_ECUDA;
+      phase_end(x, kDump, td, x->stream);
     } else if (dev) {
       if (cudaMemsetAsync(vis, 0, x->acc_bytes, x->stream) != cudaSuccess) return CORR_ECUDA;
     } else {
@@ -292,6 +415,7 @@ int corr_dump(corr_ctx* x, int64_t* vis, int reset) {
       memset(vis, 0, x->acc_bytes);
     }
   }
+  ++x->stats.dumps;
   const int st = take_status(x);
   if (reset) {
     x->acc_live = false;
@@ -313,11 +437,30 @@ int corr_normalise(corr_ctx* x, double* rho) {
     if (!x->rho_tmp && cudaMalloc(&x->rho_tmp, bytes) != cudaSuccess) return CORR_ENOMEM;
     d = x->rho_tmp;
   }
+  cudaEvent_t tn = phase_begin(x, x->stream);
   cudaError_t e = normalise_launch(x->acc, d, x->n_inputs, x->n_chans, x->stream);
   if (e != cudaSuccess) return cuda_fail(e);
+  phase_end(x, kNorm, tn, x->stream);
+  ++x->stats.norm_launches;
   if (!dev && cudaMemcpyAsync(rho, d, bytes, cudaMemcpyDeviceToHost, x->stream) != cudaSuccess)
     return CORR_ECUDA;
   return take_status(x);
+}
+
+int corr_set_timing(corr_ctx* x, int on) {
+  if (!x) return CORR_EINVAL;
+  x->timing = on != 0;
+  return CORR_OK;
+}
+
+int corr_get_stats(corr_ctx* x, corr_stats* out) {
+  if (!x || !out) return CORR_EINVAL;
+  if (cudaStreamSynchronize(x->copy_stream) != cudaSuccess ||
+      cudaStreamSynchronize(x->stream) != cudaSuccess)
+    return CORR_ECUDA;
+  collect_timings(x);
+  *out = x->stats;
+  return CORR_OK;
 }
 
 int corr_destroy(corr_ctx* x) {

@@ -23,7 +23,7 @@ __device__ __forceinline__ void transpose4x4(uint32_t& a0, uint32_t& a1, uint32_
 
 __global__ void __launch_bounds__(256) turn_kernel(const uint8_t* __restrict__ in,
                                                    uint8_t* __restrict__ out, int T, int G, int K,
-                                                   int vec_ok) {
+                                                   long long os, int vec_ok) {
   __shared__ __align__(16) uint32_t tile[kTT * kPitch];
   const int t0 = blockIdx.x * kTT, k0 = blockIdx.y * kTK, g = blockIdx.z;
   const int tid = threadIdx.x;
@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(256) turn_kernel(const uint8_t* __restrict__ i
   for (int c = 0; c < 4; ++c) {
     const int k = k0 + 4 * kq + c;
     const int tb = t0 + ts * 32;
-    uint8_t* o = out + ((long long)k * G + g) * T + tb;
+    uint8_t* o = out + ((long long)k * G + g) * os + tb;
     if (full) {
       *reinterpret_cast<uint4*>(o) = make_uint4(a[c], a[4 + c], a[8 + c], a[12 + c]);
       *reinterpret_cast<uint4*>(o + 16) = make_uint4(a[16 + c], a[20 + c], a[24 + c], a[28 + c]);
@@ -97,12 +97,13 @@ __global__ void normalise_kernel(const int64_t* __restrict__ acc, double* __rest
 
 }  // namespace
 
-cudaError_t turn_launch(const uint8_t* in, uint8_t* out, int T, int G, int K, cudaStream_t s) {
-  const int vec_ok = (K % 16 == 0) && (T % 16 == 0) &&
+cudaError_t turn_launch(const uint8_t* in, uint8_t* out, int T, int G, int K, long long out_stride,
+                        cudaStream_t s) {
+  const int vec_ok = (K % 16 == 0) && (T % 16 == 0) && (out_stride % 16 == 0) &&
                      (reinterpret_cast<uintptr_t>(in) % 16 == 0) &&
                      (reinterpret_cast<uintptr_t>(out) % 16 == 0);
   dim3 grid((T + kTT - 1) / kTT, (K + kTK - 1) / kTK, G);
-  turn_kernel<<<grid, 256, 0, s>>>(in, out, T, G, K, vec_ok);
+  turn_kernel<<<grid, 256, 0, s>>>(in, out, T, G, K, out_stride, vec_ok);
   return cudaGetLastError();
 }
 

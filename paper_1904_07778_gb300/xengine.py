@@ -26,7 +26,8 @@ CORR_SEQ_ANY = (1 << 64) - 1
 _CUDA_STREAM_LEGACY = 0x1  # cudaStreamLegacy
 
 EXPORTS = ["corr_create", "corr_push", "corr_dump", "corr_normalise", "corr_sync",
-           "corr_destroy", "corr_strerror", "corr_n_baselines"]
+           "corr_destroy", "corr_strerror", "corr_n_baselines", "corr_set_timing",
+           "corr_get_stats"]
 
 if not os.path.exists(LIB_PATH):
     raise ImportError("libxengine.so is not built (run paper_1904_07778_gb300.build.build()); "
@@ -44,7 +45,24 @@ _lib.corr_strerror.argtypes = [_I]
 _lib.corr_strerror.restype = ctypes.c_char_p
 _lib.corr_n_baselines.argtypes = [_I]
 _lib.corr_n_baselines.restype = ctypes.c_int64
-for _f in ("corr_create", "corr_push", "corr_dump", "corr_normalise", "corr_sync", "corr_destroy"):
+
+
+class CorrStats(ctypes.Structure):
+    """Mirror of struct corr_stats."""
+    _fields_ = [(n, ctypes.c_uint64) for n in ("blocks", "seq_rejects", "dumps", "turn_launches",
+                                                "herk_launches", "norm_launches")] + \
+               [(n, ctypes.c_double) for n in ("turn_ms", "herk_ms", "copy_in_ms", "dump_ms",
+                                                "norm_ms")] + \
+               [(n, ctypes.c_uint64) for n in ("timed_turn", "timed_herk")]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+_lib.corr_set_timing.argtypes = [_P, _I]
+_lib.corr_get_stats.argtypes = [_P, ctypes.POINTER(CorrStats)]
+for _f in ("corr_create", "corr_push", "corr_dump", "corr_normalise", "corr_sync", "corr_destroy",
+           "corr_set_timing", "corr_get_stats"):
     getattr(_lib, _f).restype = _I
 
 
@@ -89,6 +107,14 @@ def corr_sync(ctx) -> int:
 
 def corr_destroy(ctx) -> int:
     return _lib.corr_destroy(ctx)
+
+
+def corr_set_timing(ctx, on: int) -> int:
+    return _lib.corr_set_timing(ctx, on)
+
+
+def corr_get_stats(ctx, out: CorrStats) -> int:
+    return _lib.corr_get_stats(ctx, ctypes.byref(out))
 
 
 def _ptr_and_size(buf):
@@ -152,6 +178,16 @@ class Correlator:
 
     def normalise(self):
         return self.normalise_into(np.empty((self.n_chans, self.n_baselines, 2), dtype=np.float64))
+
+    def set_timing(self, on=True):
+        corr_set_timing(self._ctx, 1 if on else 0)
+
+    def stats(self):
+        out = CorrStats()
+        st = corr_get_stats(self._ctx, out)
+        if st != CORR_OK:
+            raise CorrError(st, "corr_get_stats")
+        return out.as_dict()
 
     def sync(self):
         st = corr_sync(self._ctx)
