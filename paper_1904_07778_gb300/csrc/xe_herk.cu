@@ -38,7 +38,7 @@ namespace xe {
 namespace {
 
 constexpr int kMaxStages = 8;
-constexpr int kMaxBlocks = 3;                 // 128-row operand blocks per stage
+constexpr int kMaxBlocks = 2;                 // 128-row operand blocks per stage
 constexpr int kStageT = 128;                  // spectra per stage = one swizzle row
 constexpr int kOpBlockBytes = 128 * kStageT;  // unpacked: 128 rows x 128 spectra
 constexpr int kPkBlockBytes = 64 * kStageT;   // packed: 64 inputs x 128 spectra
@@ -302,12 +302,15 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const bool stacked = a.rows_per_chan > 0;
   const int op_stage = g.nblk * kOpBlockBytes, pk_stage = g.nblk * kPkBlockBytes;
-  // Ring depths: operand stages for every unpack group plus slack, packed
-  // stages with the rest of shared memory.
+  // Ring depths are multiples of the number of unpack groups, so that stage
+  // k always lands in a slot that only group k % kGroups fills: a group then
+  // waits on a slot whose previous fill was its own, and an mbarrier can
+  // never be more than one phase away from the phase awaited (a parity wait
+  // on an older phase would pass falsely).
   const int avail = a.smem_bytes - 1024;
-  int no = (avail - 3 * pk_stage) / op_stage;
-  no = no > 6 ? 6 : (no < 2 ? 2 : no);
-  int np = (avail - no * op_stage) / pk_stage;
+  int no = kGroups * ((avail - kGroups * pk_stage) / (kGroups * op_stage));
+  if (no > kMaxStages) no = kMaxStages;
+  int np = kGroups * ((avail - no * op_stage) / (kGroups * pk_stage));
   if (np > kMaxStages) np = kMaxStages;
   uint8_t* pk = ops + no * op_stage;
   const int nk = (a.tn + kStageT - 1) / kStageT;

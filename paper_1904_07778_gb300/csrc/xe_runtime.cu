@@ -153,8 +153,8 @@ bool is_device_ptr(const void* p) {
 // the lower triangle exactly once.  Row block r takes the column blocks
 // r, r+1, ..., r + (nrb-1)/2 (mod nrb) -- for even nrb, r + nrb/2 goes to
 // the smaller of the two -- so the work is spread evenly over the row
-// blocks, and pairs of them form 128 x 256 MMAs.  Ordered by decreasing
-// work.
+// blocks.  Columns r and r+1 form one 128 x 256 MMA task; further columns
+// are 128 x 128 tasks.  Ordered by decreasing work.
 std::vector<HerkTask> plan_tasks(int n, int c, int* rows_per_chan) {
   std::vector<HerkTask> t;
   const int rows = 2 * n;
@@ -174,8 +174,10 @@ std::vector<HerkTask> plan_tasks(int n, int c, int* rows_per_chan) {
       for (int d = 0; 2 * d < nrb; ++d)
         if (2 * d != nrb || r < nrb / 2) cols.push_back((r + d) % nrb);
       if (nrb % 2 == 0 && r < nrb / 2 && 2 * (nrb / 2) == nrb) cols.push_back(r + nrb / 2);
-      for (size_t k = 0; k < cols.size(); k += 2)
-        t.push_back({ch, r, {cols[k], k + 1 < cols.size() ? cols[k + 1] : -1}});
+      // the first two columns (r and r+1) share the A rows with a B block;
+      // the others take one column each so at most two blocks are resident
+      t.push_back({ch, r, {cols[0], cols.size() > 1 ? cols[1] : -1}});
+      for (size_t k = 2; k < cols.size(); ++k) t.push_back({ch, r, {cols[k], -1}});
     }
   std::stable_sort(t.begin(), t.end(), [](const HerkTask& x, const HerkTask& y) {
     return (x.cb[1] >= 0) > (y.cb[1] >= 0);
@@ -299,7 +301,7 @@ int corr_create(int n_inputs, int n_chans, int n_time, int bits, int layout, uns
     if (cudaMalloc(&x->tasks, tasks.size() * sizeof(HerkTask)) != cudaSuccess) { st = CORR_ENOMEM; break; }
     if (cudaMemcpy(x->tasks, tasks.data(), tasks.size() * sizeof(HerkTask), cudaMemcpyHostToDevice) != cudaSuccess) { st = CORR_ECUDA; break; }
     x->smem_bytes = herk4_max_smem();
-    if (x->smem_bytes < 2 * 3 * (16384 + 8192) + 1024) { st = CORR_ECUDA; break; }
+    if (x->smem_bytes < 4 * 2 * (16384 + 8192) + 1024) { st = CORR_ECUDA; break; }
   } while (0);
   if (st != CORR_OK) {
     free_ctx(x);

@@ -160,3 +160,32 @@ def test_cylinder_array_full_size_sampled(xe):
     ii = np.array([i * (i + 1) // 2 + i for i in range(N)])
     assert np.array_equal(vis[:, ii, 0].sum(axis=1), p)
     assert (vis[:, ii, 1] == 0).all() and (vis[:, ii, 0] >= 0).all()
+
+
+@pytest.mark.parametrize("N,C,T,layout", [(192, 256, 8192, 1), (32, 512, 4096, 0)])
+def test_repeatable_and_full_coverage(xe, N, C, T, layout):
+    """Races show up as run-to-run differences: five runs on the same bytes
+    must agree exactly; every channel is then checked against the oracle
+    through the Hermitian quadratic form w^H V w = sum_t |w^H x(t)|^2 for
+    random Gaussian-integer weights w (a wrong entry changes the form)."""
+    dblk = synth.block_device("sky", 7, N, C, T, layout=layout, device="cuda")
+    runs = []
+    for _ in range(5):
+        with xe.Correlator(N, C, T, layout=layout) as cor:
+            cor.push(dblk)
+            runs.append(cor.dump())
+    for r in runs[1:]:
+        assert np.array_equal(r, runs[0])
+    vis = runs[0]
+    rng = np.random.default_rng(9)
+    w = rng.integers(-2, 3, size=(2, N)) + 1j * rng.integers(-2, 3, size=(2, N))
+    want = oracle.projected_power(dblk.cpu().numpy(), N, C, T, w, layout=layout)
+    # w^H V w from the lower triangle: sum_i |w_i|^2 V_ii + 2 Re sum_{i>j} conj(w_i) V_ij w_j
+    ii, jj = np.tril_indices(N)
+    b = ii * (ii + 1) // 2 + jj
+    v = vis[:, b, 0] + 1j * vis[:, b, 1]
+    coef = np.conj(w[:, ii]) * w[:, jj]                     # [nvec][B]
+    diag = ii == jj
+    q = (v[:, None, :] * coef[None]).real                   # [C][nvec][B]
+    got = q[:, :, diag].sum(axis=2) + 2 * q[:, :, ~diag].sum(axis=2)
+    assert np.array_equal(np.rint(got).astype(np.int64), want)
