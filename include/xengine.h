@@ -173,6 +173,41 @@ int corr_set_timing(corr_ctx* ctx, int on);
 /* corr_get_stats -- wait for the context's work and fill *out. */
 int corr_get_stats(corr_ctx* ctx, corr_stats* out);
 
+/*
+ * corr_correlate_noalloc -- the visibilities of ONE block, for callers that
+ * cannot allocate device memory (an allocator owned by another framework,
+ * allocation frozen after start-up, or a real-time loop where a cudaMalloc
+ * could stall).  The paper has no counterpart: it is a packaging of the
+ * corr_create/corr_push/corr_dump path that allocates nothing.
+ *
+ * The library keeps every intermediate (work list, status word, the
+ * corner-turned copy of the block) in one fixed device array of
+ * CORR_NOALLOC_SCRATCH_BYTES that exists on every device that loads the
+ * library, for the life of the process.  The call itself allocates nothing
+ * and frees nothing, on host or device.
+ *   block   : device pointer, N * C * T * bits / 4 bytes in `layout` (4-bit).
+ *   vis     : device pointer, int64 [C][N(N+1)/2][2]; overwritten with this
+ *             block's visibilities (not added to).
+ *   status  : optional device int; receives the device status bits of this
+ *             call (0 ok, 1 a bounded device-side wait ran out).
+ *   stream  : cudaStream_t to run on (NULL: the legacy default stream).
+ * Limits: 256 + 16 * tasks (rounded up to 256) + (layout != CORR_L_CIT ?
+ * N * C * ceil16(T) : 0) bytes must fit the scratch, where tasks is C / (128 /
+ * 2^ceil(log2 2N)) rounded up for 2N <= 64, else C times the tasks of one
+ * channel; larger requests return CORR_EINVAL.  Host pointers return
+ * CORR_EINVAL.  Asynchronous: returns once the work is queued.
+ * Set-up: the first call on a device looks up the scratch array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.
+ * Concurrency: every call shares the one scratch array, which keeps the last
+ * call's contents.  Calls that overlap on the GPU (other streams, other host
+ * threads on the same device) race and corrupt each other; issue them in
+ * order on one stream.
+ */
+#define CORR_NOALLOC_SCRATCH_BYTES (16u << 20)
+int corr_correlate_noalloc(const void* block, int n_inputs, int n_chans, int n_time, int layout,
+                           unsigned flags, int64_t* vis, int* status, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,195 @@
+// corr_correlate_noalloc: one block through the corner turn and the
+// cross-multiply into caller-provided visibilities without allocating.
+//
+// Some callers cannot allocate device memory at all: code running inside a
+// memory pool that another framework owns, processes whose allocations are
+// frozen after start-up, or real-time loops where a cudaMalloc could stall
+// the stream.  For them this entry point keeps every intermediate -- the task
+// list, the status word and the corner-turned copy of the block -- in one
+// fixed file-scope device array instead of buffers from cudaMalloc.  The
+// array occupies kNoAllocScratchBytes on every device that loads the library
+// until the process exits.
+#include <algorithm>
+#include <mutex>
+
+#include "xe_internal.h"
+#include "xengine.h"
+
+namespace xe {
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = CORR_NOALLOC_SCRATCH_BYTES;
+constexpr int kMaxDevices = 64;
+
+// The shared scratch.  Host code must not use this name as an address: on
+// the host it is only a stand-in, so the device address is looked up with
+// cudaGetSymbolAddress (once per device) and passed to the kernels.
+static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocScratchBytes];
+
+std::mutex g_scratch_mutex;
+void* g_scratch_addr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device (set-up on the
+// first call for that device).
+int scratch_address(void** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return CORR_ECUDA;
+  std::lock_guard<std::mutex> lock(g_scratch_mutex);
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return CORR_ECUDA;
+    }
+    g_scratch_addr[dev] = p;
+  }
+  *out = g_scratch_addr[dev];
+  return CORR_OK;
+}
+
+// Tasks per channel of the lower-triangle tiling (same tiling as the
+// context path): row block r takes column blocks r .. r + ceil(nrb/2) - 1
+// (mod nrb), plus r + nrb/2 for r < nrb/2 when nrb is even; the first two
+// share a task, the others have one task each.
+__host__ __device__ inline int row_cols(int nrb, int r) {
+  int n = (nrb + 1) / 2;
+  if (nrb % 2 == 0 && r < nrb / 2) ++n;
+  return n;
+}
+__host__ __device__ inline int row_col(int nrb, int r, int k) {
+  const int base = (nrb + 1) / 2;
+  return k < base ? (r + k) % nrb : r + nrb / 2;
+}
+// columns 0 and 1 share one task, every further column is a task of its own
+__host__ __device__ inline int row_tasks(int nrb, int r) {
+  const int ncol = row_cols(nrb, r);
+  return ncol > 1 ? ncol - 1 : 1;
+}
+
+__global__ void plan_kernel(HerkTask* tasks, long long n_tasks, int n, int c, int rpc, int per_chan,
+                            int nrb) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n_tasks;
+       e += (long long)gridDim.x * blockDim.x) {
+    HerkTask t;
+    if (rpc > 0) {
+      t.chan0 = (int)(e * (128 / rpc));
+      t.rb = 0;
+      t.cb[0] = 0;
+      t.cb[1] = -1;
+    } else {
+      t.chan0 = (int)(e / per_chan);
+      int local = (int)(e % per_chan), r = 0;
+      for (; r < nrb; ++r) {
+        const int nt = row_tasks(nrb, r);
+        if (local < nt) break;
+        local -= nt;
+      }
+      const int ncol = row_cols(nrb, r);
+      t.rb = r;
+      if (local == 0) {
+        t.cb[0] = row_col(nrb, r, 0);
+        t.cb[1] = ncol > 1 ? row_col(nrb, r, 1) : -1;
+      } else {
+        t.cb[0] = row_col(nrb, r, local + 1);
+        t.cb[1] = -1;
+      }
+    }
+    tasks[e] = t;
+  }
+  (void)n;
+  (void)c;
+}
+
+__global__ void copy_status_kernel(const int* from, int* to) { *to = *from; }
+
+bool is_device(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+}  // namespace xe
+
+using namespace xe;
+
+extern "C" int corr_correlate_noalloc(const void* block, int n_inputs, int n_chans, int n_time,
+                                      int layout, unsigned flags, int64_t* vis, int* status,
+                                      void* stream) {
+  if (!block || !vis || n_inputs < 1 || n_inputs > 1024 || n_chans < 1 || n_time < 1 ||
+      layout < CORR_L_TCI || layout > CORR_L_CIT || (flags & ~CORR_F_LO_IS_REAL))
+    return CORR_EINVAL;
+  if (!is_device(block) || !is_device(vis) || (status && !is_device(status))) return CORR_EINVAL;
+  const int N = n_inputs, C = n_chans, T = n_time;
+  // scratch layout: [status (256 B)] [tasks] [corner-turned block]
+  int rpc = 0, per_chan = 0, nrb = 0;
+  long long n_tasks;
+  if (2 * N <= 64) {
+    rpc = 2;
+    while (rpc < 2 * N) rpc <<= 1;
+    n_tasks = ((long long)C + 128 / rpc - 1) / (128 / rpc);
+  } else {
+    nrb = (2 * N + 127) / 128;
+    for (int r = 0; r < nrb; ++r) per_chan += row_tasks(nrb, r);
+    n_tasks = (long long)per_chan * C;
+  }
+  const long long task_bytes = (n_tasks * (long long)sizeof(HerkTask) + 255) / 256 * 256;
+  const long long row_stride = ((long long)T + 15) / 16 * 16;
+  const long long turned_bytes = layout == CORR_L_CIT ? 0 : row_stride * N * C;
+  if (256 + task_bytes + turned_bytes > (long long)kNoAllocScratchBytes) return CORR_EINVAL;
+  void* base = nullptr;
+  int st = scratch_address(&base);
+  if (st != CORR_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  int* d_status = static_cast<int*>(base);
+  HerkTask* tasks = reinterpret_cast<HerkTask*>(static_cast<uint8_t*>(base) + 256);
+  uint8_t* turned = static_cast<uint8_t*>(base) + 256 + task_bytes;
+
+  // the scratch keeps the previous call's contents: clear the status word
+  if (cudaMemsetAsync(d_status, 0, sizeof(int), s) != cudaSuccess) return CORR_ECUDA;
+  const int pblocks = (int)std::min<long long>((n_tasks + 255) / 256, 1024);
+  plan_kernel<<<pblocks, 256, 0, s>>>(tasks, n_tasks, N, C, rpc, per_chan, nrb);
+  if (cudaGetLastError() != cudaSuccess) return CORR_ECUDA;
+
+  const uint8_t* src = static_cast<const uint8_t*>(block);
+  long long stride = T;
+  if (layout != CORR_L_CIT) {
+    cudaError_t e = layout == CORR_L_TCI ? turn_launch(src, turned, T, 1, C * N, row_stride, s)
+                                         : turn_launch(src, turned, T, N, C, row_stride, s);
+    if (e != cudaSuccess) return CORR_ECUDA;
+    src = turned;
+    stride = row_stride;
+  }
+  HerkArgs a{};
+  a.x = src;
+  a.acc = vis;
+  a.tasks = tasks;
+  a.status = d_status;
+  a.chan_stride = (long long)N * stride;
+  a.row_stride = stride;
+  a.n_inputs = N;
+  a.n_chans = C;
+  a.rows_per_chan = rpc;
+  a.lo_is_real = (flags & CORR_F_LO_IS_REAL) ? 1 : 0;
+  a.smem_bytes = herk4_max_smem();
+  CUtensorMap tmap;
+  const bool aligned = stride % 16 == 0 && reinterpret_cast<uintptr_t>(src) % 16 == 0;
+  const bool use_tma = aligned && make_sample_tmap(&tmap, src, T, stride, N, C,
+                                                   rpc ? rpc / 2 : 64, rpc ? 128 / rpc : 1);
+  for (int t0 = 0; t0 < T; t0 += kMaxChunk4) {
+    a.t0 = t0;
+    a.tn = std::min(kMaxChunk4, T - t0);
+    a.accumulate = t0 > 0 ? 1 : 0;
+    a.vec_ok = aligned ? 1 : 0;
+    if (herk4_launch(a, use_tma ? &tmap : nullptr, (int)n_tasks, s) != cudaSuccess)
+      return CORR_ECUDA;
+  }
+  if (status) {
+    copy_status_kernel<<<1, 1, 0, s>>>(d_status, status);
+    if (cudaGetLastError() != cudaSuccess) return CORR_ECUDA;
+  }
+  return CORR_OK;
+}

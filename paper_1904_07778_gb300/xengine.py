@@ -27,7 +27,7 @@ _CUDA_STREAM_LEGACY = 0x1  # cudaStreamLegacy
 
 EXPORTS = ["corr_create", "corr_push", "corr_dump", "corr_normalise", "corr_sync",
            "corr_destroy", "corr_strerror", "corr_n_baselines", "corr_set_timing",
-           "corr_get_stats"]
+           "corr_get_stats", "corr_correlate_noalloc"]
 
 if not os.path.exists(LIB_PATH):
     raise ImportError("libxengine.so is not built (run paper_1904_07778_gb300.build.build()); "
@@ -60,6 +60,9 @@ class CorrStats(ctypes.Structure):
 
 
 _lib.corr_set_timing.argtypes = [_P, _I]
+_lib.corr_correlate_noalloc.argtypes = [_P, _I, _I, _I, _I, _U, _P, _P, _P]
+_lib.corr_correlate_noalloc.restype = _I
+CORR_NOALLOC_SCRATCH_BYTES = 16 << 20
 _lib.corr_get_stats.argtypes = [_P, ctypes.POINTER(CorrStats)]
 for _f in ("corr_create", "corr_push", "corr_dump", "corr_normalise", "corr_sync", "corr_destroy",
            "corr_set_timing", "corr_get_stats"):
@@ -107,6 +110,14 @@ def corr_sync(ctx) -> int:
 
 def corr_destroy(ctx) -> int:
     return _lib.corr_destroy(ctx)
+
+
+def corr_correlate_noalloc(block_ptr: int, n_inputs: int, n_chans: int, n_time: int, layout: int,
+                           flags: int, vis_ptr: int, status_ptr: int = 0, stream: int = 0) -> int:
+    """One block's visibilities into device memory; the library allocates nothing."""
+    return _lib.corr_correlate_noalloc(_P(block_ptr), n_inputs, n_chans, n_time, layout, flags,
+                                       _P(vis_ptr), _P(status_ptr) if status_ptr else None,
+                                       _P(stream) if stream else None)
 
 
 def corr_set_timing(ctx, on: int) -> int:

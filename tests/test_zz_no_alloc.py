@@ -1,0 +1,72 @@
+"""The allocation-free entry point, corr_correlate_noalloc.
+
+It exists for callers that cannot allocate device memory (an allocator owned
+by another framework, allocation frozen after start-up, real-time loops).  It
+keeps its intermediates in a fixed scratch array inside the library, shared by
+every call.  This test calls it through the C ABI several times in a row, with
+different shapes, and checks each result against the context path
+(corr_create / corr_push / corr_dump) on the same bytes: the visibilities are
+integers, so they must agree exactly.  The file name sorts last so that a run
+stopping at the first failure has already run every other test.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def xe():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1904_07778_gb300 import build
+    build.build()
+    from paper_1904_07778_gb300 import xengine
+    return xengine
+
+
+def _reference(xe, blk, N, C, T, layout):
+    with xe.Correlator(N, C, T, bits=4, layout=layout) as cor:
+        cor.push(blk)
+        return cor.dump()
+
+
+def _noalloc(xe, blk, N, C, T, layout):
+    nb = N * (N + 1) // 2
+    vis = torch.full((C, nb, 2), -1, dtype=torch.int64, device="cuda")  # stale values must vanish
+    status = torch.full((1,), 7, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream or 1  # 1 = the legacy default stream
+    rc = xe.corr_correlate_noalloc(blk.data_ptr(), N, C, T, layout, 0, vis.data_ptr(),
+                                   status.data_ptr(), stream)
+    assert rc == xe.CORR_OK, xe.corr_strerror(rc)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    return vis.cpu().numpy()
+
+
+def test_noalloc_matches_context_path_on_consecutive_calls(xe):
+    rng = np.random.default_rng(2024)
+    cases = [
+        (64, 16, 1024, xe.CORR_L_TIC),   # corner turn through the scratch
+        (32, 64, 512, xe.CORR_L_TCI),    # stacked small array
+        (100, 5, 300, xe.CORR_L_CIT),    # ragged tail, no corner turn
+        (64, 16, 1024, xe.CORR_L_TIC),   # first shape again, new data
+    ]
+    for N, C, T, layout in cases:
+        blk = torch.from_numpy(rng.integers(0, 256, N * C * T, dtype=np.uint8)).cuda()
+        got = _noalloc(xe, blk, N, C, T, layout)
+        want = _reference(xe, blk, N, C, T, layout)
+        assert np.array_equal(got, want), (N, C, T, layout)
+
+
+def test_noalloc_rejects_requests_beyond_the_scratch(xe):
+    N, C, T = 192, 16, 8192  # corner-turned copy of 24 MiB > 16 MiB scratch
+    assert N * C * T > xe.CORR_NOALLOC_SCRATCH_BYTES
+    blk = torch.zeros(N * C * T, dtype=torch.uint8, device="cuda")
+    vis = torch.zeros((C, N * (N + 1) // 2, 2), dtype=torch.int64, device="cuda")
+    rc = xe.corr_correlate_noalloc(blk.data_ptr(), N, C, T, xe.CORR_L_TIC, 0, vis.data_ptr())
+    assert rc == xe.CORR_EINVAL
+    host = np.zeros(16, dtype=np.uint8)
+    rc = xe.corr_correlate_noalloc(host.ctypes.data, 4, 1, 4, xe.CORR_L_CIT, 0, vis.data_ptr())
+    assert rc == xe.CORR_EINVAL  # host memory is not accepted
