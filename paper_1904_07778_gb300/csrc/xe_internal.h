@@ -64,7 +64,7 @@ bool make_sample_tmap(CUtensorMap* m, const uint8_t* x, int n_time, long long ro
                       int n_inputs, int n_chans, int box_inputs, int box_chans);
 
 // Corner turn of byte samples: in[t][g][k] -> out[k][g][t], output rows of
-// out_stride >= T bytes.
+// out_stride >= T bytes (32-byte aligned rows take the fast path).
 cudaError_t turn_launch(const uint8_t* in, uint8_t* out, int T, int G, int K, long long out_stride,
                         cudaStream_t s);
 

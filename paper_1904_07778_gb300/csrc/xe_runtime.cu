@@ -282,7 +282,7 @@ int corr_create(int n_inputs, int n_chans, int n_time, int bits, int layout, uns
     if (cudaStreamCreateWithFlags(&x->copy_stream, cudaStreamNonBlocking) != cudaSuccess) { st = CORR_ECUDA; break; }
     x->acc_bytes = (size_t)corr_n_baselines(n_inputs) * n_chans * 2 * sizeof(int64_t);
     if (cudaMalloc(&x->acc, x->acc_bytes) != cudaSuccess) { st = CORR_ENOMEM; break; }
-    x->turned_stride = ((long long)n_time + 15) / 16 * 16;
+    x->turned_stride = ((long long)n_time + 31) / 32 * 32;  // 32-byte rows for the corner turn
     if (layout != CORR_L_CIT &&
         cudaMalloc(&x->turned, (size_t)x->turned_stride * n_inputs * n_chans) != cudaSuccess) { st = CORR_ENOMEM; break; }
     if (cudaMalloc(&x->d_status, sizeof(int)) != cudaSuccess) { st = CORR_ENOMEM; break; }

@@ -7,9 +7,11 @@ namespace {
 
 // ---------------------------------------------------------------- corner turn
 // in[t][g][k] -> out[k][g][t] for byte samples, through a 256 (t) x 128 (k)
-// shared-memory tile: 16-byte coalesced loads along k, a 4 x 4 byte
-// transpose in registers, 16-byte stores along t.
-constexpr int kTT = 256, kTK = 128, kPitch = 36;  // pitch in 32-bit words (16-byte aligned)
+// shared-memory tile of 32-bit words.  Word w of tile row r is stored at
+// r * 32 + (w ^ 4 * (r >> 5)): the 16-byte chunk index is XOR-ed with the
+// row's 32-row band, which makes both the row-wise stores and the
+// column-wise loads below free of bank conflicts without padding.
+constexpr int kTT = 256, kTK = 128;
 
 __device__ __forceinline__ void transpose4x4(uint32_t& a0, uint32_t& a1, uint32_t& a2,
                                              uint32_t& a3) {
@@ -21,47 +23,78 @@ __device__ __forceinline__ void transpose4x4(uint32_t& a0, uint32_t& a1, uint32_
   a3 = __byte_perm(t1, t3, 0x7632);
 }
 
-__global__ void __launch_bounds__(256) turn_kernel(const uint8_t* __restrict__ in,
-                                                   uint8_t* __restrict__ out, int T, int G, int K,
-                                                   long long os, int vec_ok) {
-  __shared__ __align__(16) uint32_t tile[kTT * kPitch];
+__device__ __forceinline__ void ld32B(const uint8_t* p, uint32_t (&r)[8]) {
+  asm volatile("ld.global.nc.L1::no_allocate.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                 "=r"(r[6]), "=r"(r[7])
+               : "l"(p));
+}
+__device__ __forceinline__ void st32B(uint8_t* p, const uint32_t (&r)[8]) {
+  asm volatile("st.global.v8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "r"(r[0]), "r"(r[1]),
+               "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+               : "memory");
+}
+
+__device__ __forceinline__ int tile_word(int row, int w) { return row * 32 + (w ^ ((row >> 5) << 2)); }
+
+__global__ void __launch_bounds__(256, 4) turn_kernel(const uint8_t* __restrict__ in,
+                                                      uint8_t* __restrict__ out, int T, int G,
+                                                      int K, long long os, int vec_ok) {
+  __shared__ __align__(16) uint32_t tile[kTT * 32];
   const int t0 = blockIdx.x * kTT, k0 = blockIdx.y * kTK, g = blockIdx.z;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const bool full = vec_ok && t0 + kTT <= T && k0 + kTK <= K;
-  // load: 256 rows of 128 bytes
-#pragma unroll 4
-  for (int e = tid; e < kTT * 8; e += 256) {
-    const int r = e >> 3, q = e & 7;
-    const long long off = ((long long)(t0 + r) * G + g) * K + k0 + 16 * q;
-    uint4 v;
-    if (full) {
-      v = ld_stream16(in + off);
-    } else {
-      uint32_t w[4] = {0u, 0u, 0u, 0u};
-      if (t0 + r < T)
-        for (int b = 0; b < 16; ++b)
-          if (k0 + 16 * q + b < K) w[b >> 2] |= (uint32_t)in[off + b] << ((b & 3) * 8);
-      v = make_uint4(w[0], w[1], w[2], w[3]);
+  // load: 256 rows x 128 bytes as 32-byte pieces, four per thread, all
+  // issued before any of them is stored
+  if (full) {
+    uint32_t v[4][8];
+#pragma unroll
+    for (int it = 0; it < 4; ++it) {
+      const int e = it * 256 + tid, r = e >> 2, p = e & 3;
+      ld32B(in + ((long long)(t0 + r) * G + g) * K + k0 + 32 * p, v[it]);
     }
-    *reinterpret_cast<uint4*>(&tile[r * kPitch + 4 * q]) = v;
+#pragma unroll
+    for (int it = 0; it < 4; ++it) {
+      const int e = it * 256 + tid, r = e >> 2, p = e & 3;
+      // odd rows store their second 16-byte half first: the two rows of a
+      // quarter-warp then hit disjoint banks
+      const bool odd = r & 1;
+      const uint4 lo = make_uint4(v[it][0], v[it][1], v[it][2], v[it][3]);
+      const uint4 hi = make_uint4(v[it][4], v[it][5], v[it][6], v[it][7]);
+      *reinterpret_cast<uint4*>(&tile[tile_word(r, 8 * p + (odd ? 4 : 0))]) = odd ? hi : lo;
+      *reinterpret_cast<uint4*>(&tile[tile_word(r, 8 * p + (odd ? 0 : 4))]) = odd ? lo : hi;
+    }
+  } else {
+    for (int e = tid; e < kTT * 32; e += 256) {
+      const int r = e >> 5, w = e & 31;
+      uint32_t x = 0;
+      if (t0 + r < T) {
+        const long long off = ((long long)(t0 + r) * G + g) * K + k0 + 4 * w;
+        for (int b = 0; b < 4; ++b)
+          if (k0 + 4 * w + b < K) x |= (uint32_t)in[off + b] << (8 * b);
+      }
+      tile[tile_word(r, w)] = x;
+    }
   }
   __syncthreads();
-  // store: thread = (4 consecutive k, 32 consecutive t)
-  const int kq = tid & 31, ts = tid >> 5;
+  // store: thread = 4 consecutive k (word kq) x 32 consecutive t (segment ts);
+  // the eight lanes of a k-quad cover one 256-byte stretch of each output row
+  const int kq = 4 * warp + (lane >> 3), ts = lane & 7;
   uint32_t a[32];
 #pragma unroll
-  for (int j = 0; j < 32; ++j) a[j] = tile[(ts * 32 + j) * kPitch + kq];
+  for (int j = 0; j < 32; ++j) a[j] = tile[tile_word(ts * 32 + j, kq)];
 #pragma unroll
   for (int j = 0; j < 32; j += 4) transpose4x4(a[j], a[j + 1], a[j + 2], a[j + 3]);
-  // after the transposes a[4w + c] holds t = ts*32 + 4w .. +3 of k = 4 kq + c
+  // a[4w + c] now holds t = ts*32 + 4w .. +3 of k = 4 kq + c
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
     const int k = k0 + 4 * kq + c;
     const int tb = t0 + ts * 32;
     uint8_t* o = out + ((long long)k * G + g) * os + tb;
     if (full) {
-      *reinterpret_cast<uint4*>(o) = make_uint4(a[c], a[4 + c], a[8 + c], a[12 + c]);
-      *reinterpret_cast<uint4*>(o + 16) = make_uint4(a[16 + c], a[20 + c], a[24 + c], a[28 + c]);
+      const uint32_t r[8] = {a[c], a[4 + c], a[8 + c], a[12 + c],
+                             a[16 + c], a[20 + c], a[24 + c], a[28 + c]};
+      st32B(o, r);
     } else if (k < K) {
       for (int b = 0; b < 32; ++b)
         if (tb + b < T) o[b] = (uint8_t)(a[4 * (b >> 2) + c] >> ((b & 3) * 8));
@@ -99,9 +132,9 @@ __global__ void normalise_kernel(const int64_t* __restrict__ acc, double* __rest
 
 cudaError_t turn_launch(const uint8_t* in, uint8_t* out, int T, int G, int K, long long out_stride,
                         cudaStream_t s) {
-  const int vec_ok = (K % 16 == 0) && (T % 16 == 0) && (out_stride % 16 == 0) &&
-                     (reinterpret_cast<uintptr_t>(in) % 16 == 0) &&
-                     (reinterpret_cast<uintptr_t>(out) % 16 == 0);
+  const int vec_ok = (K % 32 == 0) && (T % 32 == 0) && (out_stride % 32 == 0) &&
+                     (reinterpret_cast<uintptr_t>(in) % 32 == 0) &&
+                     (reinterpret_cast<uintptr_t>(out) % 32 == 0);
   dim3 grid((T + kTT - 1) / kTT, (K + kTK - 1) / kTK, G);
   turn_kernel<<<grid, 256, 0, s>>>(in, out, T, G, K, out_stride, vec_ok);
   return cudaGetLastError();
