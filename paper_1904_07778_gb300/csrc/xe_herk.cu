@@ -23,21 +23,22 @@
 // term; padded rows are computed but never written.
 //
 // Kernels:
-//   herk4_tma_kernel  (fast path) one warp streams packed bytes into a ring
-//       of shared-memory stages with TMA; four groups of two warps unpack
-//       stages k = g (mod 4) into the 128-byte-swizzled K-major operand ring,
-//       so the latency of one stage overlaps three others; one warp issues
-//       the MMAs; the eight unpack warps then drain tensor memory.
+//   herk4_ring_kernel (fast path) persistent, one CTA per SM: a TMA warp
+//       streams packed bytes into a ring of shared-memory slots, four groups
+//       of four warps unpack them in place into the 128-byte-swizzled K-major
+//       operand layout, one warp issues the MMAs into two alternating
+//       tensor-memory accumulators, and eight warps drain the previous task.
 //   herk4_ldg_kernel  (any alignment) four warps load with 16-byte or byte
 //       loads from global memory instead of TMA.
 #include <algorithm>
+#include <cstring>
 
 #include "xe_device.cuh"
 
 namespace xe {
 namespace {
 
-constexpr int kMaxStages = 8;
+constexpr int kMaxStages = 12;
 constexpr int kMaxBlocks = 2;                 // 128-row operand blocks per stage
 constexpr int kStageT = 128;                  // spectra per stage = one swizzle row
 constexpr int kOpBlockBytes = 128 * kStageT;  // unpacked: 128 rows x 128 spectra
@@ -178,19 +179,22 @@ __device__ __forceinline__ void mma_loop(const TaskGeom& g, int nk, int nst, uin
 
 // Drain the accumulators, correct the offset codes, fold 2 x 2 real blocks
 // into complex visibilities and store or add them into the int64
-// integration buffer.  NW warps: warp w reads tensor-memory lanes
-// 32 (w % 4) .. + 31 (rows of the A block) and the (w / 4)-th share of the
-// 32-column chunks.  Column block c < rb is a lower-triangle block, c == rb
-// the diagonal block (entries j <= i only), c > rb the transpose of block
-// (c, rb): there the thread's row is the second input of the baseline and
-// the imaginary part changes sign.
-template <int NW>
+// integration buffer.  The calling warp reads tensor-memory lanes
+// 32 quad .. + 31 (rows of the A block; quad must be the warp index mod 4)
+// and the part-th of nparts shares of the 32-column chunks.  Column block
+// c < rb is a lower-triangle block, c == rb the diagonal block (entries
+// j <= i only), c > rb the transpose of block (c, rb): there the thread's
+// row is the second input of the baseline and the imaginary part changes
+// sign.  The two lanes of an input (rows 2i and 2i + 1) exchange halves so
+// that each holds whole (Re, Im) pairs: the even-numbered columns j of the
+// chunk go to the lane of row 2i, the odd ones to row 2i + 1, and each
+// visibility is one 16-byte store (adjacent lanes fill 32 contiguous bytes
+// in lower blocks, 16 lanes fill 256 contiguous bytes in upper blocks).
 __device__ __forceinline__ void epilogue(const HerkArgs& a, const HerkTask& task, const TaskGeom& g,
-                                         const int32_t* usum, uint32_t tmem, int tid) {
-  const int warp = tid >> 5;
-  const int quad = warp & 3, part = warp >> 2;
+                                         const int32_t* usum, uint32_t tmem, int quad, int part,
+                                         int nparts, int lane) {
   const bool stacked = a.rows_per_chan > 0;
-  const int p = quad * 32 + (tid & 31);
+  const int p = quad * 32 + lane;
   const int n = a.n_inputs;
   int ch, i, plane;
   bool row_ok;
@@ -210,49 +214,68 @@ __device__ __forceinline__ void epilogue(const HerkArgs& a, const HerkTask& task
   }
   const int base_term = 64 * a.tn - 8 * usum[g.a_slot * 128 + p];
   const long long nbl = (long long)n * (n + 1) / 2;
-  int64_t* chp = a.acc + (long long)ch * nbl * 2;
+  int64_t* chp = a.acc + (long long)(row_ok ? ch : 0) * nbl * 2;
+  const int tri_i = i * (i + 1) / 2;  // baselines per channel stay below 2^30 (inputs <= 32768)
   const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16);
-  const int nch = g.nb * 4, per = nch / (NW / 4);
+  const int nch = g.nb * 8, per = nch / nparts;  // 16-column chunks
   for (int cc = part * per; cc < (part + 1) * per; ++cc) {
-    uint32_t r[32];
-    tmem_load32(trow + (uint32_t)(cc * 32), r);
-    int gv[32];
+    uint32_t r[16];
+    tmem_load16(trow + (uint32_t)(cc * 16), r);
+    int gv[16];
 #pragma unroll
-    for (int k = 0; k < 32; ++k)
-      gv[k] = __float2int_rn(__uint_as_float(r[k]) * 262144.0f) + base_term - 8 * usum[cc * 32 + k];
-    const int cblk = slot_block(g, cc >> 2);
+    for (int k = 0; k < 16; ++k)
+      gv[k] = __float2int_rn(__uint_as_float(r[k]) * 262144.0f) + base_term - 8 * usum[cc * 16 + k];
+    const int cblk = slot_block(g, cc >> 3);
     const bool upper = !stacked && cblk > task.rb;
+    int vre[4], vim[4];
+    int off[4];  // element offset of the pair within the channel, -1: not stored
 #pragma unroll
-    for (int m = 0; m < 16; ++m) {
-      const int x = __shfl_xor_sync(0xFFFFFFFFu, gv[2 * m + 1], 1);
-      int v = plane ? gv[2 * m] - x : gv[2 * m] + x;
-      const int q = (cc & 3) * 32 + 2 * m;  // column within its block
-      long long b;
+    for (int u = 0; u < 4; ++u) {  // columns 2u (lane of row 2i) and 2u + 1 (row 2i + 1)
+      const int x0 = plane ? gv[4 * u + 2] : gv[4 * u];
+      const int x1 = plane ? gv[4 * u + 3] : gv[4 * u + 1];
+      const int y0 = __shfl_xor_sync(0xFFFFFFFFu, plane ? gv[4 * u] : gv[4 * u + 2], 1);
+      const int y1 = __shfl_xor_sync(0xFFFFFFFFu, plane ? gv[4 * u + 1] : gv[4 * u + 3], 1);
+      // G[2i][2j] + G[2i+1][2j+1] and G[2i+1][2j] - G[2i][2j+1] for this lane's column j
+      vre[u] = plane ? y0 + x1 : x0 + y1;
+      vim[u] = plane ? x0 - y1 : y0 - x1;
+      const int q = (cc & 7) * 16 + 2 * (2 * u + plane);  // real column of input j in its block
+      int b;
       bool ok;
       if (stacked) {
         const int rpc = a.rows_per_chan;
         const int j = (q % rpc) >> 1;
         ok = row_ok && task.chan0 + q / rpc == ch && j <= i;
-        b = (long long)i * (i + 1) / 2 + j;
+        b = tri_i + j;
       } else {
         const int j = (128 * cblk + q) >> 1;
         if (upper) {
-          // block (c, rb) transposed: baseline (j, i) with j > i
-          ok = row_ok && j < n;
-          b = (long long)j * (j + 1) / 2 + i;
-          if (plane) v = -v;
+          ok = row_ok && j < n;  // baseline (j, i), j > i: the conjugate
+          b = j * (j + 1) / 2 + i;
+          vim[u] = -vim[u];
         } else {
           ok = row_ok && j <= i;
-          b = (long long)i * (i + 1) / 2 + j;
+          b = tri_i + j;
         }
       }
-      if (ok) {
-        int64_t* d = chp + 2 * b + plane;
-        if (a.accumulate)
-          *d += v;
-        else
-          *d = v;
+      off[u] = ok ? 2 * b : -1;
+    }
+    if (a.accumulate) {
+#pragma unroll
+      for (int h = 0; h < 4; h += 2) {  // two read-modify-writes in flight
+        long long ore[2], oim[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          ore[u] = oim[u] = 0;
+          if (off[h + u] >= 0) ld_s64x2(chp + off[h + u], ore[u], oim[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+          if (off[h + u] >= 0) st_s64x2(chp + off[h + u], ore[u] + vre[h + u], oim[u] + vim[h + u]);
       }
+    } else {
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (off[u] >= 0) st_s64x2(chp + off[u], vre[u], vim[u]);
     }
   }
 }
@@ -281,168 +304,305 @@ __device__ __forceinline__ void ctrl_init_common(Ctrl& sm, int tid) {
   for (int i = tid; i < kMaxBlocks * 128; i += blockDim.x) sm.usum[i] = 0;
 }
 
-// -------------------------------------------------------------- TMA kernel
-// Warps 0..15: four unpack groups of four warps (then the epilogue); warp
-// 16 issues MMAs; warp 17 issues TMA loads.
-constexpr int kGroups = 4;
-constexpr int kGroupWarps = 4;
+// ------------------------------------------------------------- ring kernel
+// Persistent: one CTA per SM walks the tasks blockIdx.x, blockIdx.x + grid,
+// ...; stage S counts the 128-spectrum stages of all its tasks in order.
+// Shared memory is one ring of slots of max_nblk operand blocks.  Stage S
+// uses slot S mod ns:
+//   warp 17 (TMA)     waits until the MMAs of stage S - ns have finished with
+//                     the slot, then loads the packed bytes of stage S into
+//                     its upper half (packed block b at nblk + b eighths);
+//   group S mod 4     (warps 4g .. 4g + 3) waits for the same MMA completion
+//                     and for the bytes, reads all of them into registers,
+//                     meets at a group barrier, and writes the swizzled
+//                     operands over them, in place;
+//   warp 16 (MMA)     issues the four K = 32 MMAs of the stage into one of two
+//                     256-column tensor-memory accumulators (tasks alternate)
+//                     and commits the slot back;
+//   warps 20..27      (drain) convert the accumulators of task j while task
+//                     j + 1 is being multiplied (warps 18, 19 only complete
+//                     the warpgroup of warps 16, 17).
+// The unpack warpgroups take registers from the others (setmaxnreg): the
+// unpack loop holds a whole stage in registers across the group barrier.
+// Every wait on a slot barrier for phase m is preceded by a completed wait
+// for phase m - 1 of a barrier whose completion implies it (the MMAs run in
+// order), so the parity of a phase two behind can never be mistaken for the
+// awaited one, whatever ns >= 4 is.
+#ifndef XE_EPI_WARPS
+#define XE_EPI_WARPS 8
+#endif
+#ifndef XE_GROUPS
+#define XE_GROUPS 4
+#endif
+constexpr int kGroups = XE_GROUPS;            // unpack groups (stages S = g mod kGroups)
+constexpr int kGroupWarps = 16 / kGroups;
 constexpr int kGroupThreads = kGroupWarps * 32;
 constexpr int kUnpackWarps = kGroups * kGroupWarps;
-constexpr int kTmaThreads = kUnpackWarps * 32 + 64;
-constexpr int kTmaItems = kMaxBlocks * 512 / kGroupThreads;  // per thread per stage
+constexpr int kItems = kMaxBlocks * 512 / kGroupThreads;  // 16-byte items per thread per stage
+constexpr int kPairsPerItem = kGroupThreads / 8;           // inputs covered per item index
+constexpr int kMmaWarp = kUnpackWarps, kTmaWarp = kUnpackWarps + 1, kEpiWarp0 = kUnpackWarps + 4;
+constexpr int kEpiWarps = XE_EPI_WARPS;
+constexpr int kRingThreads = (kEpiWarp0 + kEpiWarps) * 32;
+// registers per thread: launch share, unpack warpgroups, the other warpgroups
+constexpr int kRegsLaunch = (65536 / kRingThreads) & ~7;
+constexpr int kRegsUnpack = 88, kRegsOther = 48;
+static_assert(kRingThreads % 128 == 0, "whole warpgroups");
+static_assert(kUnpackWarps * 32 * kRegsUnpack + (kRingThreads - kUnpackWarps * 32) * kRegsOther <=
+                  kRingThreads * kRegsLaunch,
+              "the register split must fit in the launch allocation");
+constexpr int kMaxSlots = 16;
+static_assert(kEpiWarps % 4 == 0, "drain warps cover the four tensor-memory lane quarters");
+
+struct RingCtrl {
+  uint64_t full_t[kMaxSlots];    // packed bytes of the slot landed (TMA transaction count)
+  uint64_t full_o[kMaxSlots];    // operands of the slot written (one arrival per group warp)
+  uint64_t empty[kMaxSlots];     // MMAs of the slot finished (tcgen05.commit)
+  uint64_t tmem_full[2];         // accumulator buffer complete
+  uint64_t tmem_empty[2];        // accumulator buffer drained
+  uint64_t usum_full[2];         // row sums of the task published
+  uint64_t usum_empty[2];        // row sums consumed and cleared
+  uint64_t done;                 // every MMA finished (before freeing tensor memory)
+  uint32_t tmem_base;
+  int abort;
+  int32_t usum[2][kMaxBlocks * 128];
+};
+
+__device__ __forceinline__ HerkTask my_task(const HerkArgs& a, int j) {
+  return a.tasks[blockIdx.x + j * gridDim.x];
+}
 
 template <bool LO_IS_REAL>
-__global__ void __launch_bounds__(kTmaThreads, 1)
-    herk4_tma_kernel(const __grid_constant__ CUtensorMap tmap, const HerkArgs a) {
+__global__ void __launch_bounds__(kRingThreads, 1)
+    herk4_ring_kernel(const __grid_constant__ CUtensorMap tmap, const HerkArgs a) {
   extern __shared__ uint8_t dyn_raw[];
-  __shared__ Ctrl sm;
-  uint8_t* ops = align1024(dyn_raw);
-  const HerkTask task = a.tasks[blockIdx.x];
-  const TaskGeom g = task_geom(task);
+  // control block at the end of dynamic shared memory, ring from the first
+  // 1024-byte boundary (swizzle atoms) up to it
+  RingCtrl& sm = *reinterpret_cast<RingCtrl*>(
+      dyn_raw + ((a.smem_bytes - (int)sizeof(RingCtrl)) & ~15));
+  uint8_t* ring = align1024(dyn_raw);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const bool stacked = a.rows_per_chan > 0;
-  const int op_stage = g.nblk * kOpBlockBytes, pk_stage = g.nblk * kPkBlockBytes;
-  // Ring depths are multiples of the number of unpack groups, so that stage
-  // k always lands in a slot that only group k % kGroups fills: a group then
-  // waits on a slot whose previous fill was its own, and an mbarrier can
-  // never be more than one phase away from the phase awaited (a parity wait
-  // on an older phase would pass falsely).
-  const int avail = a.smem_bytes - 1024;
-  int no = kGroups * ((avail - kGroups * pk_stage) / (kGroups * op_stage));
-  if (no > kMaxStages) no = kMaxStages;
-  int np = kGroups * ((avail - no * op_stage) / (kGroups * pk_stage));
-  if (np > kMaxStages) np = kMaxStages;
-  uint8_t* pk = ops + no * op_stage;
+  const int n_my = (a.n_tasks - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
   const int nk = (a.tn + kStageT - 1) / kStageT;
+  const int total = n_my * nk;
+  const int slot_bytes = a.max_nblk * kOpBlockBytes;
+  int ns = (int)(reinterpret_cast<uint8_t*>(&sm) - ring) / slot_bytes;
+  if (ns > kMaxSlots) ns = kMaxSlots;
+  if (ns < kGroups) {  // the host sizes shared memory for at least four slots
+    if (tid == 0) atomicOr(a.status, kStTimeout);
+    return;
+  }
   volatile int* abort = &sm.abort;
 
-  ctrl_init_common(sm, tid);
   if (tid == 0) {
-    for (int s = 0; s < np; ++s) {
-      mbar_init(&sm.full_p[s], 1);
-      mbar_init(&sm.empty_p[s], kGroupWarps);
-    }
-    for (int s = 0; s < no; ++s) {
+    for (int s = 0; s < ns; ++s) {
+      mbar_init(&sm.full_t[s], 1);
       mbar_init(&sm.full_o[s], kGroupWarps);
-      mbar_init(&sm.empty_o[s], 1);
+      mbar_init(&sm.empty[s], 1);
     }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&sm.tmem_full[b], 1);
+      mbar_init(&sm.tmem_empty[b], kEpiWarps);
+      mbar_init(&sm.usum_full[b], kUnpackWarps);
+      mbar_init(&sm.usum_empty[b], kEpiWarps);
+    }
+    mbar_init(&sm.done, 1);
+    sm.abort = 0;
   }
-  if (warp == 0) tmem_alloc(&sm.tmem_base, g.ncols);
+  for (int i = tid; i < 2 * kMaxBlocks * 128; i += blockDim.x) (&sm.usum[0][0])[i] = 0;
+  if (warp == 0) tmem_alloc(&sm.tmem_base, 512);
   fence_mbar_init();
   tc_before_sync();
   __syncthreads();
   tc_after_sync();
   const uint32_t tmem = sm.tmem_base;
-
-  if (warp == kUnpackWarps + 1) {
+  const uint32_t ring_addr = smem_addr(ring);
+  // Each role branch resizes its registers first: a setmaxnreg whose branches
+  // joined again would leave the compiler the smaller budget for all roles.
+  if (warp == kTmaWarp) {
     // ------------------------------------------------------------ TMA loader
+    regs_shrink<kRegsOther>();
     if (lane == 0) {
       tma_prefetch_desc(&tmap);
-      const uint32_t pk_addr = smem_addr(pk);
-      int s = 0;
-      uint32_t ph = 0;
-      for (int k = 0; k < nk; ++k) {
-        if (k >= np && !mbar_wait(&sm.empty_p[s], ph ^ 1u, abort)) {
+      int s = 0, m = 0, j = 0, k = 0, issued = 0;
+      HerkTask task = my_task(a, 0);
+      TaskGeom g = task_geom(task);
+      for (int S = 0; S < total; ++S, ++k) {
+        if (k == nk) {  // next task
+          k = 0;
+          task = my_task(a, ++j);
+          g = task_geom(task);
+        }
+        if (m > 0 && !mbar_wait(&sm.empty[s], (uint32_t)((m - 1) & 1), abort)) {
           raise_timeout(a.status, abort);
           break;
         }
-        mbar_expect_tx(&sm.full_p[s], (uint32_t)pk_stage);
         const int t = a.t0 + k * kStageT;
-        for (int slot = 0; slot < g.nblk; ++slot) {
-          const uint32_t dst = pk_addr + (uint32_t)(s * pk_stage + slot * kPkBlockBytes);
+        const uint32_t dst0 = ring_addr + (uint32_t)(s * slot_bytes + g.nblk * kPkBlockBytes);
+        mbar_expect_tx(&sm.full_t[s], (uint32_t)(g.nblk * kPkBlockBytes));
+        for (int b = 0; b < g.nblk; ++b) {
+          const uint32_t dst = dst0 + (uint32_t)(b * kPkBlockBytes);
           if (stacked)
-            tma_load_3d(dst, &tmap, t, 0, task.chan0, &sm.full_p[s]);
+            tma_load_3d(dst, &tmap, t, 0, task.chan0, &sm.full_t[s]);
           else
-            tma_load_3d(dst, &tmap, t, 64 * slot_block(g, slot), task.chan0, &sm.full_p[s]);
+            tma_load_3d(dst, &tmap, t, 64 * slot_block(g, b), task.chan0, &sm.full_t[s]);
         }
-        if (++s == np) {
+        ++issued;
+        if (++s == ns) {
           s = 0;
-          ph ^= 1u;
+          ++m;
         }
       }
+      // never leave with copies in flight: wait for the last loads to land
+      int never = 0;
+      for (int S = issued - 1; S >= 0 && S >= issued - ns; --S)
+        mbar_wait(&sm.full_t[S % ns], (uint32_t)((S / ns) & 1), &never);
     }
     __syncwarp();
-  } else if (warp == kUnpackWarps) {
+  } else if (warp == kMmaWarp) {
     // ------------------------------------------------------------ MMA issuer
-    if (lane == 0)
-      mma_loop(g, nk, no, smem_addr(ops), (uint32_t)op_stage, tmem, sm.full_o, sm.empty_o,
-               &sm.done, a.status, abort);
-    __syncwarp();
-  } else {
-    // ------------------------------------------------------------ unpackers
-    const int grp = warp / kGroupWarps;
-    const int gt = tid - grp * kGroupThreads;  // thread within the group
-    const int chunk = gt & 7;
-    const int nit = g.nblk * 512 / kGroupThreads;
-    int32_t sre[kTmaItems], sim[kTmaItems];
+    regs_shrink<kRegsOther>();
+    if (lane == 0) {
+      int s = 0, m = 0;
+      bool ok = true;
+      for (int j = 0; j < n_my && ok; ++j) {
+        const int b = j & 1;
+        const TaskGeom g = task_geom(my_task(a, j));
+        const uint32_t idesc = umma_idesc(0, 128, 128 * g.nb);
+        if (j >= 2 && !mbar_wait(&sm.tmem_empty[b], (uint32_t)(((j >> 1) - 1) & 1), abort)) {
+          raise_timeout(a.status, abort);
+          break;
+        }
+        tc_after_sync();
+        const uint32_t d = tmem + (uint32_t)(b * 256);
+        for (int k = 0; k < nk; ++k) {
+          if (!mbar_wait(&sm.full_o[s], (uint32_t)(m & 1), abort)) {
+            raise_timeout(a.status, abort);
+            ok = false;
+            break;
+          }
+          tc_after_sync();
+          const uint32_t st = ring_addr + (uint32_t)(s * slot_bytes);
+          const uint64_t adesc = umma_desc_sw128(st + (uint32_t)(g.a_slot * kOpBlockBytes));
+          const uint64_t bdesc = umma_desc_sw128(st);
 #pragma unroll
-    for (int it = 0; it < kTmaItems; ++it) sre[it] = sim[it] = 0;
-    const uint32_t ones[4] = {~0u, ~0u, ~0u, ~0u};
-    // this group's stages are k = grp, grp + kGroups, ...
-    int sp = grp % np, so = grp % no;
-    uint32_t php = (uint32_t)((grp / np) & 1), pho = (uint32_t)((grp / no) & 1);
-    for (int k = grp; k < nk; k += kGroups) {
-      if (!mbar_wait(&sm.full_p[sp], php, abort) ||
-          (k >= no && !mbar_wait(&sm.empty_o[so], pho ^ 1u, abort))) {
-        raise_timeout(a.status, abort);
-        break;
+          for (int kk = 0; kk < 4; ++kk)
+            umma_f8(d, adesc + 2 * kk, bdesc + 2 * kk, idesc, (k | kk) != 0);
+          umma_commit(&sm.empty[s]);
+          if (++s == ns) {
+            s = 0;
+            ++m;
+          }
+        }
+        if (ok) umma_commit(&sm.tmem_full[b]);
       }
-      const uint8_t* src = pk + sp * pk_stage + chunk * 16;
-      uint8_t* dst = ops + so * op_stage;
-      const bool tail = (k + 1) * kStageT > a.tn;
-      uint32_t keep[4] = {~0u, ~0u, ~0u, ~0u};
-      if (tail) time_keep(k * kStageT + chunk * 16, a.tn, keep);
-      // all shared-memory loads of the stage first, then hand the packed
-      // stage back to the loader so that it refills while this group unpacks
-      uint4 v[kTmaItems];
+      umma_commit(&sm.done);
+      int never = 0;
+      if (!mbar_wait(&sm.done, 0, &never)) raise_timeout(a.status, abort);
+    }
+    __syncwarp();
+  } else if (warp < kUnpackWarps) {
+    // ------------------------------------------------------------ unpackers
+    regs_grow<kRegsUnpack>();
+    const int grp = warp / kGroupWarps;
+    const int gt = tid - grp * kGroupThreads;
+    const int chunk = gt & 7, g8 = gt >> 3;
+    const uint32_t src0 = ring_addr + (uint32_t)(128 * g8 + 16 * chunk);
+    const int rre = (2 * g8) & 7, rim = (2 * g8 + 1) & 7;
+    const uint32_t dst_re = ring_addr + (uint32_t)((g8 >> 2) * 1024 + rre * 128 + ((chunk ^ rre) << 4));
+    const uint32_t dst_im = ring_addr + (uint32_t)((g8 >> 2) * 1024 + rim * 128 + ((chunk ^ rim) << 4));
+    bool ok = true;
+    // next stage of this group, its slot s = S mod ns and use m = S / ns,
+    // advanced by additions (kGroups <= ns)
+    int S = grp, s = grp, m = 0;
+    for (int j = 0; j < n_my && ok; ++j) {
+      const int b = j & 1;
+      const TaskGeom g = task_geom(my_task(a, j));
+      const int nit = g.nblk * 512 / kGroupThreads;
+      int32_t sre[kItems], sim[kItems];
 #pragma unroll
-      for (int it = 0; it < kTmaItems; ++it)
-        if (it < nit)
-          v[it] = *reinterpret_cast<const uint4*>(
-              src + (it * (kGroupThreads / 8) + (gt >> 3)) * kStageT);
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&sm.empty_p[sp]);
+      for (int it = 0; it < kItems; ++it) sre[it] = sim[it] = 0;
+      // this group's stages of task j: S = j nk + k with S = grp (mod kGroups)
+      for (; S < (j + 1) * nk; S += kGroups) {
+        const int k = S - j * nk;
+        bool got = (m == 0 || mbar_wait(&sm.empty[s], (uint32_t)((m - 1) & 1), abort)) &&
+                   mbar_wait(&sm.full_t[s], (uint32_t)(m & 1), abort);
+        if (!got) raise_timeout(a.status, abort);
+        const uint32_t so = (uint32_t)(s * slot_bytes);
+        const uint32_t src = src0 + so + (uint32_t)(g.nblk * kPkBlockBytes);
+        const bool tail = (k + 1) * kStageT > a.tn;
+        uint32_t keep[4] = {~0u, ~0u, ~0u, ~0u};
+        if (tail) time_keep(k * kStageT + chunk * 16, a.tn, keep);
+        uint4 v[kItems];
 #pragma unroll
-      for (int it = 0; it < kTmaItems; ++it) {
-        if (it < nit) {
-          const int pair = it * (kGroupThreads / 8) + (gt >> 3);
-          const uint32_t w[4] = {v[it].x, v[it].y, v[it].z, v[it].w};
-          uint32_t re[4], im[4];
-          if (tail)
+        for (int it = 0; it < kItems; ++it)
+          if (it < nit && got) v[it] = lds128(src + (uint32_t)(128 * kPairsPerItem * it));
+        // every packed byte of the stage is in registers before any is
+        // overwritten; the group leaves together if any of its waits failed
+        if (!named_bar_and(2 + grp, kGroupThreads, got)) {
+          ok = false;
+          break;
+        }
+#pragma unroll
+        for (int it = 0; it < kItems; ++it) {
+          if (it < nit) {
+            const uint32_t w[4] = {v[it].x, v[it].y, v[it].z, v[it].w};
+            uint32_t re[4], im[4];
+            // always masked (all ones before the last stage): no branch inside the unrolled loop
             unpack16<LO_IS_REAL, true>(w, keep, re, im, sre[it], sim[it]);
-          else
-            unpack16<LO_IS_REAL, false>(w, ones, re, im, sre[it], sim[it]);
-          store_pair(dst, pair, chunk, re, im);
+            const uint32_t o = so + (uint32_t)(256 * kPairsPerItem * it);
+            sts128(dst_re + o, re[0], re[1], re[2], re[3]);
+            sts128(dst_im + o, im[0], im[1], im[2], im[3]);
+          }
+        }
+        fence_smem_to_async();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&sm.full_o[s]);
+        s += kGroups;
+        if (s >= ns) {
+          s -= ns;
+          ++m;
         }
       }
-      // one arrival per warp: every lane makes its stores visible to the
-      // tensor core (async proxy), then the warp synchronises
-      fence_smem_to_async();
+      if (!ok) break;
+      // publish this task's row sums once the buffer is free again
+      const bool freed = j < 2 || mbar_wait(&sm.usum_empty[b], (uint32_t)(((j >> 1) - 1) & 1), abort);
+      if (!freed) raise_timeout(a.status, abort);
+      if (!named_bar_and(2 + grp, kGroupThreads, freed)) break;
+      publish_row_sums<kGroupThreads>(sre, sim, nit, gt, sm.usum[b]);
       __syncwarp();
-      if (lane == 0) mbar_arrive(&sm.full_o[so]);
-      sp += kGroups;
-      while (sp >= np) {
-        sp -= np;
-        php ^= 1u;
-      }
-      so += kGroups;
-      while (so >= no) {
-        so -= no;
-        pho ^= 1u;
-      }
+      if (lane == 0) mbar_arrive(&sm.usum_full[b]);
     }
-    publish_row_sums<kGroupThreads>(sre, sim, nit, gt, sm.usum);
-    named_bar_sync(1, kUnpackWarps * 32);
-    int never = 0;
-    bool good = mbar_wait(&sm.done, 0, &never);
-    good = __all_sync(0xFFFFFFFFu, good);
-    if (!good && lane == 0) raise_timeout(a.status, abort);
-    tc_after_sync();
-    if (good && !*abort) epilogue<kUnpackWarps>(a, task, g, sm.usum, tmem, tid);
+  } else if (warp < kEpiWarp0) {
+    regs_shrink<kRegsOther>();  // the two idle warps of the MMA / TMA warpgroup
+  } else {
+    // ------------------------------------------------------------ drain
+    regs_shrink<kRegsOther>();
+    const int quad = warp & 3, part = (warp - kEpiWarp0) >> 2;
+    for (int j = 0; j < n_my; ++j) {
+      const int b = j & 1;
+      const uint32_t par = (uint32_t)((j >> 1) & 1);
+      const bool got = mbar_wait(&sm.tmem_full[b], par, abort) && mbar_wait(&sm.usum_full[b], par, abort);
+      if (!got) raise_timeout(a.status, abort);
+      if (!named_bar_and(1, kEpiWarps * 32, got)) break;  // the drain warps leave together
+      tc_after_sync();
+      const HerkTask task = my_task(a, j);
+      epilogue(a, task, task_geom(task), sm.usum[b], tmem + (uint32_t)(b * 256), quad, part,
+               kEpiWarps / 4, lane);
+      tc_before_sync();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&sm.tmem_empty[b]);
+      // every drain warp has read the sums: clear them for task j + 2
+      named_bar_sync(1, kEpiWarps * 32);
+      for (int i = tid - kEpiWarp0 * 32; i < kMaxBlocks * 128; i += kEpiWarps * 32)
+        sm.usum[b][i] = 0;
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&sm.usum_empty[b]);
+    }
   }
   tc_before_sync();
   __syncthreads();
-  if (warp == 0) tmem_free(tmem, g.ncols);
+  if (warp == 0) tmem_free(tmem, 512);
 }
 
 // -------------------------------------------------------------- LDG kernel
@@ -565,7 +725,7 @@ __global__ void __launch_bounds__(kLdgThreads, 1) herk4_ldg_kernel(const HerkArg
     good = __all_sync(0xFFFFFFFFu, good);
     if (!good && lane == 0) raise_timeout(a.status, abort);
     tc_after_sync();
-    if (good && !*abort) epilogue<4>(a, task, g, sm.usum, tmem, tid);
+    if (good && !*abort) epilogue(a, task, g, sm.usum, tmem, warp & 3, 0, 1, lane);
   }
   tc_before_sync();
   __syncthreads();
@@ -586,28 +746,44 @@ cudaError_t set_smem(K kernel, int bytes) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
-}  // namespace
-
-int herk4_max_smem() {
-  int m = max_dyn_smem((const void*)herk4_tma_kernel<false>);
-  m = std::min(m, max_dyn_smem((const void*)herk4_tma_kernel<true>));
-  m = std::min(m, max_dyn_smem((const void*)herk4_ldg_kernel<false>));
-  m = std::min(m, max_dyn_smem((const void*)herk4_ldg_kernel<true>));
+int ring_smem() {
+  static int m = -1;
+  if (m < 0)
+    m = std::min(max_dyn_smem((const void*)herk4_ring_kernel<false>),
+                 max_dyn_smem((const void*)herk4_ring_kernel<true>));
   return m;
 }
 
-cudaError_t herk4_launch(const HerkArgs& a, const CUtensorMap* tmap, int n_tasks,
+}  // namespace
+
+int herk4_max_smem() {
+  int m = max_dyn_smem((const void*)herk4_ldg_kernel<false>);
+  m = std::min(m, max_dyn_smem((const void*)herk4_ldg_kernel<true>));
+  return std::min(m, ring_smem());
+}
+
+cudaError_t herk4_launch(const HerkArgs& args, const CUtensorMap* tmap, int n_tasks,
                          cudaStream_t s) {
   cudaError_t e;
   if (tmap) {
+    HerkArgs a = args;
+    a.smem_bytes = ring_smem();
+    // four slots of the largest stage, the control block and the alignment pad
+    if (a.smem_bytes < kGroups * a.max_nblk * kOpBlockBytes + (int)sizeof(RingCtrl) + 1024)
+      return cudaErrorInvalidConfiguration;
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = std::min(n_tasks, nsm);
     if (a.lo_is_real) {
-      if ((e = set_smem(herk4_tma_kernel<true>, a.smem_bytes)) != cudaSuccess) return e;
-      herk4_tma_kernel<true><<<n_tasks, kTmaThreads, a.smem_bytes, s>>>(*tmap, a);
+      if ((e = set_smem(herk4_ring_kernel<true>, a.smem_bytes)) != cudaSuccess) return e;
+      herk4_ring_kernel<true><<<grid, kRingThreads, a.smem_bytes, s>>>(*tmap, a);
     } else {
-      if ((e = set_smem(herk4_tma_kernel<false>, a.smem_bytes)) != cudaSuccess) return e;
-      herk4_tma_kernel<false><<<n_tasks, kTmaThreads, a.smem_bytes, s>>>(*tmap, a);
+      if ((e = set_smem(herk4_ring_kernel<false>, a.smem_bytes)) != cudaSuccess) return e;
+      herk4_ring_kernel<false><<<grid, kRingThreads, a.smem_bytes, s>>>(*tmap, a);
     }
   } else {
+    const HerkArgs& a = args;
     if (a.lo_is_real) {
       if ((e = set_smem(herk4_ldg_kernel<true>, a.smem_bytes)) != cudaSuccess) return e;
       herk4_ldg_kernel<true><<<n_tasks, kLdgThreads, a.smem_bytes, s>>>(a);

@@ -44,6 +44,8 @@ struct HerkArgs {
   int lo_is_real;            // 4-bit: real part in the low nibble
   int vec_ok;                // 16-byte loads are aligned everywhere
   int smem_bytes;            // dynamic shared memory of the launch
+  int n_tasks;               // tasks in `tasks`
+  int max_nblk;              // largest number of resident 128-row blocks of any task
 };
 
 // Largest number of spectra integrated in one tensor-memory accumulation:

@@ -175,6 +175,8 @@ extern "C" int corr_correlate_noalloc(const void* block, int n_inputs, int n_cha
   a.rows_per_chan = rpc;
   a.lo_is_real = (flags & CORR_F_LO_IS_REAL) ? 1 : 0;
   a.smem_bytes = herk4_max_smem();
+  a.n_tasks = (int)n_tasks;
+  a.max_nblk = (rpc == 0 && nrb >= 2) ? 2 : 1;  // row blocks resident per task (see planner)
   CUtensorMap tmap;
   const bool aligned = stride % 16 == 0 && reinterpret_cast<uintptr_t>(src) % 16 == 0;
   const bool use_tma = aligned && make_sample_tmap(&tmap, src, T, stride, N, C,

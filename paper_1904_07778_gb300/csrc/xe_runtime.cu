@@ -59,6 +59,7 @@ struct corr_ctx {
   long long turned_stride = 0;  // bytes per (channel, input) row of `turned`
   HerkTask* tasks = nullptr;
   int n_tasks = 0;
+  int max_nblk = 1;
   int rows_per_chan = 0;
   int smem_bytes = 0;
   int* d_status = nullptr;
@@ -298,6 +299,11 @@ int corr_create(int n_inputs, int n_chans, int n_time, int bits, int layout, uns
     if (st != CORR_OK) break;
     std::vector<HerkTask> tasks = plan_tasks(n_inputs, n_chans, &x->rows_per_chan);
     x->n_tasks = (int)tasks.size();
+    for (const HerkTask& t : tasks) {
+      const int nb = t.cb[1] >= 0 ? 2 : 1;
+      const bool a_in = t.rb == t.cb[0] || (nb == 2 && t.rb == t.cb[1]);
+      x->max_nblk = std::max(x->max_nblk, a_in ? nb : nb + 1);
+    }
     if (cudaMalloc(&x->tasks, tasks.size() * sizeof(HerkTask)) != cudaSuccess) { st = CORR_ENOMEM; break; }
     if (cudaMemcpy(x->tasks, tasks.data(), tasks.size() * sizeof(HerkTask), cudaMemcpyHostToDevice) != cudaSuccess) { st = CORR_ECUDA; break; }
     x->smem_bytes = herk4_max_smem();
@@ -370,6 +376,8 @@ int corr_push(corr_ctx* x, const void* block, size_t nbytes, uint64_t seq) {
   a.rows_per_chan = x->rows_per_chan;
   a.lo_is_real = (x->flags & CORR_F_LO_IS_REAL) ? 1 : 0;
   a.smem_bytes = x->smem_bytes;
+  a.n_tasks = x->n_tasks;
+  a.max_nblk = x->max_nblk;
   // The TMA kernel needs 16-byte aligned rows; otherwise plain loads.
   CUtensorMap tmap;
   const bool aligned = row_stride % 16 == 0 && reinterpret_cast<uintptr_t>(src) % 16 == 0;
