@@ -82,7 +82,11 @@ typedef struct corr_ctx corr_ctx; /* opaque, owned by the library */
  *   bits     : 4 -> one byte per complex sample, two 4-bit two's-complement
  *              numbers (the equaliser output of Sec. 2.1, values -7..7; code
  *              0x8 decodes to -8);  8 -> two int8 bytes (re, im) per sample,
- *              symmetric range -127..127 (-128 is rejected, CORR_ERANGE).
+ *              symmetric range -127..127.  A -128 is still integrated
+ *              exactly, and the next corr_sync / corr_dump / corr_normalise
+ *              returns CORR_ERANGE (once; the flag is then cleared).  In the
+ *              layouts an 8-bit sample is the byte pair (re, im) in place of
+ *              the 4-bit byte.  CORR_F_LO_IS_REAL is invalid with 8 bits.
  *   layout   : CORR_L_TCI, CORR_L_TIC or CORR_L_CIT.
  *   flags    : CORR_F_* bits.
  *   stream   : cudaStream_t to run on, or NULL for a private stream.

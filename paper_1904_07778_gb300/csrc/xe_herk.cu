@@ -82,13 +82,14 @@ __device__ __forceinline__ uint32_t swz_offset(int row, int chunk) {
 // Unpack 16 packed samples (4 words) into 16 real and 16 imaginary offset
 // codes and add them to the row sums; with MASK, `keep` zeroes samples
 // outside the time range.
-template <bool LO_IS_REAL, bool MASK>
+template <bool LO_IS_REAL, bool MASK, bool LO_UNSIGNED = false>
 __device__ __forceinline__ void unpack16(const uint32_t (&w)[4], const uint32_t (&keep)[4],
                                          uint32_t (&re)[4], uint32_t (&im)[4], int32_t& sre,
                                          int32_t& sim) {
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    uint32_t lo = (w[q] & 0x0F0F0F0Fu) ^ 0x08080808u;
+    // 8-bit low nibbles are unsigned (0..15): their code is the nibble itself
+    uint32_t lo = (w[q] & 0x0F0F0F0Fu) ^ (LO_UNSIGNED ? 0u : 0x08080808u);
     uint32_t hi = ((w[q] >> 4) & 0x0F0F0F0Fu) ^ 0x08080808u;
     if (MASK) {
       lo &= keep[q];
@@ -280,6 +281,111 @@ __device__ __forceinline__ void epilogue(const HerkArgs& a, const HerkTask& task
   }
 }
 
+// 8-bit drain.  Rows 4i + t of Y hold, for t = 0 .. 3, the signed high nibble
+// of Re x_i, its unsigned low nibble, and the same two for Im x_i (x = 16 h +
+// l).  High-nibble rows carry offset codes (offset 8), low-nibble rows plain
+// codes (offset 0), so G[p][q] = 2^18 Gu - o_q U_p - o_p U_q + o_p o_q T.  Each
+// visibility folds a 4 x 4 block of G with weights 16 (h) and 1 (l):
+//   Re V_ij = sum_{a,b} w_a w_b (G[Re_a i][Re_b j] + G[Im_a i][Im_b j])
+//   Im V_ij = sum_{a,b} w_a w_b (G[Im_a i][Re_b j] - G[Re_a i][Im_b j]).
+// A lane forms its row's share for the four inputs j of a 16-column chunk;
+// the four lanes of input i reduce-scatter them (six shuffles) so that lane
+// t ends with the visibility of the chunk's t-th input.
+__device__ __forceinline__ void epilogue8(const HerkArgs& a, const HerkTask& task, const TaskGeom& g,
+                                          const int32_t* usum, uint32_t tmem, int quad, int part,
+                                          int nparts, int lane) {
+  const bool stacked = a.rows_per_chan > 0;
+  const int p = quad * 32 + lane;
+  const int n = a.n_inputs;
+  int ch, i, ra;
+  bool row_ok;
+  if (stacked) {
+    const int rpc = a.rows_per_chan;
+    ch = task.chan0 + p / rpc;
+    const int rr = p % rpc;
+    i = rr >> 2;
+    ra = rr & 3;
+    row_ok = i < n && ch < a.n_chans;
+  } else {
+    ch = task.chan0;
+    const int prow = task.rb * 128 + p;
+    i = prow >> 2;
+    ra = prow & 3;
+    row_ok = i < n;
+  }
+  const int op = (ra & 1) ? 0 : 8;      // offset of this row's codes
+  const int wa = (ra & 1) ? 1 : 16;     // weight of this row's nibble
+  const bool im_row = ra >= 2;
+  const int up = usum[g.a_slot * 128 + p];
+  const int t8 = 8 * a.tn;
+  const long long nbl = (long long)n * (n + 1) / 2;
+  int64_t* chp = a.acc + (long long)(row_ok ? ch : 0) * nbl * 2;
+  const int tri_i = i * (i + 1) / 2;
+  const int sel = lane & 3, bit1 = (lane >> 1) & 1, bit0 = lane & 1;
+  const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16);
+  const int nch = g.nb * 8, per = nch / nparts;  // 16-column chunks = 4 inputs each
+  for (int cc = part * per; cc < (part + 1) * per; ++cc) {
+    uint32_t r[16];
+    tmem_load16(trow + (uint32_t)(cc * 16), r);
+    int pre[4], pim[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      int gq[4];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int k = 4 * u + b;
+        const int oq = (b & 1) ? 0 : 8;
+        gq[b] = __float2int_rn(__uint_as_float(r[k]) * 262144.0f) - oq * up -
+                op * usum[cc * 16 + k] + oq * (op ? t8 : 0);
+      }
+      const int sre = 16 * gq[0] + gq[1], sim = 16 * gq[2] + gq[3];
+      pre[u] = wa * (im_row ? sim : sre);
+      pim[u] = wa * (im_row ? sre : -sim);
+    }
+    // reduce-scatter over the four lanes of input i: keep the half of the
+    // chunk's inputs named by bit 1 of the lane, then the one named by bit 0
+    int hre[2], him[2];
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const int sr = bit1 ? pre[t] : pre[2 + t], si = bit1 ? pim[t] : pim[2 + t];
+      hre[t] = (bit1 ? pre[2 + t] : pre[t]) + __shfl_xor_sync(0xFFFFFFFFu, sr, 2);
+      him[t] = (bit1 ? pim[2 + t] : pim[t]) + __shfl_xor_sync(0xFFFFFFFFu, si, 2);
+    }
+    int vre = (bit0 ? hre[1] : hre[0]) + __shfl_xor_sync(0xFFFFFFFFu, bit0 ? hre[0] : hre[1], 1);
+    int vim = (bit0 ? him[1] : him[0]) + __shfl_xor_sync(0xFFFFFFFFu, bit0 ? him[0] : him[1], 1);
+    const int q = (cc & 7) * 16 + 4 * sel;  // first column of this lane's input j in its block
+    int b;
+    bool ok;
+    if (stacked) {
+      const int rpc = a.rows_per_chan;
+      const int j = (q % rpc) >> 2;
+      ok = row_ok && task.chan0 + q / rpc == ch && j <= i;
+      b = tri_i + j;
+    } else {
+      const int cblk = slot_block(g, cc >> 3);
+      const int j = (128 * cblk + q) >> 2;
+      if (cblk > task.rb) {
+        ok = row_ok && j < n;  // baseline (j, i), j > i: the conjugate
+        b = j * (j + 1) / 2 + i;
+        vim = -vim;
+      } else {
+        ok = row_ok && j <= i;
+        b = tri_i + j;
+      }
+    }
+    if (ok) {
+      int64_t* d = chp + 2 * b;
+      if (a.accumulate) {
+        long long ore, oim;
+        ld_s64x2(d, ore, oim);
+        st_s64x2(d, ore + vre, oim + vim);
+      } else {
+        st_s64x2(d, vre, vim);
+      }
+    }
+  }
+}
+
 struct Ctrl {
   uint64_t full_p[kMaxStages];   // packed stage loaded (TMA transaction bytes)
   uint64_t empty_p[kMaxStages];  // packed stage consumed by the unpackers
@@ -371,7 +477,7 @@ __device__ __forceinline__ HerkTask my_task(const HerkArgs& a, int j) {
   return a.tasks[blockIdx.x + j * gridDim.x];
 }
 
-template <bool LO_IS_REAL>
+template <bool LO_IS_REAL, bool EIGHT>
 __global__ void __launch_bounds__(kRingThreads, 1)
     herk4_ring_kernel(const __grid_constant__ CUtensorMap tmap, const HerkArgs a) {
   extern __shared__ uint8_t dyn_raw[];
@@ -515,6 +621,7 @@ __global__ void __launch_bounds__(kRingThreads, 1)
     // next stage of this group, its slot s = S mod ns and use m = S / ns,
     // advanced by additions (kGroups <= ns)
     int S = grp, s = grp, m = 0;
+    uint32_t bad = 0;  // 8-bit: a byte equal to 0x80 (-128) was seen
     for (int j = 0; j < n_my && ok; ++j) {
       const int b = j & 1;
       const TaskGeom g = task_geom(my_task(a, j));
@@ -549,7 +656,14 @@ __global__ void __launch_bounds__(kRingThreads, 1)
             const uint32_t w[4] = {v[it].x, v[it].y, v[it].z, v[it].w};
             uint32_t re[4], im[4];
             // always masked (all ones before the last stage): no branch inside the unrolled loop
-            unpack16<LO_IS_REAL, true>(w, keep, re, im, sre[it], sim[it]);
+            unpack16<LO_IS_REAL, true, EIGHT>(w, keep, re, im, sre[it], sim[it]);
+            if (EIGHT) {
+#pragma unroll
+              for (int q = 0; q < 4; ++q) {  // any valid byte equal to 0x80?
+                const uint32_t z = (w[q] ^ 0x80808080u) | ~keep[q];
+                bad |= (z - 0x01010101u) & ~z & 0x80808080u;
+              }
+            }
             const uint32_t o = so + (uint32_t)(256 * kPairsPerItem * it);
             sts128(dst_re + o, re[0], re[1], re[2], re[3]);
             sts128(dst_im + o, im[0], im[1], im[2], im[3]);
@@ -573,6 +687,7 @@ __global__ void __launch_bounds__(kRingThreads, 1)
       __syncwarp();
       if (lane == 0) mbar_arrive(&sm.usum_full[b]);
     }
+    if (EIGHT && __any_sync(0xFFFFFFFFu, bad != 0) && lane == 0) atomicOr(a.status, kStRange);
   } else if (warp < kEpiWarp0) {
     regs_shrink<kRegsOther>();  // the two idle warps of the MMA / TMA warpgroup
   } else {
@@ -587,8 +702,12 @@ __global__ void __launch_bounds__(kRingThreads, 1)
       if (!named_bar_and(1, kEpiWarps * 32, got)) break;  // the drain warps leave together
       tc_after_sync();
       const HerkTask task = my_task(a, j);
-      epilogue(a, task, task_geom(task), sm.usum[b], tmem + (uint32_t)(b * 256), quad, part,
-               kEpiWarps / 4, lane);
+      if (EIGHT)
+        epilogue8(a, task, task_geom(task), sm.usum[b], tmem + (uint32_t)(b * 256), quad, part,
+                  kEpiWarps / 4, lane);
+      else
+        epilogue(a, task, task_geom(task), sm.usum[b], tmem + (uint32_t)(b * 256), quad, part,
+                 kEpiWarps / 4, lane);
       tc_before_sync();
       __syncwarp();
       if (lane == 0) mbar_arrive(&sm.tmem_empty[b]);
@@ -749,9 +868,18 @@ cudaError_t set_smem(K kernel, int bytes) {
 int ring_smem() {
   static int m = -1;
   if (m < 0)
-    m = std::min(max_dyn_smem((const void*)herk4_ring_kernel<false>),
-                 max_dyn_smem((const void*)herk4_ring_kernel<true>));
+    m = std::min(std::min(max_dyn_smem((const void*)herk4_ring_kernel<false, false>),
+                          max_dyn_smem((const void*)herk4_ring_kernel<true, false>)),
+                 max_dyn_smem((const void*)herk4_ring_kernel<false, true>));
   return m;
+}
+
+template <bool LO, bool EIGHT>
+cudaError_t ring_launch(const HerkArgs& a, const CUtensorMap* tmap, int grid, cudaStream_t s) {
+  cudaError_t e = set_smem(herk4_ring_kernel<LO, EIGHT>, a.smem_bytes);
+  if (e != cudaSuccess) return e;
+  herk4_ring_kernel<LO, EIGHT><<<grid, kRingThreads, a.smem_bytes, s>>>(*tmap, a);
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -775,15 +903,12 @@ cudaError_t herk4_launch(const HerkArgs& args, const CUtensorMap* tmap, int n_ta
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const int grid = std::min(n_tasks, nsm);
-    if (a.lo_is_real) {
-      if ((e = set_smem(herk4_ring_kernel<true>, a.smem_bytes)) != cudaSuccess) return e;
-      herk4_ring_kernel<true><<<grid, kRingThreads, a.smem_bytes, s>>>(*tmap, a);
-    } else {
-      if ((e = set_smem(herk4_ring_kernel<false>, a.smem_bytes)) != cudaSuccess) return e;
-      herk4_ring_kernel<false><<<grid, kRingThreads, a.smem_bytes, s>>>(*tmap, a);
-    }
+    if (a.bits == 8) return ring_launch<false, true>(a, tmap, grid, s);
+    return a.lo_is_real ? ring_launch<true, false>(a, tmap, grid, s)
+                        : ring_launch<false, false>(a, tmap, grid, s);
   } else {
     const HerkArgs& a = args;
+    if (a.bits != 4) return cudaErrorInvalidValue;  // 8-bit rows are always TMA-aligned
     if (a.lo_is_real) {
       if ((e = set_smem(herk4_ldg_kernel<true>, a.smem_bytes)) != cudaSuccess) return e;
       herk4_ldg_kernel<true><<<n_tasks, kLdgThreads, a.smem_bytes, s>>>(a);

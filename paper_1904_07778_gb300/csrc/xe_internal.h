@@ -24,6 +24,12 @@ enum : int {
 // triangle and is written transposed.  When 2N <= 64, several channels are
 // stacked in one 128-row block (rows_per_chan = 2N rounded up to a power of
 // two) and the task covers channels chan0 .. chan0 + 128 / rows_per_chan - 1.
+//
+// 8-bit samples use the same machinery on byte rows: the block is first laid
+// out as [channel][input][re/im byte][time], and every byte splits into a
+// signed high nibble h and an unsigned low nibble l (value 16 h + l), so an
+// input owns four rows of Y (Re h, Re l, Im h, Im l) and the blocks above
+// count 4N rows.
 struct HerkTask {
   int chan0;
   int rb;
@@ -46,12 +52,18 @@ struct HerkArgs {
   int smem_bytes;            // dynamic shared memory of the launch
   int n_tasks;               // tasks in `tasks`
   int max_nblk;              // largest number of resident 128-row blocks of any task
+  int bits;                  // 4, or 8 (byte rows: 2 per input, 4 rows of Y per input)
 };
 
 // Largest number of spectra integrated in one tensor-memory accumulation:
 // with 4-bit offset codes u <= 15 a partial sum is at most 225 per spectrum,
 // and FP32 holds every integer below 2^24 exactly (225 * 65536 < 2^24).
 constexpr int kMaxChunk4 = 65536;
+// 8-bit: the same FP32 bound holds per nibble product, and the drain folds
+// 16 products into int32 sums that stay below 2^31 for up to 32768 spectra
+// (|Re V| <= 2 * 127^2 * 32768 and every partial sum is smaller than that bound
+// times 1.3).
+constexpr int kMaxChunk8 = 32768;
 
 int herk4_max_smem();
 // tmap == nullptr selects the kernel that loads with plain global loads (any
@@ -67,8 +79,16 @@ bool make_sample_tmap(CUtensorMap* m, const uint8_t* x, int n_time, long long ro
 
 // Corner turn of byte samples: in[t][g][k] -> out[k][g][t], output rows of
 // out_stride >= T bytes (32-byte aligned rows take the fast path).
+// With pair_rows, k = 2 c + p counts (c, p) pairs and output row (k, g) goes
+// to row (c G + g) 2 + p instead of k G + g: 8-bit [t][i][c][re/im] becomes
+// [c][i][re/im][t].
 cudaError_t turn_launch(const uint8_t* in, uint8_t* out, int T, int G, int K, long long out_stride,
-                        cudaStream_t s);
+                        cudaStream_t s, bool pair_rows = false);
+
+// 8-bit samples already in [row][t][re/im] order (row = channel x input):
+// out[row][p][t] = in[row][t][p], output rows of out_stride bytes.
+cudaError_t split_planes_launch(const uint8_t* in, uint8_t* out, long long rows, int T,
+                                long long out_stride, cudaStream_t s);
 
 // FP64 correlation coefficients from int64 visibilities.
 cudaError_t normalise_launch(const int64_t* acc, double* rho, int n_inputs, int n_chans,

@@ -177,6 +177,7 @@ extern "C" int corr_correlate_noalloc(const void* block, int n_inputs, int n_cha
   a.smem_bytes = herk4_max_smem();
   a.n_tasks = (int)n_tasks;
   a.max_nblk = (rpc == 0 && nrb >= 2) ? 2 : 1;  // row blocks resident per task (see planner)
+  a.bits = 4;
   CUtensorMap tmap;
   const bool aligned = stride % 16 == 0 && reinterpret_cast<uintptr_t>(src) % 16 == 0;
   const bool use_tma = aligned && make_sample_tmap(&tmap, src, T, stride, N, C,

@@ -253,8 +253,9 @@ int corr_create(int n_inputs, int n_chans, int n_time, int bits, int layout, uns
                 void* stream, corr_ctx** out) {
   if (!out) return CORR_EINVAL;
   *out = nullptr;
-  if (n_inputs < 1 || n_inputs > 1024 || n_chans < 1 || n_time < 1 || bits != 4 ||
-      layout < CORR_L_TCI || layout > CORR_L_CIT || (flags & ~CORR_F_LO_IS_REAL))
+  if (n_inputs < 1 || n_inputs > 1024 || n_chans < 1 || n_time < 1 || (bits != 4 && bits != 8) ||
+      layout < CORR_L_TCI || layout > CORR_L_CIT || (flags & ~CORR_F_LO_IS_REAL) ||
+      (bits == 8 && (flags & CORR_F_LO_IS_REAL)))
     return CORR_EINVAL;
   const size_t block_bytes = (size_t)n_inputs * n_chans * n_time * (size_t)(bits / 4);
   if (block_bytes / (size_t)n_inputs / (size_t)n_chans != (size_t)n_time * (bits / 4))
@@ -284,8 +285,10 @@ int corr_create(int n_inputs, int n_chans, int n_time, int bits, int layout, uns
     x->acc_bytes = (size_t)corr_n_baselines(n_inputs) * n_chans * 2 * sizeof(int64_t);
     if (cudaMalloc(&x->acc, x->acc_bytes) != cudaSuccess) { st = CORR_ENOMEM; break; }
     x->turned_stride = ((long long)n_time + 31) / 32 * 32;  // 32-byte rows for the corner turn
-    if (layout != CORR_L_CIT &&
-        cudaMalloc(&x->turned, (size_t)x->turned_stride * n_inputs * n_chans) != cudaSuccess) { st = CORR_ENOMEM; break; }
+    // byte rows per channel: one per input (4-bit), re and im bytes (8-bit)
+    const int byte_rows = n_inputs * (bits / 4);
+    if ((layout != CORR_L_CIT || bits == 8) &&
+        cudaMalloc(&x->turned, (size_t)x->turned_stride * byte_rows * n_chans) != cudaSuccess) { st = CORR_ENOMEM; break; }
     if (cudaMalloc(&x->d_status, sizeof(int)) != cudaSuccess) { st = CORR_ENOMEM; break; }
     if (cudaMemset(x->d_status, 0, sizeof(int)) != cudaSuccess) { st = CORR_ECUDA; break; }
     if (cudaMallocHost(&x->h_status, sizeof(int)) != cudaSuccess) { st = CORR_ENOMEM; break; }
@@ -297,7 +300,7 @@ int corr_create(int n_inputs, int n_chans, int n_time, int bits, int layout, uns
       }
     }
     if (st != CORR_OK) break;
-    std::vector<HerkTask> tasks = plan_tasks(n_inputs, n_chans, &x->rows_per_chan);
+    std::vector<HerkTask> tasks = plan_tasks(byte_rows, n_chans, &x->rows_per_chan);
     x->n_tasks = (int)tasks.size();
     for (const HerkTask& t : tasks) {
       const int nb = t.cb[1] >= 0 ? 2 : 1;
@@ -348,15 +351,24 @@ int corr_push(corr_ctx* x, const void* block, size_t nbytes, uint64_t seq) {
     src = x->stage[slot];
   }
   const int N = x->n_inputs, C = x->n_chans, T = x->n_time;
+  const bool eight = x->bits == 8;
+  const int R = eight ? 2 * N : N;  // byte rows per channel
   long long row_stride = T;
-  if (x->layout != CORR_L_CIT) {
+  if (x->layout != CORR_L_CIT || eight) {
     // [t][c][i] -> [c][i][t] is one transpose of a T x (C N) byte matrix;
-    // [t][i][c] -> [c][i][t] is N transposes of T x C.
+    // [t][i][c] -> [c][i][t] is N transposes of T x C.  8-bit samples are
+    // byte pairs: [t][c][i][p] turns as T x (C 2N); [t][i][c][p] as N
+    // transposes of T x 2C with each (c, p) row sent to row (c, i, p); and
+    // [c][i][t][p] only splits the planes.
     cudaEvent_t tt = phase_begin(x, x->stream);
-    cudaError_t e =
-        x->layout == CORR_L_TCI
-            ? turn_launch(src, x->turned, T, 1, C * N, x->turned_stride, x->stream)
-            : turn_launch(src, x->turned, T, N, C, x->turned_stride, x->stream);
+    cudaError_t e;
+    if (x->layout == CORR_L_TCI)
+      e = turn_launch(src, x->turned, T, 1, C * R, x->turned_stride, x->stream);
+    else if (x->layout == CORR_L_TIC)
+      e = eight ? turn_launch(src, x->turned, T, N, 2 * C, x->turned_stride, x->stream, true)
+                : turn_launch(src, x->turned, T, N, C, x->turned_stride, x->stream);
+    else
+      e = split_planes_launch(src, x->turned, (long long)C * N, T, x->turned_stride, x->stream);
     if (e != cudaSuccess) return cuda_fail(e);
     phase_end(x, kTurn, tt, x->stream);
     ++x->stats.turn_launches;
@@ -369,7 +381,7 @@ int corr_push(corr_ctx* x, const void* block, size_t nbytes, uint64_t seq) {
   a.acc = x->acc;
   a.tasks = x->tasks;
   a.status = x->d_status;
-  a.chan_stride = (long long)N * row_stride;
+  a.chan_stride = (long long)R * row_stride;
   a.row_stride = row_stride;
   a.n_inputs = N;
   a.n_chans = C;
@@ -378,16 +390,19 @@ int corr_push(corr_ctx* x, const void* block, size_t nbytes, uint64_t seq) {
   a.smem_bytes = x->smem_bytes;
   a.n_tasks = x->n_tasks;
   a.max_nblk = x->max_nblk;
+  a.bits = x->bits;
   // The TMA kernel needs 16-byte aligned rows; otherwise plain loads.
   CUtensorMap tmap;
   const bool aligned = row_stride % 16 == 0 && reinterpret_cast<uintptr_t>(src) % 16 == 0;
   const int box_in = x->rows_per_chan ? x->rows_per_chan / 2 : 64;
   const int box_ch = x->rows_per_chan ? 128 / x->rows_per_chan : 1;
   const bool use_tma =
-      aligned && make_sample_tmap(&tmap, src, T, row_stride, N, C, box_in, box_ch);
-  for (int t0 = 0; t0 < T; t0 += kMaxChunk4) {
+      aligned && make_sample_tmap(&tmap, src, T, row_stride, R, C, box_in, box_ch);
+  if (eight && !use_tma) return CORR_ECUDA;  // the plane-split copy is always aligned
+  const int chunk = eight ? kMaxChunk8 : kMaxChunk4;
+  for (int t0 = 0; t0 < T; t0 += chunk) {
     a.t0 = t0;
-    a.tn = std::min(kMaxChunk4, T - t0);
+    a.tn = std::min(chunk, T - t0);
     a.accumulate = x->acc_live ? 1 : 0;
     a.vec_ok = aligned ? 1 : 0;
     cudaEvent_t th = phase_begin(x, x->stream);

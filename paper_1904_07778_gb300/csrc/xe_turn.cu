@@ -39,7 +39,8 @@ __device__ __forceinline__ int tile_word(int row, int w) { return row * 32 + (w 
 
 __global__ void __launch_bounds__(256, 4) turn_kernel(const uint8_t* __restrict__ in,
                                                       uint8_t* __restrict__ out, int T, int G,
-                                                      int K, long long os, int vec_ok) {
+                                                      int K, long long os, int vec_ok,
+                                                      int pair_rows) {
   __shared__ __align__(16) uint32_t tile[kTT * 32];
   const int t0 = blockIdx.x * kTT, k0 = blockIdx.y * kTK, g = blockIdx.z;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -90,7 +91,9 @@ __global__ void __launch_bounds__(256, 4) turn_kernel(const uint8_t* __restrict_
   for (int c = 0; c < 4; ++c) {
     const int k = k0 + 4 * kq + c;
     const int tb = t0 + ts * 32;
-    uint8_t* o = out + ((long long)k * G + g) * os + tb;
+    const long long row =
+        pair_rows ? ((long long)(k >> 1) * G + g) * 2 + (k & 1) : (long long)k * G + g;
+    uint8_t* o = out + row * os + tb;
     if (full) {
       const uint32_t r[8] = {a[c], a[4 + c], a[8 + c], a[12 + c],
                              a[16 + c], a[20 + c], a[24 + c], a[28 + c]};
@@ -98,6 +101,39 @@ __global__ void __launch_bounds__(256, 4) turn_kernel(const uint8_t* __restrict_
     } else if (k < K) {
       for (int b = 0; b < 32; ++b)
         if (tb + b < T) o[b] = (uint8_t)(a[4 * (b >> 2) + c] >> ((b & 3) * 8));
+    }
+  }
+}
+
+// ---------------------------------------------------------------- plane split
+// out[r][p][t] = in[r][t][p] for 8-bit complex samples: 16 samples (32 bytes)
+// per thread become 16 real and 16 imaginary bytes.
+__global__ void split_planes_kernel(const uint8_t* __restrict__ in, uint8_t* __restrict__ out,
+                                    long long rows, int T, long long os, int vec_ok) {
+  const int per_row = (T + 15) / 16;
+  const long long total = rows * per_row;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long r = e / per_row;
+    const int t = (int)(e - r * per_row) * 16;
+    const uint8_t* src = in + (r * T + t) * 2;
+    uint8_t* dre = out + (2 * r) * os + t;
+    uint8_t* dim = dre + os;
+    if (vec_ok && t + 16 <= T) {
+      const uint4 a = *reinterpret_cast<const uint4*>(src);
+      const uint4 b = *reinterpret_cast<const uint4*>(src + 16);
+      // even bytes are real parts, odd bytes imaginary parts
+      *reinterpret_cast<uint4*>(dre) =
+          make_uint4(__byte_perm(a.x, a.y, 0x6420), __byte_perm(a.z, a.w, 0x6420),
+                     __byte_perm(b.x, b.y, 0x6420), __byte_perm(b.z, b.w, 0x6420));
+      *reinterpret_cast<uint4*>(dim) =
+          make_uint4(__byte_perm(a.x, a.y, 0x7531), __byte_perm(a.z, a.w, 0x7531),
+                     __byte_perm(b.x, b.y, 0x7531), __byte_perm(b.z, b.w, 0x7531));
+    } else {
+      for (int k = 0; k < 16 && t + k < T; ++k) {
+        dre[k] = src[2 * k];
+        dim[k] = src[2 * k + 1];
+      }
     }
   }
 }
@@ -131,12 +167,25 @@ __global__ void normalise_kernel(const int64_t* __restrict__ acc, double* __rest
 }  // namespace
 
 cudaError_t turn_launch(const uint8_t* in, uint8_t* out, int T, int G, int K, long long out_stride,
-                        cudaStream_t s) {
+                        cudaStream_t s, bool pair_rows) {
   const int vec_ok = (K % 32 == 0) && (T % 32 == 0) && (out_stride % 32 == 0) &&
                      (reinterpret_cast<uintptr_t>(in) % 32 == 0) &&
                      (reinterpret_cast<uintptr_t>(out) % 32 == 0);
   dim3 grid((T + kTT - 1) / kTT, (K + kTK - 1) / kTK, G);
-  turn_kernel<<<grid, 256, 0, s>>>(in, out, T, G, K, out_stride, vec_ok);
+  turn_kernel<<<grid, 256, 0, s>>>(in, out, T, G, K, out_stride, vec_ok, pair_rows ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t split_planes_launch(const uint8_t* in, uint8_t* out, long long rows, int T,
+                                long long out_stride, cudaStream_t s) {
+  const int vec_ok = (T % 16 == 0) && (out_stride % 16 == 0) &&
+                     (reinterpret_cast<uintptr_t>(in) % 16 == 0) &&
+                     (reinterpret_cast<uintptr_t>(out) % 16 == 0);
+  const long long total = rows * ((T + 15) / 16);
+  long long blocks = (total + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks < 1) blocks = 1;
+  split_planes_kernel<<<(unsigned)blocks, 256, 0, s>>>(in, out, rows, T, out_stride, vec_ok);
   return cudaGetLastError();
 }
 

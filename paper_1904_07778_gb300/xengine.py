@@ -165,18 +165,22 @@ class Correlator:
             raise CorrError(st, "corr_push")
         return st
 
-    def dump_into(self, vis, reset=True):
+    def dump_into(self, vis, reset=True, check=True):
+        """Copy the integration into ``vis``.  With check=False a non-OK
+        status (CORR_ERANGE after an 8-bit -128, for instance) does not
+        raise; it is left in ``last_status`` and ``vis`` still holds the sums."""
         p, n = _ptr_and_size(vis)
         if n != self.n_chans * self.n_baselines * 16:
             raise ValueError("vis must hold n_chans * n_baselines * 2 int64")
         st = corr_dump(self._ctx, p, 1 if reset else 0)
-        if st != CORR_OK:
+        self.last_status = st
+        if check and st != CORR_OK:
             raise CorrError(st, "corr_dump")
         return vis
 
-    def dump(self, reset=True):
+    def dump(self, reset=True, check=True):
         vis = np.empty((self.n_chans, self.n_baselines, 2), dtype=np.int64)
-        return self.dump_into(vis, reset)
+        return self.dump_into(vis, reset, check)
 
     def normalise_into(self, rho):
         p, n = _ptr_and_size(rho)
