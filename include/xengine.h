@@ -195,7 +195,7 @@ int corr_get_stats(corr_ctx* ctx, corr_stats* out);
  *   status  : optional device int; receives the device status bits of this
  *             call (0 ok, 1 a bounded device-side wait ran out).
  *   stream  : cudaStream_t to run on (NULL: the legacy default stream).
- * Limits: 256 + 16 * tasks (rounded up to 256) + (layout != CORR_L_CIT ?
+ * Limits: 256 + 20 * tasks (rounded up to 256) + (layout != CORR_L_CIT ?
  * N * C * ceil16(T) : 0) bytes must fit the scratch, where tasks is C / (128 /
  * 2^ceil(log2 2N)) rounded up for 2N <= 64, else C times the tasks of one
  * channel; larger requests return CORR_EINVAL.  Host pointers return
@@ -211,6 +211,101 @@ int corr_get_stats(corr_ctx* ctx, corr_stats* out);
 #define CORR_NOALLOC_SCRATCH_BYTES (16u << 20)
 int corr_correlate_noalloc(const void* block, int n_inputs, int n_chans, int n_time, int layout,
                            unsigned flags, int64_t* vis, int* status, void* stream);
+
+/*
+ * Batches: several arrays correlated in one persistent launch.
+ *
+ * A correlator node may serve several arrays (or subarrays) at once, each
+ * with its own input count, channel count and block length (the paper's
+ * Sec. 2 node takes F/N channels of M m inputs; here the shapes differ).
+ * A batch holds every array's device state and correlates one block of
+ * every array per run: the corner turns, then ONE persistent cross-multiply
+ * launch over all arrays' tasks, replayed from a CUDA graph.  The task
+ * schedule (tile grouping, assignment of tasks to SMs) can be autotuned at
+ * creation by timing candidate schedules on the device.
+ */
+typedef struct corr_shape {
+  int n_inputs;   /* N, 1 <= N <= 1024                                      */
+  int n_chans;    /* C >= 1                                                 */
+  int n_time;     /* T spectra per block, 1 <= T <= 65536 (4-bit), 32768 (8-bit) */
+  int bits;       /* 4 or 8 (the same for every array of a batch)           */
+  int layout;     /* CORR_L_*                                               */
+  unsigned flags; /* CORR_F_* (the same for every array of a batch)         */
+} corr_shape;
+
+typedef struct corr_batch corr_batch; /* opaque, owned by the library */
+
+/* Schedules an autotuned batch can choose from (corr_batch_info.schedule). */
+#define CORR_SCHED_PAIRS_LPT 0   /* 128x256 tasks, longest-first onto the least loaded SM */
+#define CORR_SCHED_SINGLES_LPT 1 /* 128x128 tasks, longest-first                      */
+#define CORR_SCHED_PAIRS_RR 2    /* 128x256 tasks, round robin in list order           */
+
+typedef struct corr_batch_info {
+  int schedule;          /* CORR_SCHED_* in use                                  */
+  int n_tasks;           /* tasks of one cross-multiply launch                   */
+  int n_ctas;            /* CTAs (one per SM)                                    */
+  int launches_per_run;  /* kernels one corr_batch_run launches                  */
+  double tuned_ms[3];    /* median run time of each schedule (autotune), else 0  */
+} corr_batch_info;
+
+/*
+ * corr_batch_create -- device state for n arrays (inputs, corner-turn
+ * copies, int64 visibilities) and the run's CUDA graph.
+ *   shapes : n array shapes; every array must have the same bits and flags.
+ *   stream : cudaStream_t for the runs; NULL or a default stream (legacy,
+ *            per-thread), on which no graph can be captured, gives a private
+ *            stream (the caller then orders its own work with corr_batch_sync).
+ *   tune   : 0 uses CORR_SCHED_PAIRS_LPT; 1 times every schedule on the
+ *            device (on the current contents of the input buffers) and keeps
+ *            the fastest.
+ * Returns CORR_EINVAL for a bad shape or mixed bits/flags, CORR_ENOMEM,
+ * CORR_ECUDA.
+ */
+int corr_batch_create(const corr_shape* shapes, int n, void* stream, int tune, corr_batch** out);
+
+/* Device buffer of array k's input block (N C T bits/4 bytes, the array's
+ * layout); the caller fills it before corr_batch_run.  NULL if k is invalid. */
+void* corr_batch_input(corr_batch* b, int k);
+
+/* Device int64 [C][N(N+1)/2][2] visibilities of array k's last block, valid
+ * after the run completes (corr_batch_sync).  NULL if k is invalid. */
+int64_t* corr_batch_output(corr_batch* b, int k);
+
+/* Copy array k's block in (host or device src, exactly N C T bits/4 bytes),
+ * or its visibilities out (host or device dst, N(N+1)/2 C 2 int64), ordered
+ * on the batch's stream; CORR_EINVAL for a bad k, pointer or size. */
+int corr_batch_set_input(corr_batch* b, int k, const void* src, size_t nbytes);
+int corr_batch_get_output(corr_batch* b, int k, int64_t* dst);
+
+/* corr_batch_run -- correlate the current block of every array (the outputs
+ * are overwritten, not accumulated): replays the batch's CUDA graph on its
+ * stream.  Asynchronous. */
+int corr_batch_run(corr_batch* b);
+
+/* corr_batch_run_plain -- the same work as one corner turn and one
+ * cross-multiply launch per array, without a graph (the comparison form).
+ * Asynchronous. */
+int corr_batch_run_plain(corr_batch* b);
+
+/* Wait for the batch's stream; returns a pending device status (CORR_ERANGE,
+ * CORR_ETIMEDOUT) once, else CORR_OK. */
+int corr_batch_sync(corr_batch* b);
+
+int corr_batch_info_get(corr_batch* b, corr_batch_info* out);
+void corr_batch_destroy(corr_batch* b);
+
+/*
+ * corr_plan_schedule -- longest-processing-time-first assignment of tasks to
+ * CTAs (host only; no device needed).
+ *   cost      : n_tasks task costs (any positive unit).
+ *   order     : out, n_tasks task indices grouped by CTA, each CTA's tasks in
+ *               decreasing cost.
+ *   cta_first : out, n_ctas + 1 offsets into order (CTA b runs
+ *               order[cta_first[b] .. cta_first[b + 1]) ).
+ * Tasks are taken in decreasing cost and each goes to the CTA with the least
+ * total so far (ties: lowest index).  Returns CORR_EINVAL for bad arguments.
+ */
+int corr_plan_schedule(const double* cost, int n_tasks, int n_ctas, int* order, int* cta_first);
 
 #ifdef __cplusplus
 }

@@ -191,7 +191,7 @@ __device__ __forceinline__ void mma_loop(const TaskGeom& g, int nk, int nst, uin
 // chunk go to the lane of row 2i, the odd ones to row 2i + 1, and each
 // visibility is one 16-byte store (adjacent lanes fill 32 contiguous bytes
 // in lower blocks, 16 lanes fill 256 contiguous bytes in upper blocks).
-__device__ __forceinline__ void epilogue(const HerkArgs& a, const HerkTask& task, const TaskGeom& g,
+__device__ __forceinline__ void epilogue(const HerkInst& a, const HerkTask& task, const TaskGeom& g,
                                          const int32_t* usum, uint32_t tmem, int quad, int part,
                                          int nparts, int lane) {
   const bool stacked = a.rows_per_chan > 0;
@@ -291,7 +291,7 @@ __device__ __forceinline__ void epilogue(const HerkArgs& a, const HerkTask& task
 // A lane forms its row's share for the four inputs j of a 16-column chunk;
 // the four lanes of input i reduce-scatter them (six shuffles) so that lane
 // t ends with the visibility of the chunk's t-th input.
-__device__ __forceinline__ void epilogue8(const HerkArgs& a, const HerkTask& task, const TaskGeom& g,
+__device__ __forceinline__ void epilogue8(const HerkInst& a, const HerkTask& task, const TaskGeom& g,
                                           const int32_t* usum, uint32_t tmem, int quad, int part,
                                           int nparts, int lane) {
   const bool stacked = a.rows_per_chan > 0;
@@ -473,8 +473,19 @@ struct RingCtrl {
   int32_t usum[2][kMaxBlocks * 128];
 };
 
+// Task j of this CTA: its explicit list, or round robin over the CTAs.
 __device__ __forceinline__ HerkTask my_task(const HerkArgs& a, int j) {
-  return a.tasks[blockIdx.x + j * gridDim.x];
+  return a.cta_first ? a.tasks[a.cta_first[blockIdx.x] + j] : a.tasks[blockIdx.x + j * gridDim.x];
+}
+__device__ __forceinline__ int my_task_count(const HerkArgs& a) {
+  if (a.cta_first) return a.cta_first[blockIdx.x + 1] - a.cta_first[blockIdx.x];
+  return (a.n_tasks - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+}
+__device__ __forceinline__ HerkInst task_inst(const HerkArgs& a, const HerkTask& t) {
+  return a.insts ? a.insts[t.inst] : a.in;
+}
+__device__ __forceinline__ int stages_of(const HerkInst& in) {
+  return (in.tn + kStageT - 1) / kStageT;
 }
 
 template <bool LO_IS_REAL, bool EIGHT>
@@ -487,10 +498,7 @@ __global__ void __launch_bounds__(kRingThreads, 1)
       dyn_raw + ((a.smem_bytes - (int)sizeof(RingCtrl)) & ~15));
   uint8_t* ring = align1024(dyn_raw);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const bool stacked = a.rows_per_chan > 0;
-  const int n_my = (a.n_tasks - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
-  const int nk = (a.tn + kStageT - 1) / kStageT;
-  const int total = n_my * nk;
+  const int n_my = my_task_count(a);  // tasks of this CTA; stage counts vary per array
   const int slot_bytes = a.max_nblk * kOpBlockBytes;
   int ns = (int)(reinterpret_cast<uint8_t*>(&sm) - ring) / slot_bytes;
   if (ns > kMaxSlots) ns = kMaxSlots;
@@ -528,30 +536,41 @@ __global__ void __launch_bounds__(kRingThreads, 1)
   if (warp == kTmaWarp) {
     // ------------------------------------------------------------ TMA loader
     regs_shrink<kRegsOther>();
-    if (lane == 0) {
-      tma_prefetch_desc(&tmap);
+    if (lane == 0 && n_my > 0) {
+      if (!a.tmaps) tma_prefetch_desc(&tmap);
       int s = 0, m = 0, j = 0, k = 0, issued = 0;
       HerkTask task = my_task(a, 0);
       TaskGeom g = task_geom(task);
-      for (int S = 0; S < total; ++S, ++k) {
+      HerkInst in = task_inst(a, task);
+      const CUtensorMap* tm = a.tmaps ? &a.tmaps[task.inst] : &tmap;
+      if (a.tmaps) tensormap_acquire(tm);
+      int nk = stages_of(in);
+      bool stacked = in.rows_per_chan > 0;
+      for (int S = 0;; ++S, ++k) {
         if (k == nk) {  // next task
+          if (++j == n_my) break;
           k = 0;
-          task = my_task(a, ++j);
+          task = my_task(a, j);
           g = task_geom(task);
+          in = task_inst(a, task);
+          tm = a.tmaps ? &a.tmaps[task.inst] : &tmap;
+          if (a.tmaps) tensormap_acquire(tm);
+          nk = stages_of(in);
+          stacked = in.rows_per_chan > 0;
         }
         if (m > 0 && !mbar_wait(&sm.empty[s], (uint32_t)((m - 1) & 1), abort)) {
           raise_timeout(a.status, abort);
           break;
         }
-        const int t = a.t0 + k * kStageT;
+        const int t = in.t0 + k * kStageT;
         const uint32_t dst0 = ring_addr + (uint32_t)(s * slot_bytes + g.nblk * kPkBlockBytes);
         mbar_expect_tx(&sm.full_t[s], (uint32_t)(g.nblk * kPkBlockBytes));
         for (int b = 0; b < g.nblk; ++b) {
           const uint32_t dst = dst0 + (uint32_t)(b * kPkBlockBytes);
           if (stacked)
-            tma_load_3d(dst, &tmap, t, 0, task.chan0, &sm.full_t[s]);
+            tma_load_3d(dst, tm, t, 0, task.chan0, &sm.full_t[s]);
           else
-            tma_load_3d(dst, &tmap, t, 64 * slot_block(g, b), task.chan0, &sm.full_t[s]);
+            tma_load_3d(dst, tm, t, 64 * slot_block(g, b), task.chan0, &sm.full_t[s]);
         }
         ++issued;
         if (++s == ns) {
@@ -573,7 +592,9 @@ __global__ void __launch_bounds__(kRingThreads, 1)
       bool ok = true;
       for (int j = 0; j < n_my && ok; ++j) {
         const int b = j & 1;
-        const TaskGeom g = task_geom(my_task(a, j));
+        const HerkTask task = my_task(a, j);
+        const TaskGeom g = task_geom(task);
+        const int nk = stages_of(task_inst(a, task));
         const uint32_t idesc = umma_idesc(0, 128, 128 * g.nb);
         if (j >= 2 && !mbar_wait(&sm.tmem_empty[b], (uint32_t)(((j >> 1) - 1) & 1), abort)) {
           raise_timeout(a.status, abort);
@@ -622,24 +643,28 @@ __global__ void __launch_bounds__(kRingThreads, 1)
     // advanced by additions (kGroups <= ns)
     int S = grp, s = grp, m = 0;
     uint32_t bad = 0;  // 8-bit: a byte equal to 0x80 (-128) was seen
+    int S0 = 0;  // first stage of task j
     for (int j = 0; j < n_my && ok; ++j) {
       const int b = j & 1;
-      const TaskGeom g = task_geom(my_task(a, j));
+      const HerkTask task = my_task(a, j);
+      const TaskGeom g = task_geom(task);
+      const int tn = task_inst(a, task).tn;
+      const int S1 = S0 + (tn + kStageT - 1) / kStageT;
       const int nit = g.nblk * 512 / kGroupThreads;
       int32_t sre[kItems], sim[kItems];
 #pragma unroll
       for (int it = 0; it < kItems; ++it) sre[it] = sim[it] = 0;
-      // this group's stages of task j: S = j nk + k with S = grp (mod kGroups)
-      for (; S < (j + 1) * nk; S += kGroups) {
-        const int k = S - j * nk;
+      // this group's stages of task j: S0 <= S < S1 with S = grp (mod kGroups)
+      for (; S < S1; S += kGroups) {
+        const int k = S - S0;
         bool got = (m == 0 || mbar_wait(&sm.empty[s], (uint32_t)((m - 1) & 1), abort)) &&
                    mbar_wait(&sm.full_t[s], (uint32_t)(m & 1), abort);
         if (!got) raise_timeout(a.status, abort);
         const uint32_t so = (uint32_t)(s * slot_bytes);
         const uint32_t src = src0 + so + (uint32_t)(g.nblk * kPkBlockBytes);
-        const bool tail = (k + 1) * kStageT > a.tn;
+        const bool tail = (k + 1) * kStageT > tn;
         uint32_t keep[4] = {~0u, ~0u, ~0u, ~0u};
-        if (tail) time_keep(k * kStageT + chunk * 16, a.tn, keep);
+        if (tail) time_keep(k * kStageT + chunk * 16, tn, keep);
         uint4 v[kItems];
 #pragma unroll
         for (int it = 0; it < kItems; ++it)
@@ -686,6 +711,7 @@ __global__ void __launch_bounds__(kRingThreads, 1)
       publish_row_sums<kGroupThreads>(sre, sim, nit, gt, sm.usum[b]);
       __syncwarp();
       if (lane == 0) mbar_arrive(&sm.usum_full[b]);
+      S0 = S1;
     }
     if (EIGHT && __any_sync(0xFFFFFFFFu, bad != 0) && lane == 0) atomicOr(a.status, kStRange);
   } else if (warp < kEpiWarp0) {
@@ -702,11 +728,12 @@ __global__ void __launch_bounds__(kRingThreads, 1)
       if (!named_bar_and(1, kEpiWarps * 32, got)) break;  // the drain warps leave together
       tc_after_sync();
       const HerkTask task = my_task(a, j);
+      const HerkInst in = task_inst(a, task);
       if (EIGHT)
-        epilogue8(a, task, task_geom(task), sm.usum[b], tmem + (uint32_t)(b * 256), quad, part,
+        epilogue8(in, task, task_geom(task), sm.usum[b], tmem + (uint32_t)(b * 256), quad, part,
                   kEpiWarps / 4, lane);
       else
-        epilogue(a, task, task_geom(task), sm.usum[b], tmem + (uint32_t)(b * 256), quad, part,
+        epilogue(in, task, task_geom(task), sm.usum[b], tmem + (uint32_t)(b * 256), quad, part,
                  kEpiWarps / 4, lane);
       tc_before_sync();
       __syncwarp();
@@ -730,16 +757,17 @@ constexpr int kLdgThreads = 160;
 constexpr int kLdgItems = kMaxBlocks * 4;
 
 template <bool LO_IS_REAL>
-__global__ void __launch_bounds__(kLdgThreads, 1) herk4_ldg_kernel(const HerkArgs a) {
+__global__ void __launch_bounds__(kLdgThreads, 1) herk4_ldg_kernel(const HerkArgs args) {
+  const HerkInst& a = args.in;
   extern __shared__ uint8_t dyn_raw[];
   __shared__ Ctrl sm;
   uint8_t* ops = align1024(dyn_raw);
-  const HerkTask task = a.tasks[blockIdx.x];
+  const HerkTask task = args.tasks[blockIdx.x];
   const TaskGeom g = task_geom(task);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const bool stacked = a.rows_per_chan > 0;
   const int stage_bytes = g.nblk * kOpBlockBytes;
-  int nst = (a.smem_bytes - 1024) / stage_bytes;
+  int nst = (args.smem_bytes - 1024) / stage_bytes;
   if (nst > kMaxStages) nst = kMaxStages;
   const int nk = (a.tn + kStageT - 1) / kStageT;
   volatile int* abort = &sm.abort;
@@ -761,7 +789,7 @@ __global__ void __launch_bounds__(kLdgThreads, 1) herk4_ldg_kernel(const HerkArg
   if (warp == 4) {
     if (lane == 0)
       mma_loop(g, nk, nst, smem_addr(ops), (uint32_t)stage_bytes, tmem, sm.full_o, sm.empty_o,
-               &sm.done, a.status, abort);
+               &sm.done, args.status, abort);
     __syncwarp();
   } else {
     const int chunk = tid & 7;
@@ -793,7 +821,7 @@ __global__ void __launch_bounds__(kLdgThreads, 1) herk4_ldg_kernel(const HerkArg
     uint32_t ph = 0;
     for (int k = 0; k < nk; ++k) {
       if (k >= nst && !mbar_wait(&sm.empty_o[s], ph ^ 1u, abort)) {
-        raise_timeout(a.status, abort);
+        raise_timeout(args.status, abort);
         break;
       }
       uint8_t* st = ops + s * stage_bytes;
@@ -842,7 +870,7 @@ __global__ void __launch_bounds__(kLdgThreads, 1) herk4_ldg_kernel(const HerkArg
     int never = 0;
     bool good = mbar_wait(&sm.done, 0, &never);
     good = __all_sync(0xFFFFFFFFu, good);
-    if (!good && lane == 0) raise_timeout(a.status, abort);
+    if (!good && lane == 0) raise_timeout(args.status, abort);
     tc_after_sync();
     if (good && !*abort) epilogue(a, task, g, sm.usum, tmem, warp & 3, 0, 1, lane);
   }
@@ -876,8 +904,14 @@ int ring_smem() {
 
 template <bool LO, bool EIGHT>
 cudaError_t ring_launch(const HerkArgs& a, const CUtensorMap* tmap, int grid, cudaStream_t s) {
-  cudaError_t e = set_smem(herk4_ring_kernel<LO, EIGHT>, a.smem_bytes);
-  if (e != cudaSuccess) return e;
+  // the attribute persists: set it once, so that launches captured into a
+  // CUDA graph are plain stream work
+  static int set_bytes = -1;
+  if (set_bytes != a.smem_bytes) {
+    cudaError_t e = set_smem(herk4_ring_kernel<LO, EIGHT>, a.smem_bytes);
+    if (e != cudaSuccess) return e;
+    set_bytes = a.smem_bytes;
+  }
   herk4_ring_kernel<LO, EIGHT><<<grid, kRingThreads, a.smem_bytes, s>>>(*tmap, a);
   return cudaGetLastError();
 }
@@ -893,29 +927,36 @@ int herk4_max_smem() {
 cudaError_t herk4_launch(const HerkArgs& args, const CUtensorMap* tmap, int n_tasks,
                          cudaStream_t s) {
   cudaError_t e;
-  if (tmap) {
+  if (tmap || args.tmaps) {
     HerkArgs a = args;
     a.smem_bytes = ring_smem();
     // four slots of the largest stage, the control block and the alignment pad
     if (a.smem_bytes < kGroups * a.max_nblk * kOpBlockBytes + (int)sizeof(RingCtrl) + 1024)
       return cudaErrorInvalidConfiguration;
-    int dev = 0, nsm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const int grid = std::min(n_tasks, nsm);
-    if (a.bits == 8) return ring_launch<false, true>(a, tmap, grid, s);
-    return a.lo_is_real ? ring_launch<true, false>(a, tmap, grid, s)
-                        : ring_launch<false, false>(a, tmap, grid, s);
-  } else {
-    const HerkArgs& a = args;
-    if (a.bits != 4) return cudaErrorInvalidValue;  // 8-bit rows are always TMA-aligned
-    if (a.lo_is_real) {
-      if ((e = set_smem(herk4_ldg_kernel<true>, a.smem_bytes)) != cudaSuccess) return e;
-      herk4_ldg_kernel<true><<<n_tasks, kLdgThreads, a.smem_bytes, s>>>(a);
+    int grid;
+    if (a.cta_first) {
+      grid = a.grid;
     } else {
-      if ((e = set_smem(herk4_ldg_kernel<false>, a.smem_bytes)) != cudaSuccess) return e;
-      herk4_ldg_kernel<false><<<n_tasks, kLdgThreads, a.smem_bytes, s>>>(a);
+      int dev = 0, nsm = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+      grid = std::min(n_tasks, nsm);
     }
+    if (grid < 1) return cudaSuccess;
+    static const CUtensorMap unused{};  // batched launches read their maps from a.tmaps
+    const CUtensorMap* m = tmap ? tmap : &unused;
+    if (a.bits == 8) return ring_launch<false, true>(a, m, grid, s);
+    return a.lo_is_real ? ring_launch<true, false>(a, m, grid, s)
+                        : ring_launch<false, false>(a, m, grid, s);
+  }
+  const HerkArgs& a = args;
+  if (a.bits != 4) return cudaErrorInvalidValue;  // 8-bit rows are always TMA-aligned
+  if (a.lo_is_real) {
+    if ((e = set_smem(herk4_ldg_kernel<true>, a.smem_bytes)) != cudaSuccess) return e;
+    herk4_ldg_kernel<true><<<n_tasks, kLdgThreads, a.smem_bytes, s>>>(a);
+  } else {
+    if ((e = set_smem(herk4_ldg_kernel<false>, a.smem_bytes)) != cudaSuccess) return e;
+    herk4_ldg_kernel<false><<<n_tasks, kLdgThreads, a.smem_bytes, s>>>(a);
   }
   return cudaGetLastError();
 }

@@ -3,6 +3,7 @@
 #pragma once
 #include <cstddef>
 #include <cstdint>
+#include <vector>
 
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -34,25 +35,37 @@ struct HerkTask {
   int chan0;
   int rb;
   int cb[2];
+  int inst;  // array (instance) of a batched launch; 0 for a single array
 };
 
-struct HerkArgs {
-  const uint8_t* x;          // samples, [channel][input][time] order
+// One array's block as the cross-multiply sees it.
+struct HerkInst {
+  const uint8_t* x;          // samples, [channel][byte row][time] order
   int64_t* acc;              // int64 visibilities [C][N(N+1)/2][2]
-  const HerkTask* tasks;
-  int* status;
   long long chan_stride;     // bytes between channels of x
-  long long row_stride;      // bytes between inputs of x
+  long long row_stride;      // bytes between byte rows of x
   int n_inputs, n_chans;
   int t0, tn;                // time range [t0, t0 + tn) of this launch, samples
   int rows_per_chan;         // stacked mode: rows per channel in a tile; 0 = not stacked
   int accumulate;            // 0: store into acc, 1: add into acc
-  int lo_is_real;            // 4-bit: real part in the low nibble
   int vec_ok;                // 16-byte loads are aligned everywhere
+  int pad;
+};
+
+struct HerkArgs {
+  HerkInst in;               // the array of a single-array launch
+  const HerkInst* insts;     // batched launch: per-array parameters (device memory), else null
+  const CUtensorMap* tmaps;  // batched launch: per-array tensor maps (device, 64-byte aligned)
+  const HerkTask* tasks;
+  const int* cta_first;      // if set, CTA b runs tasks [cta_first[b], cta_first[b + 1]);
+                             // otherwise task j of CTA b is b + j * gridDim.x
+  int* status;
+  int lo_is_real;            // 4-bit: real part in the low nibble (whole launch)
+  int bits;                  // 4, or 8 (byte rows: 2 per input, 4 rows of Y per input)
   int smem_bytes;            // dynamic shared memory of the launch
   int n_tasks;               // tasks in `tasks`
   int max_nblk;              // largest number of resident 128-row blocks of any task
-  int bits;                  // 4, or 8 (byte rows: 2 per input, 4 rows of Y per input)
+  int grid;                  // CTAs of a launch with cta_first
 };
 
 // Largest number of spectra integrated in one tensor-memory accumulation:
@@ -66,9 +79,11 @@ constexpr int kMaxChunk4 = 65536;
 constexpr int kMaxChunk8 = 32768;
 
 int herk4_max_smem();
-// tmap == nullptr selects the kernel that loads with plain global loads (any
-// alignment); otherwise tmap describes x as a 3-D byte tensor
-// {time (row_stride apart: inner), input, channel} for the TMA kernel.
+// Launch the cross-multiply.  Batched (a.insts and a.tmaps set): the ring
+// kernel over every array's tasks in one persistent launch.  Otherwise tmap
+// describes a.in.x as a 3-D byte tensor {time (inner), byte row, channel} for
+// the ring kernel, or is null for the kernel that loads with plain global
+// loads (any alignment).
 cudaError_t herk4_launch(const HerkArgs& a, const CUtensorMap* tmap, int n_tasks, cudaStream_t s);
 
 // Build the tensor map of a [channel][input][time] byte array with rows of
@@ -89,6 +104,20 @@ cudaError_t turn_launch(const uint8_t* in, uint8_t* out, int T, int G, int K, lo
 // out[row][p][t] = in[row][t][p], output rows of out_stride bytes.
 cudaError_t split_planes_launch(const uint8_t* in, uint8_t* out, long long rows, int T,
                                 long long out_stride, cudaStream_t s);
+
+// Lay one block out as [channel][byte row][time] with rows of out_stride
+// bytes (byte rows: one per input at 4 bits, re and im bytes at 8 bits).
+// Returns false without launching when the layout is already that one
+// (4-bit [c][i][t]): the block itself is then the cross-multiply's input.
+bool needs_turn(int layout, int bits);
+cudaError_t turn_rows(const uint8_t* in, uint8_t* out, int layout, int bits, int n_inputs,
+                      int n_chans, int n_time, long long out_stride, cudaStream_t s);
+
+// Tasks of one array (see HerkTask): rows_per_chan is set for stacked
+// arrays.  With singles, every task has one column block (128 x 128).
+std::vector<HerkTask> plan_tasks(int byte_rows, int n_chans, int* rows_per_chan, bool singles = false);
+// Largest number of resident 128-row blocks of any task in the list.
+int tasks_max_nblk(const std::vector<HerkTask>& tasks);
 
 // FP64 correlation coefficients from int64 visibilities.
 cudaError_t normalise_launch(const int64_t* acc, double* rho, int n_inputs, int n_chans,

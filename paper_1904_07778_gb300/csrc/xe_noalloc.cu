@@ -71,6 +71,7 @@ __global__ void plan_kernel(HerkTask* tasks, long long n_tasks, int n, int c, in
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n_tasks;
        e += (long long)gridDim.x * blockDim.x) {
     HerkTask t;
+    t.inst = 0;
     if (rpc > 0) {
       t.chan0 = (int)(e * (128 / rpc));
       t.rb = 0;
@@ -164,15 +165,15 @@ extern "C" int corr_correlate_noalloc(const void* block, int n_inputs, int n_cha
     stride = row_stride;
   }
   HerkArgs a{};
-  a.x = src;
-  a.acc = vis;
+  a.in.x = src;
+  a.in.acc = vis;
   a.tasks = tasks;
   a.status = d_status;
-  a.chan_stride = (long long)N * stride;
-  a.row_stride = stride;
-  a.n_inputs = N;
-  a.n_chans = C;
-  a.rows_per_chan = rpc;
+  a.in.chan_stride = (long long)N * stride;
+  a.in.row_stride = stride;
+  a.in.n_inputs = N;
+  a.in.n_chans = C;
+  a.in.rows_per_chan = rpc;
   a.lo_is_real = (flags & CORR_F_LO_IS_REAL) ? 1 : 0;
   a.smem_bytes = herk4_max_smem();
   a.n_tasks = (int)n_tasks;
@@ -183,10 +184,10 @@ extern "C" int corr_correlate_noalloc(const void* block, int n_inputs, int n_cha
   const bool use_tma = aligned && make_sample_tmap(&tmap, src, T, stride, N, C,
                                                    rpc ? rpc / 2 : 64, rpc ? 128 / rpc : 1);
   for (int t0 = 0; t0 < T; t0 += kMaxChunk4) {
-    a.t0 = t0;
-    a.tn = std::min(kMaxChunk4, T - t0);
-    a.accumulate = t0 > 0 ? 1 : 0;
-    a.vec_ok = aligned ? 1 : 0;
+    a.in.t0 = t0;
+    a.in.tn = std::min(kMaxChunk4, T - t0);
+    a.in.accumulate = t0 > 0 ? 1 : 0;
+    a.in.vec_ok = aligned ? 1 : 0;
     if (herk4_launch(a, use_tma ? &tmap : nullptr, (int)n_tasks, s) != cudaSuccess)
       return CORR_ECUDA;
   }

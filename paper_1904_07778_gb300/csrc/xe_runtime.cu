@@ -38,6 +38,57 @@ bool make_sample_tmap(CUtensorMap* m, const uint8_t* x, int n_time, long long ro
                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Tasks of the real Gram matrix (n byte rows: 2n rows of Y): every 128 x 128
+// block (r, c), c <= r, of
+// the lower triangle exactly once.  Row block r takes the column blocks
+// r, r+1, ..., r + (nrb-1)/2 (mod nrb) -- for even nrb, r + nrb/2 goes to
+// the smaller of the two -- so the work is spread evenly over the row
+// blocks.  Columns r and r+1 form one 128 x 256 MMA task; further columns
+// are 128 x 128 tasks.  Ordered by decreasing work.
+std::vector<HerkTask> plan_tasks(int n, int c, int* rows_per_chan, bool singles) {
+  std::vector<HerkTask> t;
+  const int rows = 2 * n;
+  if (rows <= 64) {
+    int rpc = 2;
+    while (rpc < rows) rpc <<= 1;
+    *rows_per_chan = rpc;
+    const int per = 128 / rpc;
+    for (int c0 = 0; c0 < c; c0 += per) t.push_back({c0, 0, {0, -1}, 0});
+    return t;
+  }
+  *rows_per_chan = 0;
+  const int nrb = (rows + 127) / 128;
+  for (int ch = 0; ch < c; ++ch)
+    for (int r = 0; r < nrb; ++r) {
+      std::vector<int> cols;
+      for (int d = 0; 2 * d < nrb; ++d)
+        if (2 * d != nrb || r < nrb / 2) cols.push_back((r + d) % nrb);
+      if (nrb % 2 == 0 && r < nrb / 2 && 2 * (nrb / 2) == nrb) cols.push_back(r + nrb / 2);
+      // the first two columns (r and r+1) share the A rows with a B block;
+      // the others take one column each so at most two blocks are resident
+      if (singles) {
+        for (size_t k = 0; k < cols.size(); ++k) t.push_back({ch, r, {cols[k], -1}, 0});
+      } else {
+        t.push_back({ch, r, {cols[0], cols.size() > 1 ? cols[1] : -1}, 0});
+        for (size_t k = 2; k < cols.size(); ++k) t.push_back({ch, r, {cols[k], -1}, 0});
+      }
+    }
+  std::stable_sort(t.begin(), t.end(), [](const HerkTask& x, const HerkTask& y) {
+    return (x.cb[1] >= 0) > (y.cb[1] >= 0);
+  });
+  return t;
+}
+
+int tasks_max_nblk(const std::vector<HerkTask>& tasks) {
+  int m = 1;
+  for (const HerkTask& t : tasks) {
+    const int nb = t.cb[1] >= 0 ? 2 : 1;
+    const bool a_in = t.rb == t.cb[0] || (nb == 2 && t.rb == t.cb[1]);
+    m = std::max(m, a_in ? nb : nb + 1);
+  }
+  return m;
+}
+
 }  // namespace xe
 
 struct corr_ctx {
@@ -148,42 +199,6 @@ bool is_device_ptr(const void* p) {
     return false;
   }
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
-}
-
-// Tasks of the real Gram matrix: every 128 x 128 block (r, c), c <= r, of
-// the lower triangle exactly once.  Row block r takes the column blocks
-// r, r+1, ..., r + (nrb-1)/2 (mod nrb) -- for even nrb, r + nrb/2 goes to
-// the smaller of the two -- so the work is spread evenly over the row
-// blocks.  Columns r and r+1 form one 128 x 256 MMA task; further columns
-// are 128 x 128 tasks.  Ordered by decreasing work.
-std::vector<HerkTask> plan_tasks(int n, int c, int* rows_per_chan) {
-  std::vector<HerkTask> t;
-  const int rows = 2 * n;
-  if (rows <= 64) {
-    int rpc = 2;
-    while (rpc < rows) rpc <<= 1;
-    *rows_per_chan = rpc;
-    const int per = 128 / rpc;
-    for (int c0 = 0; c0 < c; c0 += per) t.push_back({c0, 0, {0, -1}});
-    return t;
-  }
-  *rows_per_chan = 0;
-  const int nrb = (rows + 127) / 128;
-  for (int ch = 0; ch < c; ++ch)
-    for (int r = 0; r < nrb; ++r) {
-      std::vector<int> cols;
-      for (int d = 0; 2 * d < nrb; ++d)
-        if (2 * d != nrb || r < nrb / 2) cols.push_back((r + d) % nrb);
-      if (nrb % 2 == 0 && r < nrb / 2 && 2 * (nrb / 2) == nrb) cols.push_back(r + nrb / 2);
-      // the first two columns (r and r+1) share the A rows with a B block;
-      // the others take one column each so at most two blocks are resident
-      t.push_back({ch, r, {cols[0], cols.size() > 1 ? cols[1] : -1}});
-      for (size_t k = 2; k < cols.size(); ++k) t.push_back({ch, r, {cols[k], -1}});
-    }
-  std::stable_sort(t.begin(), t.end(), [](const HerkTask& x, const HerkTask& y) {
-    return (x.cb[1] >= 0) > (y.cb[1] >= 0);
-  });
-  return t;
 }
 
 void free_ctx(corr_ctx* x) {
@@ -302,11 +317,7 @@ int corr_create(int n_inputs, int n_chans, int n_time, int bits, int layout, uns
     if (st != CORR_OK) break;
     std::vector<HerkTask> tasks = plan_tasks(byte_rows, n_chans, &x->rows_per_chan);
     x->n_tasks = (int)tasks.size();
-    for (const HerkTask& t : tasks) {
-      const int nb = t.cb[1] >= 0 ? 2 : 1;
-      const bool a_in = t.rb == t.cb[0] || (nb == 2 && t.rb == t.cb[1]);
-      x->max_nblk = std::max(x->max_nblk, a_in ? nb : nb + 1);
-    }
+    x->max_nblk = tasks_max_nblk(tasks);
     if (cudaMalloc(&x->tasks, tasks.size() * sizeof(HerkTask)) != cudaSuccess) { st = CORR_ENOMEM; break; }
     if (cudaMemcpy(x->tasks, tasks.data(), tasks.size() * sizeof(HerkTask), cudaMemcpyHostToDevice) != cudaSuccess) { st = CORR_ECUDA; break; }
     x->smem_bytes = herk4_max_smem();
@@ -354,21 +365,10 @@ int corr_push(corr_ctx* x, const void* block, size_t nbytes, uint64_t seq) {
   const bool eight = x->bits == 8;
   const int R = eight ? 2 * N : N;  // byte rows per channel
   long long row_stride = T;
-  if (x->layout != CORR_L_CIT || eight) {
-    // [t][c][i] -> [c][i][t] is one transpose of a T x (C N) byte matrix;
-    // [t][i][c] -> [c][i][t] is N transposes of T x C.  8-bit samples are
-    // byte pairs: [t][c][i][p] turns as T x (C 2N); [t][i][c][p] as N
-    // transposes of T x 2C with each (c, p) row sent to row (c, i, p); and
-    // [c][i][t][p] only splits the planes.
+  if (needs_turn(x->layout, x->bits)) {
     cudaEvent_t tt = phase_begin(x, x->stream);
-    cudaError_t e;
-    if (x->layout == CORR_L_TCI)
-      e = turn_launch(src, x->turned, T, 1, C * R, x->turned_stride, x->stream);
-    else if (x->layout == CORR_L_TIC)
-      e = eight ? turn_launch(src, x->turned, T, N, 2 * C, x->turned_stride, x->stream, true)
-                : turn_launch(src, x->turned, T, N, C, x->turned_stride, x->stream);
-    else
-      e = split_planes_launch(src, x->turned, (long long)C * N, T, x->turned_stride, x->stream);
+    cudaError_t e = turn_rows(src, x->turned, x->layout, x->bits, N, C, T, x->turned_stride,
+                              x->stream);
     if (e != cudaSuccess) return cuda_fail(e);
     phase_end(x, kTurn, tt, x->stream);
     ++x->stats.turn_launches;
@@ -377,15 +377,15 @@ int corr_push(corr_ctx* x, const void* block, size_t nbytes, uint64_t seq) {
   }
   HerkArgs a;
   memset(&a, 0, sizeof(a));
-  a.x = src;
-  a.acc = x->acc;
+  a.in.x = src;
+  a.in.acc = x->acc;
   a.tasks = x->tasks;
   a.status = x->d_status;
-  a.chan_stride = (long long)R * row_stride;
-  a.row_stride = row_stride;
-  a.n_inputs = N;
-  a.n_chans = C;
-  a.rows_per_chan = x->rows_per_chan;
+  a.in.chan_stride = (long long)R * row_stride;
+  a.in.row_stride = row_stride;
+  a.in.n_inputs = N;
+  a.in.n_chans = C;
+  a.in.rows_per_chan = x->rows_per_chan;
   a.lo_is_real = (x->flags & CORR_F_LO_IS_REAL) ? 1 : 0;
   a.smem_bytes = x->smem_bytes;
   a.n_tasks = x->n_tasks;
@@ -401,10 +401,10 @@ int corr_push(corr_ctx* x, const void* block, size_t nbytes, uint64_t seq) {
   if (eight && !use_tma) return CORR_ECUDA;  // the plane-split copy is always aligned
   const int chunk = eight ? kMaxChunk8 : kMaxChunk4;
   for (int t0 = 0; t0 < T; t0 += chunk) {
-    a.t0 = t0;
-    a.tn = std::min(chunk, T - t0);
-    a.accumulate = x->acc_live ? 1 : 0;
-    a.vec_ok = aligned ? 1 : 0;
+    a.in.t0 = t0;
+    a.in.tn = std::min(chunk, T - t0);
+    a.in.accumulate = x->acc_live ? 1 : 0;
+    a.in.vec_ok = aligned ? 1 : 0;
     cudaEvent_t th = phase_begin(x, x->stream);
     cudaError_t e = herk4_launch(a, use_tma ? &tmap : nullptr, x->n_tasks, x->stream);
     if (e != cudaSuccess) return cuda_fail(e);

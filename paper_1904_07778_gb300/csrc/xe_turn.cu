@@ -189,6 +189,25 @@ cudaError_t split_planes_launch(const uint8_t* in, uint8_t* out, long long rows,
   return cudaGetLastError();
 }
 
+bool needs_turn(int layout, int bits) { return layout != 2 || bits == 8; }
+
+cudaError_t turn_rows(const uint8_t* in, uint8_t* out, int layout, int bits, int n_inputs,
+                      int n_chans, int n_time, long long out_stride, cudaStream_t s) {
+  const int N = n_inputs, C = n_chans, T = n_time;
+  const bool eight = bits == 8;
+  const int R = eight ? 2 * N : N;
+  // [t][c][i] is one transpose of a T x (C N) byte matrix, [t][i][c] is N
+  // transposes of T x C.  8-bit samples are byte pairs: [t][c][i][p] turns as
+  // T x (C 2N); [t][i][c][p] as N transposes of T x 2C with each (c, p) row
+  // sent to row (c, i, p); [c][i][t][p] only splits the planes.
+  if (layout == 0) return turn_launch(in, out, T, 1, C * R, out_stride, s);
+  if (layout == 1)
+    return eight ? turn_launch(in, out, T, N, 2 * C, out_stride, s, true)
+                 : turn_launch(in, out, T, N, C, out_stride, s);
+  if (eight) return split_planes_launch(in, out, (long long)C * N, T, out_stride, s);
+  return cudaSuccess;
+}
+
 cudaError_t normalise_launch(const int64_t* acc, double* rho, int n_inputs, int n_chans,
                              cudaStream_t s) {
   const long long nbl = (long long)n_inputs * (n_inputs + 1) / 2;

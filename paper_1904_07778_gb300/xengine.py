@@ -225,3 +225,125 @@ class Correlator:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------------------------- batches
+EXPORTS += ["corr_batch_create", "corr_batch_input", "corr_batch_output", "corr_batch_set_input",
+            "corr_batch_get_output", "corr_batch_run", "corr_batch_run_plain", "corr_batch_sync",
+            "corr_batch_info_get", "corr_batch_destroy", "corr_plan_schedule"]
+CORR_SCHED_PAIRS_LPT, CORR_SCHED_SINGLES_LPT, CORR_SCHED_PAIRS_RR = 0, 1, 2
+
+
+class CorrShape(ctypes.Structure):
+    """Mirror of struct corr_shape."""
+    _fields_ = [("n_inputs", _I), ("n_chans", _I), ("n_time", _I), ("bits", _I), ("layout", _I),
+                ("flags", _U)]
+
+
+class CorrBatchInfo(ctypes.Structure):
+    """Mirror of struct corr_batch_info."""
+    _fields_ = [("schedule", _I), ("n_tasks", _I), ("n_ctas", _I), ("launches_per_run", _I),
+                ("tuned_ms", ctypes.c_double * 3)]
+
+
+_lib.corr_batch_create.argtypes = [ctypes.POINTER(CorrShape), _I, _P, _I, ctypes.POINTER(_P)]
+_lib.corr_batch_input.argtypes = [_P, _I]
+_lib.corr_batch_input.restype = _P
+_lib.corr_batch_output.argtypes = [_P, _I]
+_lib.corr_batch_output.restype = _P
+_lib.corr_batch_set_input.argtypes = [_P, _I, _P, _SZ]
+_lib.corr_batch_get_output.argtypes = [_P, _I, _P]
+_lib.corr_batch_run.argtypes = [_P]
+_lib.corr_batch_run_plain.argtypes = [_P]
+_lib.corr_batch_sync.argtypes = [_P]
+_lib.corr_batch_info_get.argtypes = [_P, ctypes.POINTER(CorrBatchInfo)]
+_lib.corr_batch_destroy.argtypes = [_P]
+_lib.corr_batch_destroy.restype = None
+_lib.corr_plan_schedule.argtypes = [_P, _I, _I, _P, _P]
+for _f in ("corr_batch_create", "corr_batch_set_input", "corr_batch_get_output", "corr_batch_run",
+           "corr_batch_run_plain", "corr_batch_sync", "corr_batch_info_get", "corr_plan_schedule"):
+    getattr(_lib, _f).restype = _I
+
+
+def corr_plan_schedule(cost, n_ctas):
+    """Longest-first assignment of tasks to CTAs (host only): (order, cta_first)."""
+    c = np.ascontiguousarray(np.asarray(cost, dtype=np.float64))
+    order = np.empty(c.size, dtype=np.int32)
+    first = np.empty(n_ctas + 1, dtype=np.int32)
+    st = _lib.corr_plan_schedule(c.ctypes.data, c.size, n_ctas, order.ctypes.data,
+                                 first.ctypes.data)
+    if st != CORR_OK:
+        raise CorrError(st, "corr_plan_schedule")
+    return order, first
+
+
+class Batch:
+    """Several arrays correlated by one persistent launch per run (corr_batch_*).
+
+    ``shapes`` is a list of (n_inputs, n_chans, n_time, bits, layout[, flags])."""
+
+    def __init__(self, shapes, tune=False, stream=None):
+        arr = (CorrShape * len(shapes))()
+        for k, sh in enumerate(shapes):
+            n, c, t, bits, layout = sh[:5]
+            flags = sh[5] if len(sh) > 5 else 0
+            arr[k] = CorrShape(n, c, t, bits, layout, flags)
+        self.shapes = [tuple(s[:5]) for s in shapes]
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream or _CUDA_STREAM_LEGACY
+        out = _P()
+        st = _lib.corr_batch_create(arr, len(shapes), _P(stream), 1 if tune else 0,
+                                    ctypes.byref(out))
+        if st != CORR_OK:
+            raise CorrError(st, "corr_batch_create")
+        self._b = out
+
+    def set_input(self, k, block):
+        p, n = _ptr_and_size(block)
+        st = _lib.corr_batch_set_input(self._b, k, _P(p), n)
+        if st != CORR_OK:
+            raise CorrError(st, "corr_batch_set_input")
+
+    def output(self, k):
+        n, c = self.shapes[k][0], self.shapes[k][1]
+        vis = np.empty((c, n * (n + 1) // 2, 2), dtype=np.int64)
+        st = _lib.corr_batch_get_output(self._b, k, _P(vis.ctypes.data))
+        if st != CORR_OK:
+            raise CorrError(st, "corr_batch_get_output")
+        return vis
+
+    def run(self):
+        st = _lib.corr_batch_run(self._b)
+        if st != CORR_OK:
+            raise CorrError(st, "corr_batch_run")
+
+    def run_plain(self):
+        st = _lib.corr_batch_run_plain(self._b)
+        if st != CORR_OK:
+            raise CorrError(st, "corr_batch_run_plain")
+
+    def sync(self):
+        return _lib.corr_batch_sync(self._b)
+
+    def info(self):
+        out = CorrBatchInfo()
+        st = _lib.corr_batch_info_get(self._b, ctypes.byref(out))
+        if st != CORR_OK:
+            raise CorrError(st, "corr_batch_info_get")
+        return {"schedule": out.schedule, "n_tasks": out.n_tasks, "n_ctas": out.n_ctas,
+                "launches_per_run": out.launches_per_run, "tuned_ms": list(out.tuned_ms)}
+
+    def close(self):
+        if getattr(self, "_b", None):
+            _lib.corr_batch_destroy(self._b)
+            self._b = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        self.close()

@@ -1,0 +1,103 @@
+"""Batched arrays (corr_batch_*): one persistent cross-multiply over several
+arrays of different shapes, replayed from a CUDA graph.  Every array's
+visibilities must equal the oracle's exactly, on every replay, in the plain
+one-launch-per-array form and under every autotuned schedule."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def xe():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1904_07778_gb300 import build
+    build.build()
+    from paper_1904_07778_gb300 import xengine
+    return xengine
+
+
+SHAPES4 = [  # (N, C, T, bits, layout): stacked, one block, two blocks, three blocks
+    (32, 64, 1024, 4, 0),
+    (64, 48, 512, 4, 1),
+    (20, 40, 320, 4, 2),
+    (192, 6, 256, 4, 1),
+    (100, 3, 384, 4, 0),
+]
+SHAPES8 = [(16, 8, 128, 8, 0), (48, 4, 256, 8, 1), (100, 2, 160, 8, 2)]
+
+
+def _blocks(shapes, seed):
+    rng = np.random.default_rng(seed)
+    out = []
+    for n, c, t, bits, _ in shapes:
+        if bits == 4:
+            out.append(rng.integers(0, 256, n * c * t, dtype=np.uint8))
+        else:
+            out.append(rng.integers(-127, 128, 2 * n * c * t, dtype=np.int16).astype(np.int8).view(np.uint8))
+    return out
+
+
+def _check(b, shapes, blocks):
+    for k, ((n, c, t, bits, layout), blk) in enumerate(zip(shapes, blocks)):
+        want = oracle.correlate(blk, n, c, t, bits=bits, layout=layout)
+        assert np.array_equal(b.output(k), want), (k, shapes[k])
+
+
+@pytest.mark.parametrize("shapes", [SHAPES4, SHAPES8], ids=["4bit", "8bit"])
+def test_batch_graph_replays_and_plain_form(xe, shapes):
+    with xe.Batch(shapes) as b:
+        for rep in range(2):                      # the graph replays with new data
+            blocks = _blocks(shapes, 100 + rep)
+            for k, blk in enumerate(blocks):
+                b.set_input(k, torch.from_numpy(blk).cuda() if k % 2 else blk)
+            b.run()
+            assert b.sync() == xe.CORR_OK
+            _check(b, shapes, blocks)
+        blocks = _blocks(shapes, 200)
+        for k, blk in enumerate(blocks):
+            b.set_input(k, blk)
+        b.run_plain()
+        assert b.sync() == xe.CORR_OK
+        _check(b, shapes, blocks)
+        info = b.info()
+        assert info["launches_per_run"] == 1 + sum(1 for s in shapes if s[4] != 2 or s[3] == 8)
+
+
+def test_batch_autotune_every_schedule_exact(xe):
+    blocks = _blocks(SHAPES4, 300)
+    with xe.Batch(SHAPES4, tune=True) as b:
+        info = b.info()
+        assert info["schedule"] in (0, 1, 2) and all(ms > 0 for ms in info["tuned_ms"])
+        assert info["tuned_ms"][info["schedule"]] == min(info["tuned_ms"])
+        for k, blk in enumerate(blocks):
+            b.set_input(k, blk)
+        b.run()
+        assert b.sync() == xe.CORR_OK
+        _check(b, SHAPES4, blocks)
+
+
+def test_batch_matches_single_array_contexts(xe):
+    """Each array alone through corr_create/corr_push/corr_dump gives the same."""
+    blocks = _blocks(SHAPES4, 400)
+    with xe.Batch(SHAPES4) as b:
+        for k, blk in enumerate(blocks):
+            b.set_input(k, blk)
+        b.run()
+        b.sync()
+        for k, ((n, c, t, bits, layout), blk) in enumerate(zip(SHAPES4, blocks)):
+            with xe.Correlator(n, c, t, bits=bits, layout=layout) as cor:
+                cor.push(blk)
+                assert np.array_equal(cor.dump(), b.output(k))
+
+
+def test_batch_rejects_bad_shapes(xe):
+    for shapes in ([(32, 4, 64, 4, 0), (32, 4, 64, 8, 0)],      # mixed bits
+                   [(32, 4, 70000, 4, 0)],                        # longer than one accumulation
+                   [(32, 4, 40, 4, 2)]):                          # unaligned rows in place
+        with pytest.raises(xe.CorrError):
+            xe.Batch(shapes)
