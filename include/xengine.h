@@ -307,6 +307,93 @@ void corr_batch_destroy(corr_batch* b);
  */
 int corr_plan_schedule(const double* cost, int n_tasks, int n_ctas, int* order, int* cta_first);
 
+/*
+ * Streaming service: continuous batching of integration requests.
+ *
+ * The paper's pipeline integrates for a pre-set duration and then dumps
+ * (Sec. 2, Sec. 2.2).  The service generalises that to many concurrent
+ * integrations of different arrays and lengths sharing one GPU: each request
+ * asks for n_blocks blocks of block_spectra spectra of one array.  Requests
+ * are admitted in arrival order while their device state (int64 accumulator,
+ * two ingest buffers, the corner-turn buffer) fits in a fixed HBM budget,
+ * carved out of one allocation made at creation.  Every tick correlates the
+ * pending block of every active request in one persistent launch (one per
+ * sample width), so requests that arrive while others run join the next
+ * tick; a request's blocks are copied in on a second stream while the
+ * previous tick computes.  When its last block is integrated the request is
+ * done; corr_svc_fetch copies its visibilities out and frees its memory,
+ * which admits queued requests.  Latency = submit to done (host clock, the
+ * completion observed by a host callback on the stream).
+ *
+ * Not thread-safe: one host thread drives a service.
+ */
+typedef struct corr_svc corr_svc; /* opaque, owned by the library */
+
+typedef struct corr_req {
+  int n_inputs;       /* N, 1 <= N <= 1024                              */
+  int n_chans;        /* C >= 1                                         */
+  int bits;           /* 4 or 8                                         */
+  int layout;         /* CORR_L_*                                       */
+  unsigned flags;     /* CORR_F_*                                       */
+  int block_spectra;  /* spectra per block, <= 65536 (4-bit), 32768 (8-bit); for CORR_L_CIT
+                         at 4 bits a multiple of 16 */
+  int64_t n_blocks;   /* blocks to integrate, >= 1                      */
+} corr_req;
+
+#define CORR_SVC_DRY_RUN 1u /* host logic only: no device memory, no kernels (tests) */
+
+#define CORR_REQ_QUEUED 0   /* waiting for memory                        */
+#define CORR_REQ_ACTIVE 1   /* admitted: accepts blocks                  */
+#define CORR_REQ_DONE 2     /* every block integrated; fetch the result  */
+#define CORR_REQ_FETCHED 3  /* result copied out, memory released        */
+
+typedef struct corr_svc_stats {
+  uint64_t submitted, admitted, completed, fetched;
+  uint64_t ticks;            /* corr_svc_tick calls that launched work    */
+  uint64_t launches;         /* kernels launched by ticks                  */
+  uint64_t blocks;           /* blocks integrated                          */
+  double chan_spectra;       /* sum over integrated blocks of C x spectra  */
+  double ops;                /* correlator ops integrated (8 N(N+1)/2 C T) */
+  double p50_ms, p99_ms, max_ms; /* submit-to-done latency of done requests */
+  uint64_t budget, in_use, peak_in_use; /* bytes of the HBM budget         */
+  int active, queued;
+} corr_svc_stats;
+
+/* corr_svc_create -- a service with hbm_budget bytes of device state (one
+ * allocation now).  flags: CORR_SVC_DRY_RUN or 0.  stream as for batches. */
+int corr_svc_create(size_t hbm_budget, unsigned flags, void* stream, corr_svc** out);
+
+/* corr_svc_submit -- queue a request; it is admitted at once if its state
+ * fits.  *id receives its handle.  CORR_EINVAL for a bad shape, CORR_EBUSY if
+ * it could never fit the budget. */
+int corr_svc_submit(corr_svc* s, const corr_req* r, int64_t* id);
+
+/* corr_svc_state -- CORR_REQ_* of a request.  CORR_EINVAL for an unknown id. */
+int corr_svc_state(corr_svc* s, int64_t id, int* state);
+
+/* corr_svc_push -- the request's next block (host or device memory, N C T
+ * bits/4 bytes in its layout), copied in on the ingest stream.  CORR_ESTATE
+ * unless the request is active and still expects blocks; CORR_EBUSY while two
+ * pushed blocks are waiting for ticks. */
+int corr_svc_push(corr_svc* s, int64_t id, const void* block, size_t nbytes);
+
+/* corr_svc_tick -- correlate the oldest waiting block of every active
+ * request in one launch per sample width.  *n_requests (optional) receives
+ * how many requests took part.  Asynchronous. */
+int corr_svc_tick(corr_svc* s, int* n_requests);
+
+/* corr_svc_fetch -- for a done request: copy its visibilities (int64
+ * [C][N(N+1)/2][2], host or device; NULL to discard), release its memory and
+ * admit queued requests.  CORR_ESTATE if it is not done yet. */
+int corr_svc_fetch(corr_svc* s, int64_t id, int64_t* vis);
+
+/* corr_svc_wait -- wait for the work queued so far; returns a pending device
+ * status once (CORR_ERANGE, CORR_ETIMEDOUT), else CORR_OK. */
+int corr_svc_wait(corr_svc* s);
+
+int corr_svc_stats_get(corr_svc* s, corr_svc_stats* out);
+void corr_svc_destroy(corr_svc* s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libxengine.so")
-SOURCES = ["xe_herk.cu", "xe_turn.cu", "xe_runtime.cu", "xe_noalloc.cu", "xe_batch.cu"]
+SOURCES = ["xe_herk.cu", "xe_turn.cu", "xe_runtime.cu", "xe_noalloc.cu", "xe_batch.cu", "xe_service.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -347,3 +347,128 @@ class Batch:
 
     def __del__(self):
         self.close()
+
+
+# ------------------------------------------------------------------- service
+EXPORTS += ["corr_svc_create", "corr_svc_submit", "corr_svc_state", "corr_svc_push", "corr_svc_tick",
+            "corr_svc_fetch", "corr_svc_wait", "corr_svc_stats_get", "corr_svc_destroy"]
+CORR_SVC_DRY_RUN = 1
+CORR_REQ_QUEUED, CORR_REQ_ACTIVE, CORR_REQ_DONE, CORR_REQ_FETCHED = 0, 1, 2, 3
+
+
+class CorrReq(ctypes.Structure):
+    """Mirror of struct corr_req."""
+    _fields_ = [("n_inputs", _I), ("n_chans", _I), ("bits", _I), ("layout", _I), ("flags", _U),
+                ("block_spectra", _I), ("n_blocks", ctypes.c_int64)]
+
+
+class CorrSvcStats(ctypes.Structure):
+    """Mirror of struct corr_svc_stats."""
+    _fields_ = [(n, ctypes.c_uint64) for n in ("submitted", "admitted", "completed", "fetched",
+                                                "ticks", "launches", "blocks")] + \
+               [(n, ctypes.c_double) for n in ("chan_spectra", "ops", "p50_ms", "p99_ms", "max_ms")] + \
+               [(n, ctypes.c_uint64) for n in ("budget", "in_use", "peak_in_use")] + \
+               [("active", _I), ("queued", _I)]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+_lib.corr_svc_create.argtypes = [_SZ, _U, _P, ctypes.POINTER(_P)]
+_lib.corr_svc_submit.argtypes = [_P, ctypes.POINTER(CorrReq), ctypes.POINTER(ctypes.c_int64)]
+_lib.corr_svc_state.argtypes = [_P, ctypes.c_int64, ctypes.POINTER(_I)]
+_lib.corr_svc_push.argtypes = [_P, ctypes.c_int64, _P, _SZ]
+_lib.corr_svc_tick.argtypes = [_P, ctypes.POINTER(_I)]
+_lib.corr_svc_fetch.argtypes = [_P, ctypes.c_int64, _P]
+_lib.corr_svc_wait.argtypes = [_P]
+_lib.corr_svc_stats_get.argtypes = [_P, ctypes.POINTER(CorrSvcStats)]
+_lib.corr_svc_destroy.argtypes = [_P]
+_lib.corr_svc_destroy.restype = None
+for _f in ("corr_svc_create", "corr_svc_submit", "corr_svc_state", "corr_svc_push", "corr_svc_tick",
+           "corr_svc_fetch", "corr_svc_wait", "corr_svc_stats_get"):
+    getattr(_lib, _f).restype = _I
+
+
+class Service:
+    """Continuous batching of integration requests (corr_svc_*)."""
+
+    def __init__(self, hbm_budget, dry_run=False, stream=None):
+        if stream is None and not dry_run:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream or _CUDA_STREAM_LEGACY
+        out = _P()
+        st = _lib.corr_svc_create(int(hbm_budget), CORR_SVC_DRY_RUN if dry_run else 0,
+                                  _P(stream or 0), ctypes.byref(out))
+        if st != CORR_OK:
+            raise CorrError(st, "corr_svc_create")
+        self._s = out
+        self._shape = {}
+
+    def submit(self, n_inputs, n_chans, bits, layout, block_spectra, n_blocks, flags=0, check=True):
+        rid = ctypes.c_int64()
+        r = CorrReq(n_inputs, n_chans, bits, layout, flags, block_spectra, n_blocks)
+        st = _lib.corr_svc_submit(self._s, ctypes.byref(r), ctypes.byref(rid))
+        if st != CORR_OK:
+            if check:
+                raise CorrError(st, "corr_svc_submit")
+            return st
+        self._shape[rid.value] = (n_inputs, n_chans)
+        return rid.value
+
+    def state(self, rid):
+        out = _I()
+        st = _lib.corr_svc_state(self._s, rid, ctypes.byref(out))
+        if st != CORR_OK:
+            raise CorrError(st, "corr_svc_state")
+        return out.value
+
+    def push(self, rid, block, check=True):
+        p, n = _ptr_and_size(block)
+        st = _lib.corr_svc_push(self._s, rid, _P(p), n)
+        if check and st != CORR_OK:
+            raise CorrError(st, "corr_svc_push")
+        return st
+
+    def tick(self):
+        n = _I()
+        st = _lib.corr_svc_tick(self._s, ctypes.byref(n))
+        if st != CORR_OK:
+            raise CorrError(st, "corr_svc_tick")
+        return n.value
+
+    def fetch(self, rid, vis=None, check=True):
+        """Copy a done request's visibilities into ``vis`` (or a new array)."""
+        if vis is None and rid in self._shape:
+            n, c = self._shape[rid]
+            vis = np.empty((c, n * (n + 1) // 2, 2), dtype=np.int64)
+        p = _ptr_and_size(vis)[0] if vis is not None else 0
+        st = _lib.corr_svc_fetch(self._s, rid, _P(p))
+        if st != CORR_OK:
+            if check:
+                raise CorrError(st, "corr_svc_fetch")
+            return st
+        return vis
+
+    def wait(self):
+        return _lib.corr_svc_wait(self._s)
+
+    def stats(self):
+        out = CorrSvcStats()
+        st = _lib.corr_svc_stats_get(self._s, ctypes.byref(out))
+        if st != CORR_OK:
+            raise CorrError(st, "corr_svc_stats_get")
+        return out.as_dict()
+
+    def close(self):
+        if getattr(self, "_s", None):
+            _lib.corr_svc_destroy(self._s)
+            self._s = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        self.close()
