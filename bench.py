@@ -57,6 +57,14 @@ WORKLOADS["batch3"] = dict(
          "(inputs x channels x spectra), 4-bit complex, [time][channel][input] order, "
          "i.i.d. Gaussian sigma 2.5, one persistent cross-multiply per run",
     batch=BATCH3, layout=0, kind="gauss")
+# Streaming service: integration requests over mixed arrays arriving as a
+# Poisson process, admitted by an HBM budget, continuously batched.
+WORKLOADS["service4"] = dict(
+    desc="streaming service: requests over 32/192/512-input arrays x 2048 channels, 8-bit "
+         "complex (sigma 20, clip 127), 2^k spectra with k uniform in 12..18, 4096-spectrum "
+         "blocks, Poisson arrivals at 80% of measured capacity, admitted by an HBM budget",
+    service=dict(arrays=[32, 192, 512], C=2048, bits=8, layout=0, kmin=12, kmax=18,
+                 block=4096, requests=200, load=0.8, budget_gb=170))
 METRIC = "X-engine correlator Tops/s at 192 inputs (8 int ops per complex MAC, lower triangle incl. autos)"
 PAPER_TOPS = 1.2  # xGPU on one GTX 690 core, >= 96 dual-pol stations (Sec. 2.2); context only
 REAL_TIME_RATE = 125e6  # spectra x channels per second per input at 250 MSPS real sampling
@@ -426,6 +434,116 @@ def run_batch(args, w, world, rank, local):
     return 0
 
 
+def run_service(args, w, world, rank, local):
+    """Poisson request stream through the continuous-batching service."""
+    import numpy as np
+    import torch
+    from paper_1904_07778_gb300 import build, synth
+    build.build()
+    from paper_1904_07778_gb300.xengine import CORR_OK, CORR_REQ_ACTIVE, CORR_REQ_DONE, Service
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    cfg = w["service"]
+    C, bits, layout, blk_t = cfg["C"], cfg["bits"], cfg["layout"], cfg["block"]
+    n_req = args.service_requests or cfg["requests"]
+    # sample data, generated once on the device (outside the timing) and
+    # reused cyclically: two blocks per array
+    data = {n: [synth.block_device("gauss", 40 + 10 * n + s_, n, C, blk_t, layout, dev, bits=bits)
+                for s_ in range(2)] for n in cfg["arrays"]}
+    outs = {n: torch.empty((C, n * (n + 1) // 2, 2), dtype=torch.int64, device=dev)
+            for n in cfg["arrays"]}
+    torch.cuda.synchronize()
+    svc = Service(int(cfg["budget_gb"] * 2**30))
+
+    def drain(ids):
+        """Push and tick until every request in ids is done and fetched."""
+        left = dict(ids)  # id -> [n, blocks pushed, n_blocks]
+        while left:
+            for rid, st_ in list(left.items()):
+                n, pushed, nb = st_
+                if pushed < nb and svc.state(rid) == CORR_REQ_ACTIVE:
+                    if svc.push(rid, data[n][pushed & 1], check=False) == CORR_OK:
+                        st_[1] += 1
+            svc.tick()
+            for rid, st_ in list(left.items()):
+                if svc.state(rid) == CORR_REQ_DONE:
+                    svc.fetch(rid, outs[st_[0]])
+                    del left[rid]
+
+    # capacity: each array alone, 3 blocks (after one warm-up request)
+    per_block = {}
+    for n in cfg["arrays"]:
+        drain({svc.submit(n, C, bits, layout, blk_t, 1): [n, 0, 1]})
+        svc.wait()
+        t0 = time.perf_counter()
+        drain({svc.submit(n, C, bits, layout, blk_t, 3): [n, 0, 3]})
+        svc.wait()
+        per_block[n] = (time.perf_counter() - t0) / 3
+    rng = np.random.default_rng(2024)
+    arrays = rng.choice(cfg["arrays"], size=n_req)
+    ks = rng.integers(cfg["kmin"], cfg["kmax"] + 1, size=n_req)
+    nblocks = [max(1, (1 << int(k)) // blk_t) for k in ks]
+    mean_s = float(np.mean([per_block[int(n)] * nb for n, nb in zip(arrays, nblocks)]))
+    rate = cfg["load"] / mean_s  # requests per second
+    arrive = np.cumsum(rng.exponential(1.0 / rate, size=n_req))
+    s0 = svc.stats()
+    sampler = ClockSampler(local) if not args.no_clocks else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    t0 = time.perf_counter()
+    live = {}  # id -> [n, pushed, n_blocks]
+    nxt = 0
+    while nxt < n_req or live:
+        now = time.perf_counter() - t0
+        while nxt < n_req and arrive[nxt] <= now:
+            n = int(arrays[nxt])
+            live[svc.submit(n, C, bits, layout, blk_t, nblocks[nxt])] = [n, 0, nblocks[nxt]]
+            nxt += 1
+        for rid, st_ in live.items():
+            n, pushed, nb = st_
+            if pushed < nb and svc.state(rid) == CORR_REQ_ACTIVE:
+                if svc.push(rid, data[n][pushed & 1], check=False) == CORR_OK:
+                    st_[1] += 1
+        launched = svc.tick()
+        for rid in [r for r, st_ in live.items() if svc.state(r) == CORR_REQ_DONE]:
+            svc.fetch(rid, outs[live[rid][0]])
+            del live[rid]
+        if not launched and not live and nxt < n_req:
+            time.sleep(max(0.0, min(0.01, arrive[nxt] - (time.perf_counter() - t0))))
+    svc.wait()
+    wall = time.perf_counter() - t0
+    clocks = sampler.stop() if sampler else None
+    st = svc.stats()
+    svc.close()
+    if rank != 0:
+        return 0
+    ops = st["ops"] - s0["ops"]
+    chs = st["chan_spectra"] - s0["chan_spectra"]
+    # latency percentiles of the Poisson requests only (the calibration ran first)
+    alone_tops = {str(n): 8 * n * (n + 1) // 2 * C * blk_t / per_block[n] / 1e12 for n in cfg["arrays"]}
+    line = {
+        "metric": "X-engine streaming service: sustained x real time and p50/p99 dump latency",
+        "value": chs / REAL_TIME_RATE / wall, "unit": "x real time (250 MSPS)",
+        "n_gpus": world, "steps": n_req, "warmup": len(cfg["arrays"]) * 2,
+        "ms_per_step": 1e3 * wall / n_req, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8", "data": "synthetic (seeded Gaussian, device-generated, "
+        "two blocks per array reused cyclically)",
+        "config": {"workload": w["desc"], "requests": n_req, "budget_gb": cfg["budget_gb"],
+                   "arrival_rate_per_s": rate, "mean_request_gpu_s": mean_s},
+        "throughput_tops": ops / wall / 1e12,
+        "latency_ms": {"p50": st["p50_ms"], "p99": st["p99_ms"], "max": st["max_ms"],
+                       "note": "submit to done, all requests incl. 6 calibration ones"},
+        "alone_tops_per_array": alone_tops, "ms_per_block_alone": {str(n): 1e3 * v for n, v in per_block.items()},
+        "service": {k: st[k] for k in ("submitted", "completed", "ticks", "launches", "blocks",
+                                       "peak_in_use", "budget")},
+        "gpu_launches": st["launches"] - s0["launches"], "wall_s": wall, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -438,6 +556,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--service-requests", type=int, default=0,
+                    help="requests of the service workload (default: its configured count)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -447,6 +567,8 @@ def main():
         rc = run_reference(args, w, world, rank)
     elif "batch" in w:
         rc = run_batch(args, w, world, rank, local)
+    elif "service" in w:
+        rc = run_service(args, w, world, rank, local)
     else:
         rc = run_gpu(args, w, world, rank, local)
     if world > 1:
