@@ -110,6 +110,16 @@ __device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr) {
   d |= (uint64_t)2 << 61;             // 128-byte swizzle
   return d;
 }
+// The same for rows of 64 bytes: 8-row atoms of 512 bytes, 16-byte chunk c of
+// row r stored at chunk position c ^ ((r >> 1) & 3); atoms on 512-byte boundaries.
+__device__ __forceinline__ uint64_t umma_desc_sw64(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;             // leading-dimension offset (unused here)
+  d |= (uint64_t)(512 >> 4) << 32;    // stride between 8-row atoms
+  d |= (uint64_t)1 << 46;             // descriptor version
+  d |= (uint64_t)4 << 61;             // 64-byte swizzle
+  return d;
+}
 // Instruction descriptor: FP32 accumulate, K-major A and B, M x N.
 // fmt 0 = E4M3 (kind::f8f6f4) or F16 (kind::f16).
 __host__ __device__ constexpr uint32_t umma_idesc(uint32_t fmt, int m, int n) {
@@ -207,6 +217,14 @@ __device__ __forceinline__ void regs_grow() {
 template <int R>
 __device__ __forceinline__ void regs_shrink() {
   asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(R));
+}
+
+// Add an int64 pair into global memory without waiting for it: two
+// reductions performed at L2 (two's-complement addition modulo 2^64 is the
+// same for signed values).
+__device__ __forceinline__ void red_s64x2(int64_t* p, long long x, long long y) {
+  asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(x) : "memory");
+  asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(p + 1), "l"(y) : "memory");
 }
 
 // Named barrier that also ANDs a flag over the participating threads: every

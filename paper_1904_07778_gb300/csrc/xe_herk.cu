@@ -123,24 +123,23 @@ __device__ __forceinline__ void time_keep(int tk, int tn, uint32_t (&keep)[4]) {
   }
 }
 
-// Row sums: the eight lanes of a pair hold its eight 16-spectrum chunks;
-// item it of a thread covers pair it * (NT / 8) + tid / 8.  Partial sums of
+// Row sums: the CH lanes of a pair hold its CH 16-spectrum chunks; item it
+// of a thread covers pair it * (NT / CH) + tid / CH.  Partial sums of
 // several unpack groups are added with shared-memory atomics.
-template <int NT, int NI>
+template <int NT, int NI, int CH = 8>
 __device__ __forceinline__ void publish_row_sums(int32_t (&sre)[NI], int32_t (&sim)[NI], int nit,
                                                  int tid, int32_t* usum) {
 #pragma unroll
   for (int it = 0; it < NI; ++it) {
     if (it < nit) {
       int r = sre[it], m = sim[it];
-      r += __shfl_xor_sync(0xFFFFFFFFu, r, 1);
-      r += __shfl_xor_sync(0xFFFFFFFFu, r, 2);
-      r += __shfl_xor_sync(0xFFFFFFFFu, r, 4);
-      m += __shfl_xor_sync(0xFFFFFFFFu, m, 1);
-      m += __shfl_xor_sync(0xFFFFFFFFu, m, 2);
-      m += __shfl_xor_sync(0xFFFFFFFFu, m, 4);
-      if ((tid & 7) == 0) {
-        const int pair = it * (NT / 8) + (tid >> 3);
+#pragma unroll
+      for (int x = 1; x < CH; x <<= 1) {
+        r += __shfl_xor_sync(0xFFFFFFFFu, r, x);
+        m += __shfl_xor_sync(0xFFFFFFFFu, m, x);
+      }
+      if ((tid & (CH - 1)) == 0) {
+        const int pair = it * (NT / CH) + tid / CH;
         atomicAdd(&usum[(pair >> 6) * 128 + (pair & 63) * 2], r);
         atomicAdd(&usum[(pair >> 6) * 128 + (pair & 63) * 2 + 1], m);
       }
@@ -261,18 +260,10 @@ __device__ __forceinline__ void epilogue(const HerkInst& a, const HerkTask& task
       off[u] = ok ? 2 * b : -1;
     }
     if (a.accumulate) {
+      // reductions at L2: nothing waits for the old value
 #pragma unroll
-      for (int h = 0; h < 4; h += 2) {  // two read-modify-writes in flight
-        long long ore[2], oim[2];
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          ore[u] = oim[u] = 0;
-          if (off[h + u] >= 0) ld_s64x2(chp + off[h + u], ore[u], oim[u]);
-        }
-#pragma unroll
-        for (int u = 0; u < 2; ++u)
-          if (off[h + u] >= 0) st_s64x2(chp + off[h + u], ore[u] + vre[h + u], oim[u] + vim[h + u]);
-      }
+      for (int u = 0; u < 4; ++u)
+        if (off[u] >= 0) red_s64x2(chp + off[u], vre[u], vim[u]);
     } else {
 #pragma unroll
       for (int u = 0; u < 4; ++u)
@@ -376,9 +367,7 @@ __device__ __forceinline__ void epilogue8(const HerkInst& a, const HerkTask& tas
     if (ok) {
       int64_t* d = chp + 2 * b;
       if (a.accumulate) {
-        long long ore, oim;
-        ld_s64x2(d, ore, oim);
-        st_s64x2(d, ore + vre, oim + vim);
+        red_s64x2(d, vre, vim);  // reduction at L2: nothing waits for the old value
       } else {
         st_s64x2(d, vre, vim);
       }
@@ -444,8 +433,28 @@ constexpr int kGroups = XE_GROUPS;            // unpack groups (stages S = g mod
 constexpr int kGroupWarps = 16 / kGroups;
 constexpr int kGroupThreads = kGroupWarps * 32;
 constexpr int kUnpackWarps = kGroups * kGroupWarps;
-constexpr int kItems = kMaxBlocks * 512 / kGroupThreads;  // 16-byte items per thread per stage
-constexpr int kPairsPerItem = kGroupThreads / 8;           // inputs covered per item index
+// Ring stages: kRStageT spectra (128: 128-byte-swizzled operand rows; 64:
+// 64-byte-swizzled rows and twice the slots for the same shared memory).
+#ifndef XE_STAGE_T
+#define XE_STAGE_T 128
+#endif
+constexpr int kRStageT = XE_STAGE_T;
+static_assert(kRStageT == 128 || kRStageT == 64, "stage of 128 or 64 spectra");
+constexpr int kROpBlock = 128 * kRStageT;  // unpacked 128-row block of a stage
+constexpr int kRPkBlock = 64 * kRStageT;   // packed 64-input block of a stage
+constexpr int kRChunks = kRStageT / 16;    // 16-byte chunks per row
+constexpr int kRKSteps = kRStageT / 32;    // K = 32 MMAs per stage
+constexpr int kItems = kMaxBlocks * 64 * kRChunks / kGroupThreads;  // 16-byte items per thread
+constexpr int kPairsPerItem = kGroupThreads / kRChunks;             // inputs per item index
+
+// Byte offset of 16-byte chunk c of row r in a swizzled operand block.
+__device__ __forceinline__ uint32_t op_offset(int r, int c) {
+  const int sw = kRStageT == 128 ? (r & 7) : ((r >> 1) & 3);
+  return (uint32_t)((r >> 3) * (8 * kRStageT) + (r & 7) * kRStageT + ((c ^ sw) << 4));
+}
+__device__ __forceinline__ uint64_t op_desc(uint32_t saddr) {
+  return kRStageT == 128 ? umma_desc_sw128(saddr) : umma_desc_sw64(saddr);
+}
 constexpr int kMmaWarp = kUnpackWarps, kTmaWarp = kUnpackWarps + 1, kEpiWarp0 = kUnpackWarps + 4;
 constexpr int kEpiWarps = XE_EPI_WARPS;
 constexpr int kRingThreads = (kEpiWarp0 + kEpiWarps) * 32;
@@ -485,7 +494,7 @@ __device__ __forceinline__ HerkInst task_inst(const HerkArgs& a, const HerkTask&
   return a.insts ? a.insts[t.inst] : a.in;
 }
 __device__ __forceinline__ int stages_of(const HerkInst& in) {
-  return (in.tn + kStageT - 1) / kStageT;
+  return (in.tn + kRStageT - 1) / kRStageT;
 }
 
 template <bool LO_IS_REAL, bool EIGHT>
@@ -499,7 +508,7 @@ __global__ void __launch_bounds__(kRingThreads, 1)
   uint8_t* ring = align1024(dyn_raw);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int n_my = my_task_count(a);  // tasks of this CTA; stage counts vary per array
-  const int slot_bytes = a.max_nblk * kOpBlockBytes;
+  const int slot_bytes = a.max_nblk * kROpBlock;
   int ns = (int)(reinterpret_cast<uint8_t*>(&sm) - ring) / slot_bytes;
   if (ns > kMaxSlots) ns = kMaxSlots;
   if (ns < kGroups) {  // the host sizes shared memory for at least four slots
@@ -562,11 +571,11 @@ __global__ void __launch_bounds__(kRingThreads, 1)
           raise_timeout(a.status, abort);
           break;
         }
-        const int t = in.t0 + k * kStageT;
-        const uint32_t dst0 = ring_addr + (uint32_t)(s * slot_bytes + g.nblk * kPkBlockBytes);
-        mbar_expect_tx(&sm.full_t[s], (uint32_t)(g.nblk * kPkBlockBytes));
+        const int t = in.t0 + k * kRStageT;
+        const uint32_t dst0 = ring_addr + (uint32_t)(s * slot_bytes + g.nblk * kRPkBlock);
+        mbar_expect_tx(&sm.full_t[s], (uint32_t)(g.nblk * kRPkBlock));
         for (int b = 0; b < g.nblk; ++b) {
-          const uint32_t dst = dst0 + (uint32_t)(b * kPkBlockBytes);
+          const uint32_t dst = dst0 + (uint32_t)(b * kRPkBlock);
           if (stacked)
             tma_load_3d(dst, tm, t, 0, task.chan0, &sm.full_t[s]);
           else
@@ -610,10 +619,10 @@ __global__ void __launch_bounds__(kRingThreads, 1)
           }
           tc_after_sync();
           const uint32_t st = ring_addr + (uint32_t)(s * slot_bytes);
-          const uint64_t adesc = umma_desc_sw128(st + (uint32_t)(g.a_slot * kOpBlockBytes));
-          const uint64_t bdesc = umma_desc_sw128(st);
+          const uint64_t adesc = op_desc(st + (uint32_t)(g.a_slot * kROpBlock));
+          const uint64_t bdesc = op_desc(st);
 #pragma unroll
-          for (int kk = 0; kk < 4; ++kk)
+          for (int kk = 0; kk < kRKSteps; ++kk)
             umma_f8(d, adesc + 2 * kk, bdesc + 2 * kk, idesc, (k | kk) != 0);
           umma_commit(&sm.empty[s]);
           if (++s == ns) {
@@ -633,11 +642,12 @@ __global__ void __launch_bounds__(kRingThreads, 1)
     regs_grow<kRegsUnpack>();
     const int grp = warp / kGroupWarps;
     const int gt = tid - grp * kGroupThreads;
-    const int chunk = gt & 7, g8 = gt >> 3;
-    const uint32_t src0 = ring_addr + (uint32_t)(128 * g8 + 16 * chunk);
-    const int rre = (2 * g8) & 7, rim = (2 * g8 + 1) & 7;
-    const uint32_t dst_re = ring_addr + (uint32_t)((g8 >> 2) * 1024 + rre * 128 + ((chunk ^ rre) << 4));
-    const uint32_t dst_im = ring_addr + (uint32_t)((g8 >> 2) * 1024 + rim * 128 + ((chunk ^ rim) << 4));
+    const int chunk = gt % kRChunks, g8 = gt / kRChunks;  // this thread's chunk and pair
+    const uint32_t src0 = ring_addr + (uint32_t)(kRStageT * g8 + 16 * chunk);
+    // rows 2 g8 and 2 g8 + 1; later items add whole 8-row atoms, so the
+    // swizzle position stays the same
+    const uint32_t dst_re = ring_addr + op_offset(2 * g8, chunk);
+    const uint32_t dst_im = ring_addr + op_offset(2 * g8 + 1, chunk);
     bool ok = true;
     // next stage of this group, its slot s = S mod ns and use m = S / ns,
     // advanced by additions (kGroups <= ns)
@@ -649,8 +659,8 @@ __global__ void __launch_bounds__(kRingThreads, 1)
       const HerkTask task = my_task(a, j);
       const TaskGeom g = task_geom(task);
       const int tn = task_inst(a, task).tn;
-      const int S1 = S0 + (tn + kStageT - 1) / kStageT;
-      const int nit = g.nblk * 512 / kGroupThreads;
+      const int S1 = S0 + (tn + kRStageT - 1) / kRStageT;
+      const int nit = g.nblk * 64 * kRChunks / kGroupThreads;
       int32_t sre[kItems], sim[kItems];
 #pragma unroll
       for (int it = 0; it < kItems; ++it) sre[it] = sim[it] = 0;
@@ -661,14 +671,14 @@ __global__ void __launch_bounds__(kRingThreads, 1)
                    mbar_wait(&sm.full_t[s], (uint32_t)(m & 1), abort);
         if (!got) raise_timeout(a.status, abort);
         const uint32_t so = (uint32_t)(s * slot_bytes);
-        const uint32_t src = src0 + so + (uint32_t)(g.nblk * kPkBlockBytes);
-        const bool tail = (k + 1) * kStageT > tn;
+        const uint32_t src = src0 + so + (uint32_t)(g.nblk * kRPkBlock);
+        const bool tail = (k + 1) * kRStageT > tn;
         uint32_t keep[4] = {~0u, ~0u, ~0u, ~0u};
-        if (tail) time_keep(k * kStageT + chunk * 16, tn, keep);
+        if (tail) time_keep(k * kRStageT + chunk * 16, tn, keep);
         uint4 v[kItems];
 #pragma unroll
         for (int it = 0; it < kItems; ++it)
-          if (it < nit && got) v[it] = lds128(src + (uint32_t)(128 * kPairsPerItem * it));
+          if (it < nit && got) v[it] = lds128(src + (uint32_t)(kRStageT * kPairsPerItem * it));
         // every packed byte of the stage is in registers before any is
         // overwritten; the group leaves together if any of its waits failed
         if (!named_bar_and(2 + grp, kGroupThreads, got)) {
@@ -689,7 +699,7 @@ __global__ void __launch_bounds__(kRingThreads, 1)
                 bad |= (z - 0x01010101u) & ~z & 0x80808080u;
               }
             }
-            const uint32_t o = so + (uint32_t)(256 * kPairsPerItem * it);
+            const uint32_t o = so + (uint32_t)(2 * kRStageT * kPairsPerItem * it);
             sts128(dst_re + o, re[0], re[1], re[2], re[3]);
             sts128(dst_im + o, im[0], im[1], im[2], im[3]);
           }
@@ -708,7 +718,7 @@ __global__ void __launch_bounds__(kRingThreads, 1)
       const bool freed = j < 2 || mbar_wait(&sm.usum_empty[b], (uint32_t)(((j >> 1) - 1) & 1), abort);
       if (!freed) raise_timeout(a.status, abort);
       if (!named_bar_and(2 + grp, kGroupThreads, freed)) break;
-      publish_row_sums<kGroupThreads>(sre, sim, nit, gt, sm.usum[b]);
+      publish_row_sums<kGroupThreads, kItems, kRChunks>(sre, sim, nit, gt, sm.usum[b]);
       __syncwarp();
       if (lane == 0) mbar_arrive(&sm.usum_full[b]);
       S0 = S1;
@@ -918,6 +928,8 @@ cudaError_t ring_launch(const HerkArgs& a, const CUtensorMap* tmap, int grid, cu
 
 }  // namespace
 
+int herk_ring_stage() { return kRStageT; }
+
 int herk4_max_smem() {
   int m = max_dyn_smem((const void*)herk4_ldg_kernel<false>);
   m = std::min(m, max_dyn_smem((const void*)herk4_ldg_kernel<true>));
@@ -931,7 +943,7 @@ cudaError_t herk4_launch(const HerkArgs& args, const CUtensorMap* tmap, int n_ta
     HerkArgs a = args;
     a.smem_bytes = ring_smem();
     // four slots of the largest stage, the control block and the alignment pad
-    if (a.smem_bytes < kGroups * a.max_nblk * kOpBlockBytes + (int)sizeof(RingCtrl) + 1024)
+    if (a.smem_bytes < kGroups * a.max_nblk * kROpBlock + (int)sizeof(RingCtrl) + 1024)
       return cudaErrorInvalidConfiguration;
     int grid;
     if (a.cta_first) {

@@ -79,6 +79,8 @@ constexpr int kMaxChunk4 = 65536;
 constexpr int kMaxChunk8 = 32768;
 
 int herk4_max_smem();
+// Spectra per stage of the ring kernel: the time extent of its TMA boxes.
+int herk_ring_stage();
 // Launch the cross-multiply.  Batched (a.insts and a.tmaps set): the ring
 // kernel over every array's tasks in one persistent launch.  Otherwise tmap
 // describes a.in.x as a 3-D byte tensor {time (inner), byte row, channel} for
@@ -87,8 +89,9 @@ int herk4_max_smem();
 cudaError_t herk4_launch(const HerkArgs& a, const CUtensorMap* tmap, int n_tasks, cudaStream_t s);
 
 // Build the tensor map of a [channel][input][time] byte array with rows of
-// row_stride bytes (a multiple of 16, base 16-byte aligned).  Box: 128
-// spectra x box_inputs x box_chans.  Returns false if the driver rejects it.
+// row_stride bytes (a multiple of 16, base 16-byte aligned).  Box:
+// herk_ring_stage() spectra x box_inputs x box_chans.  Returns false if the
+// driver rejects it.
 bool make_sample_tmap(CUtensorMap* m, const uint8_t* x, int n_time, long long row_stride,
                       int n_inputs, int n_chans, int box_inputs, int box_chans);
 

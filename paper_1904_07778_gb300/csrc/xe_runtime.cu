@@ -31,7 +31,8 @@ bool make_sample_tmap(CUtensorMap* m, const uint8_t* x, int n_time, long long ro
   }
   const cuuint64_t dims[3] = {(cuuint64_t)n_time, (cuuint64_t)n_inputs, (cuuint64_t)n_chans};
   const cuuint64_t strides[2] = {(cuuint64_t)row_stride, (cuuint64_t)row_stride * n_inputs};
-  const cuuint32_t box[3] = {128u, (cuuint32_t)box_inputs, (cuuint32_t)box_chans};
+  const cuuint32_t box[3] = {(cuuint32_t)herk_ring_stage(), (cuuint32_t)box_inputs,
+                             (cuuint32_t)box_chans};
   const cuuint32_t estr[3] = {1u, 1u, 1u};
   return encode(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<uint8_t*>(x), dims, strides, box,
                 estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
