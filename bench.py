@@ -47,6 +47,16 @@ WORKLOADS = {
         desc="dish array: 32 inputs x 1024 channels x 4096 spectra/block, 4-bit complex, "
              "[time][channel][input] payload order, sky+noise model",
         N=32, C=1024, T=4096, layout=0, kind="sky"),
+    "dish0": dict(
+        desc="dish array, plain: 32 inputs x 256 channels x 1024 spectra/block, 4-bit complex, "
+             "[time][channel][input] payload order, i.i.d. Gaussian sigma 2.5 (40 distinct blocks "
+             "cycled: 335 MB, larger than L2)",
+        N=32, C=256, T=1024, layout=0, kind="gauss", alt_blocks=40),
+    "dish_stream": dict(
+        desc="dish array, streaming integration: 32 inputs x 1024 channels, blocks of 4096 spectra, "
+             "32 blocks integrated per dump into int64, 4-bit complex, [time][channel][input] "
+             "order, sky+noise model (4 distinct 134 MB blocks cycled)",
+        N=32, C=1024, T=4096, layout=0, kind="sky", alt_blocks=4, per_dump=32),
 }
 # Mixed arrays correlated as one batch (one persistent launch per run, from a
 # CUDA graph) against one launch per array: Gaussian samples as the 32-input
@@ -72,6 +82,10 @@ REAL_TIME_RATE = 125e6  # spectra x channels per second per input at 250 MSPS re
 
 def ops_per_block(w):
     return 8 * w["N"] * (w["N"] + 1) // 2 * w["C"] * w["T"]
+
+
+def ops_per_step(w):
+    return ops_per_block(w) * w.get("per_dump", 1)
 
 
 def executed_flops_per_block(w, bits=4):
@@ -227,7 +241,7 @@ def time_oracle(blk, w, nch, ts, cores):
 def run_reference(args, w, world, rank):
     if rank != 0:
         return 0
-    budget = max(0.05, min(2.0, 120.0 / max(1, args.steps + args.warmup)))
+    budget = max(0.05, min(2.0, args.cpu_seconds, 120.0 / max(1, args.steps + args.warmup)))
     blk, nch, ts, cores = cpu_oracle_run(w, budget)
     for _ in range(args.warmup):
         time_oracle(blk, w, nch, ts, cores)
@@ -259,17 +273,21 @@ def run_gpu(args, w, world, rank, local):
     stream = torch.cuda.Stream(device=dev)
     N, C, T = w["N"], w["C"], w["T"]
     nb = N * (N + 1) // 2
+    nalt = w.get("alt_blocks", 2)
+    per_dump = w.get("per_dump", 1)
     with torch.cuda.stream(stream):
-        # two different blocks (2 x 1.5 GiB for the default workload, both far
-        # larger than the 129 MB L2): alternate so no step reuses cached input
+        # distinct blocks (2 x 1.5 GiB for the default workload, each far larger
+        # than the 129 MB L2; more, smaller ones for the small workloads) cycled
+        # so that no step reuses cached input
         blocks = [synth.block_device(w["kind"], 1000 * rank + s, N, C, T, w["layout"], dev)
-                  for s in range(2)]
+                  for s in range(nalt)]
         vis = torch.empty((C, nb, 2), dtype=torch.int64, device=dev)
     stream.synchronize()
     cor = Correlator(N, C, T, bits=4, layout=w["layout"], stream=stream.cuda_stream)
 
     def step(k):
-        cor.push(blocks[k & 1])
+        for p in range(per_dump):
+            cor.push(blocks[(k * per_dump + p) % nalt])
         cor.dump_into(vis, reset=True)
 
     for k in range(args.warmup):
@@ -301,13 +319,15 @@ def run_gpu(args, w, world, rank, local):
     # blocks copied in and the visibilities read back every step
     e2e = None
     if not args.no_e2e:
-        hb = [torch.empty(blocks[0].numel(), dtype=torch.uint8, pin_memory=True) for _ in range(2)]
+        hb = [torch.empty(blocks[0].numel(), dtype=torch.uint8, pin_memory=True)
+              for _ in range(min(nalt, 2))]
         for h, b in zip(hb, blocks):
             h.copy_(b)
         hv = torch.empty((C, nb, 2), dtype=torch.int64, pin_memory=True)
 
         def step_host(k):
-            cor.push(hb[k & 1])
+            for p in range(per_dump):
+                cor.push(hb[(k * per_dump + p) % len(hb)])
             cor.dump_into(hv, reset=True)
 
         for k in range(max(2, args.warmup // 4)):
@@ -324,8 +344,8 @@ def run_gpu(args, w, world, rank, local):
         torch.cuda.synchronize()
         e2e_wall = time.perf_counter() - t0
         e2e_ms = max_over_ranks(1e3 * e2e_wall / ke, world)
-        e2e = {"value": world * ops_per_block(w) / (e2e_ms * 1e-3) / 1e12, "unit": "Tops/s",
-               "h2d_bytes_per_step": blocks[0].numel(), "d2h_bytes_per_step": vis.numel() * 8,
+        e2e = {"value": world * ops_per_step(w) / (e2e_ms * 1e-3) / 1e12, "unit": "Tops/s",
+               "h2d_bytes_per_step": blocks[0].numel() * per_dump, "d2h_bytes_per_step": vis.numel() * 8,
                "ms_per_step": e2e_ms, "steps": ke}
 
     cpu = None
@@ -373,7 +393,7 @@ def run_gpu(args, w, world, rank, local):
             roof[k] = dom[k]
     roof["kernel"] = dom["kernel"]
     ms_step = ms_max / args.steps
-    value = world * ops_per_block(w) / (ms_step * 1e-3) / 1e12
+    value = world * ops_per_step(w) / (ms_step * 1e-3) / 1e12
     line = {
         "metric": METRIC, "value": value, "unit": "Tops/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -381,9 +401,11 @@ def run_gpu(args, w, world, rank, local):
         "data": "synthetic (seeded sky+noise model, device-generated)",
         "config": {"workload": w["desc"], "n_inputs": N, "n_chans": C, "n_time": T,
                    "bits": 4, "layout": ["tci", "tic", "cit"][w["layout"]],
-                   "l2": "inputs larger than L2 (two alternating 1.5 GiB blocks)",
+                   "l2": "inputs larger than L2 (%d distinct blocks of %.0f MB cycled)" % (
+                       nalt, N * C * T / 1e6),
+                   "blocks_per_dump": per_dump,
                    "parallelism": "replica per GPU, channels independent" if world > 1 else "1 GPU"},
-        "x_real_time": world * C * T / REAL_TIME_RATE / (ms_step * 1e-3),
+        "x_real_time": world * C * T * per_dump / REAL_TIME_RATE / (ms_step * 1e-3),
         "wall_ms_per_step": 1e3 * wall / args.steps,
         "gpu_launches": (d["herk_launches"] + d["turn_launches"] + d["norm_launches"]),
         "roofline": roof, "kernels": kernels,

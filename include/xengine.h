@@ -149,6 +149,16 @@ const char* corr_strerror(int status);
 int64_t corr_n_baselines(int n_inputs);
 
 /*
+ * corr_restore -- resume an integration from a saved state (checkpoint /
+ * resume: a corr_dump with reset = 0 is the snapshot).
+ *   vis : int64 [C][N(N+1)/2][2], host or device, as corr_dump wrote it.
+ * The context's running integration becomes vis; later pushes add to it.
+ * The sequence check restarts (any seq is accepted next).  Stream-ordered;
+ * vis is read before the call returns.  CORR_EINVAL for a null argument.
+ */
+int corr_restore(corr_ctx* ctx, const int64_t* vis);
+
+/*
  * Run-time counters of a context, in the spirit of the per-thread key/value
  * status buffer of the paper's pipeline manager (Sec. 2.2, Hashpipe status).
  * Device times are summed over launches since the context was created and

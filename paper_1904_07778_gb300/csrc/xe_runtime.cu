@@ -450,6 +450,16 @@ int corr_dump(corr_ctx* x, int64_t* vis, int reset) {
   return st;
 }
 
+int corr_restore(corr_ctx* x, const int64_t* vis) {
+  if (!x || !vis) return CORR_EINVAL;
+  if (cudaMemcpyAsync(x->acc, vis, x->acc_bytes, cudaMemcpyDefault, x->stream) != cudaSuccess ||
+      cudaStreamSynchronize(x->stream) != cudaSuccess)
+    return CORR_ECUDA;
+  x->acc_live = true;
+  x->seq_started = false;
+  return CORR_OK;
+}
+
 int corr_normalise(corr_ctx* x, double* rho) {
   if (!x || !rho) return CORR_EINVAL;
   const size_t bytes = x->acc_bytes;  // same element count, 8-byte elements

@@ -60,6 +60,9 @@ class CorrStats(ctypes.Structure):
 
 
 _lib.corr_set_timing.argtypes = [_P, _I]
+_lib.corr_restore.argtypes = [_P, _P]
+_lib.corr_restore.restype = _I
+EXPORTS.append("corr_restore")
 _lib.corr_correlate_noalloc.argtypes = [_P, _I, _I, _I, _I, _U, _P, _P, _P]
 _lib.corr_correlate_noalloc.restype = _I
 CORR_NOALLOC_SCRATCH_BYTES = 16 << 20
@@ -181,6 +184,15 @@ class Correlator:
     def dump(self, reset=True, check=True):
         vis = np.empty((self.n_chans, self.n_baselines, 2), dtype=np.int64)
         return self.dump_into(vis, reset, check)
+
+    def restore(self, vis):
+        """Resume from a saved integration (a dump taken with reset=False)."""
+        p, n = _ptr_and_size(vis)
+        if n != self.n_chans * self.n_baselines * 16:
+            raise ValueError("vis must hold n_chans * n_baselines * 2 int64")
+        st = _lib.corr_restore(self._ctx, _P(p))
+        if st != CORR_OK:
+            raise CorrError(st, "corr_restore")
 
     def normalise_into(self, rho):
         p, n = _ptr_and_size(rho)

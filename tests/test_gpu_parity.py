@@ -259,3 +259,41 @@ def test_eight_bit_512_inputs(xe):
     blk = _sym8(512, 2 * N * C * T)
     got = _run8(xe, [blk], N, C, T, 0)
     assert np.array_equal(got, oracle.correlate(blk, N, C, T, bits=8, layout=0))
+
+
+def test_checkpoint_restore_resume(xe):
+    """Snapshot (dump without reset) + restore into a fresh context + the
+    remaining blocks equals the uninterrupted integration, bit for bit."""
+    N, C, T = 48, 6, 512
+    blks = [synth.random_bytes(500 + s, N * C * T) for s in range(4)]
+    with xe.Correlator(N, C, T, layout=1) as cor:
+        for b in blks:
+            cor.push(b)
+        whole = cor.dump()
+    with xe.Correlator(N, C, T, layout=1) as cor:
+        cor.push(blks[0], seq=7)
+        cor.push(blks[1], seq=8)
+        snap = cor.dump(reset=False)
+    with xe.Correlator(N, C, T, layout=1) as cor:
+        cor.restore(torch.from_numpy(snap).cuda())
+        cor.push(blks[2], seq=9)            # the sequence restarts after a restore
+        cor.push(blks[3], seq=10)
+        resumed = cor.dump()
+    assert np.array_equal(resumed, whole)
+    assert np.array_equal(whole, _oracle(blks, N, C, T, 1))
+
+
+def test_dump_leaves_neighbouring_memory_alone(xe):
+    """Canaries on both sides of the output: a dump writes exactly the
+    visibilities, nothing before or after them."""
+    N, C, T = 40, 5, 256
+    nb = N * (N + 1) // 2
+    guard = 4096
+    buf = torch.full((2 * guard + C * nb * 2,), 0x5A5A5A5A5A5A5A5A, dtype=torch.int64, device="cuda")
+    blk = synth.random_bytes(77, N * C * T)
+    with xe.Correlator(N, C, T, layout=0) as cor:
+        cor.push(blk)
+        cor.dump_into(buf[guard:guard + C * nb * 2])
+    h = buf.cpu().numpy()
+    assert (h[:guard] == 0x5A5A5A5A5A5A5A5A).all() and (h[-guard:] == 0x5A5A5A5A5A5A5A5A).all()
+    assert np.array_equal(h[guard:-guard].reshape(C, nb, 2), _oracle([blk], N, C, T, 0))
