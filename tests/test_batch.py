@@ -101,3 +101,23 @@ def test_batch_rejects_bad_shapes(xe):
                    [(32, 4, 40, 4, 2)]):                          # unaligned rows in place
         with pytest.raises(xe.CorrError):
             xe.Batch(shapes)
+
+
+def test_batch_of_many_small_arrays(xe):
+    """Sixteen arrays of assorted shapes and layouts in one launch."""
+    rng = np.random.default_rng(77)
+    shapes = []
+    for _ in range(16):
+        n = int(rng.choice([3, 8, 16, 24, 40, 64, 72]))
+        layout = int(rng.integers(0, 3))
+        t = int(rng.choice([96, 128, 256, 320]))
+        if layout == 2:
+            t = t // 16 * 16
+        shapes.append((n, int(rng.integers(1, 9)), t, 4, layout))
+    blocks = _blocks(shapes, 900)
+    with xe.Batch(shapes) as b:
+        for k, blk in enumerate(blocks):
+            b.set_input(k, blk)
+        b.run()
+        assert b.sync() == xe.CORR_OK
+        _check(b, shapes, blocks)

@@ -297,3 +297,27 @@ def test_dump_leaves_neighbouring_memory_alone(xe):
     h = buf.cpu().numpy()
     assert (h[:guard] == 0x5A5A5A5A5A5A5A5A).all() and (h[-guard:] == 0x5A5A5A5A5A5A5A5A).all()
     assert np.array_equal(h[guard:-guard].reshape(C, nb, 2), _oracle([blk], N, C, T, 0))
+
+
+@pytest.mark.parametrize("bits,N,C,T", [(4, 1024, 2, 256), (8, 1024, 1, 128)])
+def test_maximum_input_count(xe, bits, N, C, T):
+    """1024 inputs, the largest the ABI accepts: 16 (4-bit) and 32 (8-bit)
+    row blocks of the real Gram, every tile kind of the schedule."""
+    if bits == 4:
+        blk = synth.random_bytes(1024 + bits, N * C * T)
+    else:
+        blk = _sym8(1024 + bits, 2 * N * C * T)
+    with xe.Correlator(N, C, T, bits=bits, layout=0) as cor:
+        cor.push(torch.from_numpy(blk).cuda())
+        got = cor.dump()
+    assert np.array_equal(got, oracle.correlate(blk, N, C, T, bits=bits, layout=0))
+
+
+def test_one_full_accumulation_worst_case(xe):
+    """Exactly 65536 spectra in one accumulation with the largest offset codes
+    (u = 15 everywhere: 225 x 65536 < 2^24, the FP32 bound the path relies on)."""
+    N, C, T = 6, 2, 65536
+    blk = np.full(N * C * T, 0x77, np.uint8)  # +7 + 7i: offset code 15 in both planes
+    blk[::5] = 0x88                           # and -8 - 8i (offset code 0)
+    got = _run(xe, [blk], N, C, T, 2)
+    assert np.array_equal(got, _oracle([blk], N, C, T, 2))
