@@ -256,6 +256,7 @@ typedef struct corr_batch_info {
   int n_ctas;            /* CTAs (one per SM)                                    */
   int launches_per_run;  /* kernels one corr_batch_run launches                  */
   double tuned_ms[3];    /* median run time of each schedule (autotune), else 0  */
+  int tune_source;       /* 0 default schedule, 1 timed now, 2 from the tune cache */
 } corr_batch_info;
 
 /*
@@ -267,7 +268,10 @@ typedef struct corr_batch_info {
  *            stream (the caller then orders its own work with corr_batch_sync).
  *   tune   : 0 uses CORR_SCHED_PAIRS_LPT; 1 times every schedule on the
  *            device (on the current contents of the input buffers) and keeps
- *            the fastest.
+ *            the fastest.  If the environment variable XE_TUNE_CACHE names a
+ *            file, a result for the same GPU (name, SM count) and the same
+ *            shapes is taken from it instead of timing, and new results are
+ *            appended to it (JSON lines: key, schedule, tuned_ms).
  * Returns CORR_EINVAL for a bad shape or mixed bits/flags, CORR_ENOMEM,
  * CORR_ECUDA.
  */

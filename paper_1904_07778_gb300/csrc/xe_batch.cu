@@ -8,9 +8,12 @@
 // are grouped into tasks and which SM runs which task -- is chosen by the
 // host, optionally by timing every candidate on the device (autotune).
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <numeric>
+#include <string>
 #include <vector>
 
 #include "xe_internal.h"
@@ -39,6 +42,7 @@ struct corr_batch {
   std::vector<int> n_tasks_one, max_nblk_one;
   int schedule = CORR_SCHED_PAIRS_LPT;
   double tuned_ms[3] = {0, 0, 0};
+  int tune_source = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int* d_status = nullptr;
@@ -218,6 +222,55 @@ double time_schedule(corr_batch* b, int reps) {
   return ms.empty() ? 0.0 : ms[ms.size() / 2];
 }
 
+// Autotuner cache: one JSON object per line, {"key": K, "schedule": S,
+// "tuned_ms": [a, b, c]}, the key naming the GPU and every array's shape.
+std::string tune_key(const corr_batch* b) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceProp p;
+  std::string k = cudaGetDeviceProperties(&p, dev) == cudaSuccess ? p.name : "unknown";
+  for (char& c : k)
+    if (c == '"' || c == '\\') c = '_';
+  k += "/" + std::to_string(sm_count());
+  for (const corr_shape& s : b->shapes)
+    k += "|" + std::to_string(s.n_inputs) + "," + std::to_string(s.n_chans) + "," +
+         std::to_string(s.n_time) + "," + std::to_string(s.bits) + "," +
+         std::to_string(s.layout) + "," + std::to_string(s.flags);
+  return k;
+}
+
+bool cache_lookup(const char* path, const std::string& key, int* sched, double ms[3]) {
+  FILE* f = fopen(path, "r");
+  if (!f) return false;
+  const std::string want = "{\"key\": \"" + key + "\", ";
+  bool found = false;
+  char line[8192];
+  while (fgets(line, sizeof(line), f)) {
+    if (strncmp(line, want.c_str(), want.size()) != 0) continue;
+    int s = -1;
+    double a = 0, b2 = 0, c = 0;
+    if (sscanf(line + want.size(), "\"schedule\": %d, \"tuned_ms\": [%lf, %lf, %lf]", &s, &a, &b2,
+               &c) == 4 &&
+        s >= 0 && s <= 2) {  // the last matching line wins
+      *sched = s;
+      ms[0] = a;
+      ms[1] = b2;
+      ms[2] = c;
+      found = true;
+    }
+  }
+  fclose(f);
+  return found;
+}
+
+void cache_store(const char* path, const std::string& key, int sched, const double ms[3]) {
+  FILE* f = fopen(path, "a");
+  if (!f) return;
+  fprintf(f, "{\"key\": \"%s\", \"schedule\": %d, \"tuned_ms\": [%.6f, %.6f, %.6f]}\n", key.c_str(),
+          sched, ms[0], ms[1], ms[2]);
+  fclose(f);
+}
+
 }  // namespace
 
 extern "C" {
@@ -248,6 +301,7 @@ int corr_plan_schedule(const double* cost, int n_tasks, int n_ctas, int* order, 
 }
 
 int corr_batch_create(const corr_shape* shapes, int n, void* stream, int tune, corr_batch** out) {
+  TraceRange trace_("corr_batch_create");
   if (!out) return CORR_EINVAL;
   *out = nullptr;
   if (!shapes || n < 1) return CORR_EINVAL;
@@ -330,7 +384,12 @@ int corr_batch_create(const corr_shape* shapes, int n, void* stream, int tune, c
         cudaMalloc(&b->d_tmaps, sizeof(CUtensorMap) * n) != cudaSuccess) { st = CORR_ENOMEM; break; }
     if (cudaMemcpy(b->d_insts, b->insts.data(), sizeof(HerkInst) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(b->d_tmaps, b->tmaps.data(), sizeof(CUtensorMap) * n, cudaMemcpyHostToDevice) != cudaSuccess) { st = CORR_ECUDA; break; }
-    if (tune) {
+    const char* cache = tune ? getenv("XE_TUNE_CACHE") : nullptr;
+    int cached_s = -1;
+    if (cache && *cache && cache_lookup(cache, tune_key(b), &cached_s, b->tuned_ms)) {
+      b->tune_source = 2;
+      st = build_schedule(b, cached_s);
+    } else if (tune) {
       double best = 0.0;
       int best_s = CORR_SCHED_PAIRS_LPT;
       for (int sch = 0; sch < 3 && st == CORR_OK; ++sch) {
@@ -348,6 +407,8 @@ int corr_batch_create(const corr_shape* shapes, int n, void* stream, int tune, c
       if (cudaStreamSynchronize(b->stream) != cudaSuccess ||
           cudaMemset(b->d_status, 0, sizeof(int)) != cudaSuccess) { st = CORR_ECUDA; break; }
       st = build_schedule(b, best_s);
+      b->tune_source = 1;
+      if (cache && *cache) cache_store(cache, tune_key(b), best_s, b->tuned_ms);
     } else {
       st = build_schedule(b, CORR_SCHED_PAIRS_LPT);
     }
@@ -394,11 +455,13 @@ int corr_batch_get_output(corr_batch* b, int k, int64_t* dst) {
 }
 
 int corr_batch_run(corr_batch* b) {
+  TraceRange trace_("corr_batch_run");
   if (!b || !b->exec) return CORR_EINVAL;
   return cudaGraphLaunch(b->exec, b->stream) == cudaSuccess ? CORR_OK : CORR_ECUDA;
 }
 
 int corr_batch_run_plain(corr_batch* b) {
+  TraceRange trace_("corr_batch_run_plain");
   if (!b) return CORR_EINVAL;
   for (int k = 0; k < b->n; ++k) {
     const corr_shape& sh = b->shapes[k];
@@ -434,6 +497,7 @@ int corr_batch_info_get(corr_batch* b, corr_batch_info* out) {
   for (const corr_shape& s : b->shapes) launches += needs_turn(s.layout, s.bits) ? 1 : 0;
   out->launches_per_run = launches;
   for (int i = 0; i < 3; ++i) out->tuned_ms[i] = b->tuned_ms[i];
+  out->tune_source = b->tune_source;
   return CORR_OK;
 }
 

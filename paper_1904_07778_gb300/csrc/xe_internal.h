@@ -7,8 +7,18 @@
 
 #include <cuda.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 namespace xe {
+
+// A named NVTX range for the scope (visible in a profiler's timeline; free
+// when no tool is attached).
+struct TraceRange {
+  explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+  TraceRange(const TraceRange&) = delete;
+  TraceRange& operator=(const TraceRange&) = delete;
+};
 
 // Device status word bits (OR-ed by kernels, read and cleared by the host).
 enum : int {

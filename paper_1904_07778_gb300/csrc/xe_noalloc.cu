@@ -120,6 +120,7 @@ using namespace xe;
 extern "C" int corr_correlate_noalloc(const void* block, int n_inputs, int n_chans, int n_time,
                                       int layout, unsigned flags, int64_t* vis, int* status,
                                       void* stream) {
+  TraceRange trace_("corr_correlate_noalloc");
   if (!block || !vis || n_inputs < 1 || n_inputs > 1024 || n_chans < 1 || n_time < 1 ||
       layout < CORR_L_TCI || layout > CORR_L_CIT || (flags & ~CORR_F_LO_IS_REAL))
     return CORR_EINVAL;

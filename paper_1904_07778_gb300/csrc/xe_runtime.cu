@@ -333,6 +333,7 @@ int corr_create(int n_inputs, int n_chans, int n_time, int bits, int layout, uns
 }
 
 int corr_push(corr_ctx* x, const void* block, size_t nbytes, uint64_t seq) {
+  TraceRange trace_("corr_push");
   if (!x || !block) return CORR_EINVAL;
   if (nbytes != x->block_bytes) return CORR_EINVAL;
   if (seq != CORR_SEQ_ANY) {
@@ -426,6 +427,7 @@ int corr_sync(corr_ctx* x) {
 }
 
 int corr_dump(corr_ctx* x, int64_t* vis, int reset) {
+  TraceRange trace_("corr_dump");
   if (!x) return CORR_EINVAL;
   if (vis) {
     const bool dev = is_device_ptr(vis);
@@ -451,6 +453,7 @@ int corr_dump(corr_ctx* x, int64_t* vis, int reset) {
 }
 
 int corr_restore(corr_ctx* x, const int64_t* vis) {
+  TraceRange trace_("corr_restore");
   if (!x || !vis) return CORR_EINVAL;
   if (cudaMemcpyAsync(x->acc, vis, x->acc_bytes, cudaMemcpyDefault, x->stream) != cudaSuccess ||
       cudaStreamSynchronize(x->stream) != cudaSuccess)
@@ -461,6 +464,7 @@ int corr_restore(corr_ctx* x, const int64_t* vis) {
 }
 
 int corr_normalise(corr_ctx* x, double* rho) {
+  TraceRange trace_("corr_normalise");
   if (!x || !rho) return CORR_EINVAL;
   const size_t bytes = x->acc_bytes;  // same element count, 8-byte elements
   if (!x->acc_live) {

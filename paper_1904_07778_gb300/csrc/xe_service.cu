@@ -320,6 +320,7 @@ int corr_svc_state(corr_svc* s, int64_t id, int* state) {
 }
 
 int corr_svc_push(corr_svc* s, int64_t id, const void* block, size_t nbytes) {
+  TraceRange trace_("corr_svc_push");
   if (!s || !block) return CORR_EINVAL;
   auto it = s->reqs.find(id);
   if (it == s->reqs.end()) return CORR_EINVAL;
@@ -341,6 +342,7 @@ int corr_svc_push(corr_svc* s, int64_t id, const void* block, size_t nbytes) {
 }
 
 int corr_svc_tick(corr_svc* s, int* n_requests) {
+  TraceRange trace_("corr_svc_tick");
   if (!s) return CORR_EINVAL;
   std::vector<Req*> parts;
   for (auto& kv : s->reqs) {
@@ -472,6 +474,7 @@ int corr_svc_tick(corr_svc* s, int* n_requests) {
 }
 
 int corr_svc_fetch(corr_svc* s, int64_t id, int64_t* vis) {
+  TraceRange trace_("corr_svc_fetch");
   if (!s) return CORR_EINVAL;
   auto it = s->reqs.find(id);
   if (it == s->reqs.end()) return CORR_EINVAL;

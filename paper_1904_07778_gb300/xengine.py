@@ -255,7 +255,7 @@ class CorrShape(ctypes.Structure):
 class CorrBatchInfo(ctypes.Structure):
     """Mirror of struct corr_batch_info."""
     _fields_ = [("schedule", _I), ("n_tasks", _I), ("n_ctas", _I), ("launches_per_run", _I),
-                ("tuned_ms", ctypes.c_double * 3)]
+                ("tuned_ms", ctypes.c_double * 3), ("tune_source", _I)]
 
 
 _lib.corr_batch_create.argtypes = [ctypes.POINTER(CorrShape), _I, _P, _I, ctypes.POINTER(_P)]
@@ -344,7 +344,8 @@ class Batch:
         if st != CORR_OK:
             raise CorrError(st, "corr_batch_info_get")
         return {"schedule": out.schedule, "n_tasks": out.n_tasks, "n_ctas": out.n_ctas,
-                "launches_per_run": out.launches_per_run, "tuned_ms": list(out.tuned_ms)}
+                "launches_per_run": out.launches_per_run, "tuned_ms": list(out.tuned_ms),
+                "tune_source": out.tune_source}
 
     def close(self):
         if getattr(self, "_b", None):

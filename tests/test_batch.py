@@ -81,6 +81,39 @@ def test_batch_autotune_every_schedule_exact(xe):
         _check(b, SHAPES4, blocks)
 
 
+def test_batch_tune_cache_reuses_schedule(xe, tmp_path, monkeypatch):
+    """With XE_TUNE_CACHE set, the first tuned batch times and records its
+    schedule; a later batch of the same shapes takes it from the file (the
+    last matching line wins) and still correlates exactly."""
+    cache = tmp_path / "tune.jsonl"
+    monkeypatch.setenv("XE_TUNE_CACHE", str(cache))
+    with xe.Batch(SHAPES4, tune=True) as b:
+        first = b.info()
+    assert first["tune_source"] == 1
+    lines = cache.read_text().splitlines()
+    assert len(lines) == 1 and '"schedule": %d' % first["schedule"] in lines[0]
+    with xe.Batch(SHAPES4, tune=True) as b:
+        again = b.info()
+    assert again["tune_source"] == 2 and again["schedule"] == first["schedule"]
+    assert np.allclose(again["tuned_ms"], first["tuned_ms"], atol=1e-6)
+    forced = (first["schedule"] + 1) % 3             # a later line overrides
+    cache.write_text(cache.read_text() + lines[0].replace(
+        '"schedule": %d' % first["schedule"], '"schedule": %d' % forced) + "\n")
+    blocks = _blocks(SHAPES4, 310)
+    with xe.Batch(SHAPES4, tune=True) as b:
+        assert b.info()["tune_source"] == 2 and b.info()["schedule"] == forced
+        for k, blk in enumerate(blocks):
+            b.set_input(k, blk)
+        b.run()
+        assert b.sync() == xe.CORR_OK
+        _check(b, SHAPES4, blocks)
+    with xe.Batch(SHAPES4[:2], tune=True) as b:      # other shapes: timed anew
+        assert b.info()["tune_source"] == 1
+    assert len(cache.read_text().splitlines()) == 3
+    with xe.Batch(SHAPES4) as b:                     # untuned: the default
+        assert b.info()["tune_source"] == 0 and b.info()["schedule"] == 0
+
+
 def test_batch_matches_single_array_contexts(xe):
     """Each array alone through corr_create/corr_push/corr_dump gives the same."""
     blocks = _blocks(SHAPES4, 400)
