@@ -323,30 +323,53 @@ def run_gpu(args, w, world, rank, local):
               for _ in range(min(nalt, 2))]
         for h, b in zip(hb, blocks):
             h.copy_(b)
-        hv = torch.empty((C, nb, 2), dtype=torch.int64, pin_memory=True)
+        hv = [torch.empty((C, nb, 2), dtype=torch.int64, pin_memory=True) for _ in range(2)]
 
+        # one step of lookahead: step k queues its pushes and an overlapped
+        # dump, then waits for step k-1's visibilities to reach the host
         def step_host(k):
             for p in range(per_dump):
                 cor.push(hb[(k * per_dump + p) % len(hb)])
-            cor.dump_into(hv, reset=True)
+            cor.dump_async(hv[k % 2], reset=True)
+            if k > 0:
+                cor.dump_wait()
 
         for k in range(max(2, args.warmup // 4)):
             step_host(k)
+        cor.dump_wait()
         ke = max(3, min(args.steps, args.e2e_steps))
         barrier(world)
         torch.cuda.synchronize()
-        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        f0.record(stream)
         t0 = time.perf_counter()
         for k in range(ke):
             step_host(k)
-        f1.record(stream)
-        torch.cuda.synchronize()
+        cor.dump_wait()
         e2e_wall = time.perf_counter() - t0
+        # the host link alone: one pinned block in and one result out, timed
+        # with events (plain copies, for the e2e floor)
+        l_in, l_out = [], []
+        dv = torch.empty((C, nb, 2), dtype=torch.int64, device="cuda")
+        for _ in range(3):
+            g0, g1, g2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            g0.record()
+            blocks[0].view(-1).copy_(hb[0], non_blocking=True)
+            g1.record()
+            hv[0].copy_(dv, non_blocking=True)
+            g2.record()
+            torch.cuda.synchronize()
+            l_in.append(g0.elapsed_time(g1))
+            l_out.append(g1.elapsed_time(g2))
+        link = {"h2d_gbs": hb[0].numel() / (min(l_in) * 1e-3) / 1e9,
+                "d2h_gbs": hv[0].numel() * 8 / (min(l_out) * 1e-3) / 1e9}
+        del dv
         e2e_ms = max_over_ranks(1e3 * e2e_wall / ke, world)
         e2e = {"value": world * ops_per_step(w) / (e2e_ms * 1e-3) / 1e12, "unit": "Tops/s",
                "h2d_bytes_per_step": blocks[0].numel() * per_dump, "d2h_bytes_per_step": vis.numel() * 8,
-               "ms_per_step": e2e_ms, "steps": ke}
+               "ms_per_step": e2e_ms, "steps": ke,
+               "pipeline": "step k's dump overlaps step k+1's pushes (corr_dump_async)",
+               "link": dict(link, floor_ms_per_step=max(
+                   blocks[0].numel() * per_dump / link["h2d_gbs"] / 1e6,
+                   vis.numel() * 8 / link["d2h_gbs"] / 1e6))}
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:

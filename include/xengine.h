@@ -127,6 +127,33 @@ int corr_push(corr_ctx* ctx, const void* block, size_t nbytes, uint64_t seq);
 int corr_dump(corr_ctx* ctx, int64_t* vis, int reset);
 
 /*
+ * corr_dump_async -- overlapped dump: queue the copy of the integrated
+ * visibilities into vis and return without waiting.
+ *   vis   : int64 [C][N(N+1)/2][2], device or host memory (pinned host memory
+ *           keeps the call asynchronous; a pageable buffer makes it wait).
+ *           vis holds the sums once the matching corr_dump_wait returns.
+ *   reset : nonzero -> the next integration starts from zero at once, in a
+ *           second accumulator (allocated on the first such call), so pushes
+ *           after this call overlap the copy; zero -> pushes after this call
+ *           wait for the copy and then keep adding to the same sums.
+ * At most CORR_MAX_ASYNC_DUMPS dumps may be outstanding (CORR_EBUSY beyond).
+ * The deferred device status of the blocks in the dumped integration
+ * (CORR_ERANGE, CORR_ETIMEDOUT) is returned by its corr_dump_wait, not by a
+ * later corr_sync / corr_dump.  A host block pushed before this call may be
+ * changed once the matching corr_dump_wait returns.  CORR_EINVAL for a null
+ * argument.
+ */
+#define CORR_MAX_ASYNC_DUMPS 4
+int corr_dump_async(corr_ctx* ctx, int64_t* vis, int reset);
+
+/*
+ * corr_dump_wait -- wait for the oldest outstanding corr_dump_async (dumps
+ * complete in the order they were queued) and return its status.
+ * CORR_ESTATE when no dump is outstanding.
+ */
+int corr_dump_wait(corr_ctx* ctx);
+
+/*
  * corr_normalise -- correlation coefficients of the current integration:
  * rho_ij = V_ij / sqrt(V_ii * V_jj) computed in FP64 on the GPU as
  * double(V_ij) / sqrt(double(V_ii) * double(V_jj)); rho = 0 where
@@ -136,7 +163,8 @@ int corr_dump(corr_ctx* ctx, int64_t* vis, int reset);
  */
 int corr_normalise(corr_ctx* ctx, double* rho);
 
-/* corr_sync -- wait for all pushed work; returns any deferred device error. */
+/* corr_sync -- wait for all pushed work and queued dumps; returns any deferred
+ * device error not already returned by corr_dump_wait. */
 int corr_sync(corr_ctx* ctx);
 
 /* corr_destroy -- free the context (waits for its work first).  NULL is ok. */

@@ -100,9 +100,22 @@ struct corr_ctx {
   bool own_stream = false;
   cudaStream_t copy_stream = nullptr;
   size_t block_bytes = 0;
-  int64_t* acc = nullptr;  // int64 [C][B][2] long integration
+  int64_t* acc = nullptr;  // int64 [C][B][2] long integration (= acc_buf[cur])
   size_t acc_bytes = 0;
   bool acc_live = false;   // false: next push stores instead of adding
+  // Overlapped dumps (corr_dump_async): a reset switches to the other
+  // accumulator while the copy of the finished one runs on dump_stream.
+  int64_t* acc_buf[2] = {nullptr, nullptr};
+  int cur = 0;
+  cudaStream_t dump_stream = nullptr;
+  cudaEvent_t acc_free[2] = {nullptr, nullptr};  // last copy out of acc_buf[k] done
+  bool read_pending[2] = {false, false};
+  struct AsyncDump {
+    cudaEvent_t done;
+    int slot;  // index into h_dump_status
+  };
+  std::vector<AsyncDump> dumps;  // outstanding, oldest first
+  int* h_dump_status = nullptr;  // pinned, kMaxAsyncDumps status snapshots
   uint8_t* stage[2] = {nullptr, nullptr};
   cudaEvent_t stage_free[2] = {nullptr, nullptr};
   cudaEvent_t stage_ready[2] = {nullptr, nullptr};
@@ -206,7 +219,14 @@ void free_ctx(corr_ctx* x) {
   if (!x) return;
   if (x->stream) cudaStreamSynchronize(x->stream);
   if (x->copy_stream) cudaStreamSynchronize(x->copy_stream);
-  cudaFree(x->acc);
+  if (x->dump_stream) cudaStreamSynchronize(x->dump_stream);
+  cudaFree(x->acc_buf[0]);
+  cudaFree(x->acc_buf[1]);
+  for (int i = 0; i < 2; ++i)
+    if (x->acc_free[i]) cudaEventDestroy(x->acc_free[i]);
+  for (auto& d : x->dumps) cudaEventDestroy(d.done);
+  if (x->h_dump_status) cudaFreeHost(x->h_dump_status);
+  if (x->dump_stream) cudaStreamDestroy(x->dump_stream);
   for (int i = 0; i < 2; ++i) {
     cudaFree(x->stage[i]);
     if (x->stage_free[i]) cudaEventDestroy(x->stage_free[i]);
@@ -227,6 +247,22 @@ void free_ctx(corr_ctx* x) {
   delete x;
 }
 
+// Before the context's stream writes the current accumulator: wait for an
+// overlapped dump that still reads it.
+int guard_acc_write(corr_ctx* x) {
+  if (!x->read_pending[x->cur]) return CORR_OK;
+  if (cudaStreamWaitEvent(x->stream, x->acc_free[x->cur], 0) != cudaSuccess) return CORR_ECUDA;
+  x->read_pending[x->cur] = false;
+  return CORR_OK;
+}
+
+int status_code(int st) {
+  if (st == 0) return CORR_OK;
+  if (st & kStTimeout) return CORR_ETIMEDOUT;
+  if (st & kStRange) return CORR_ERANGE;
+  return CORR_ECUDA;
+}
+
 // Read and clear the device status word (waits for the stream).
 int take_status(corr_ctx* x) {
   if (cudaMemcpyAsync(x->h_status, x->d_status, sizeof(int), cudaMemcpyDeviceToHost,
@@ -237,9 +273,7 @@ int take_status(corr_ctx* x) {
   if (st == 0) return CORR_OK;
   if (cudaMemsetAsync(x->d_status, 0, sizeof(int), x->stream) != cudaSuccess) return CORR_ECUDA;
   if (cudaStreamSynchronize(x->stream) != cudaSuccess) return CORR_ECUDA;
-  if (st & kStTimeout) return CORR_ETIMEDOUT;
-  if (st & kStRange) return CORR_ERANGE;
-  return CORR_ECUDA;
+  return status_code(st);
 }
 
 }  // namespace
@@ -299,7 +333,8 @@ int corr_create(int n_inputs, int n_chans, int n_time, int bits, int layout, uns
     }
     if (cudaStreamCreateWithFlags(&x->copy_stream, cudaStreamNonBlocking) != cudaSuccess) { st = CORR_ECUDA; break; }
     x->acc_bytes = (size_t)corr_n_baselines(n_inputs) * n_chans * 2 * sizeof(int64_t);
-    if (cudaMalloc(&x->acc, x->acc_bytes) != cudaSuccess) { st = CORR_ENOMEM; break; }
+    if (cudaMalloc(&x->acc_buf[0], x->acc_bytes) != cudaSuccess) { st = CORR_ENOMEM; break; }
+    x->acc = x->acc_buf[0];
     x->turned_stride = ((long long)n_time + 31) / 32 * 32;  // 32-byte rows for the corner turn
     // byte rows per channel: one per input (4-bit), re and im bytes (8-bit)
     const int byte_rows = n_inputs * (bits / 4);
@@ -402,6 +437,7 @@ int corr_push(corr_ctx* x, const void* block, size_t nbytes, uint64_t seq) {
       aligned && make_sample_tmap(&tmap, src, T, row_stride, R, C, box_in, box_ch);
   if (eight && !use_tma) return CORR_ECUDA;  // the plane-split copy is always aligned
   const int chunk = eight ? kMaxChunk8 : kMaxChunk4;
+  if (int g = guard_acc_write(x)) return g;
   for (int t0 = 0; t0 < T; t0 += chunk) {
     a.in.t0 = t0;
     a.in.tn = std::min(chunk, T - t0);
@@ -423,7 +459,87 @@ int corr_push(corr_ctx* x, const void* block, size_t nbytes, uint64_t seq) {
 int corr_sync(corr_ctx* x) {
   if (!x) return CORR_EINVAL;
   if (cudaStreamSynchronize(x->copy_stream) != cudaSuccess) return CORR_ECUDA;
+  if (x->dump_stream && cudaStreamSynchronize(x->dump_stream) != cudaSuccess) return CORR_ECUDA;
   return take_status(x);
+}
+
+int corr_dump_async(corr_ctx* x, int64_t* vis, int reset) {
+  TraceRange trace_("corr_dump_async");
+  if (!x || !vis) return CORR_EINVAL;
+  if ((int)x->dumps.size() >= CORR_MAX_ASYNC_DUMPS) return CORR_EBUSY;
+  if (!x->dump_stream) {
+    if (cudaStreamCreateWithFlags(&x->dump_stream, cudaStreamNonBlocking) != cudaSuccess)
+      return CORR_ECUDA;
+    for (int i = 0; i < 2; ++i)
+      if (cudaEventCreateWithFlags(&x->acc_free[i], cudaEventDisableTiming) != cudaSuccess)
+        return CORR_ECUDA;
+    if (cudaMallocHost(&x->h_dump_status, CORR_MAX_ASYNC_DUMPS * sizeof(int)) != cudaSuccess)
+      return CORR_ENOMEM;
+  }
+  if (reset && !x->acc_buf[1] && cudaMalloc(&x->acc_buf[1], x->acc_bytes) != cudaSuccess)
+    return CORR_ENOMEM;
+  if (!x->acc_live) {  // nothing pushed since the last reset: an all-zero integration
+    if (int g = guard_acc_write(x)) return g;
+    if (cudaMemsetAsync(x->acc, 0, x->acc_bytes, x->stream) != cudaSuccess) return CORR_ECUDA;
+    x->acc_live = true;
+  }
+  // a status slot no outstanding dump uses
+  int slot = 0;
+  while (std::any_of(x->dumps.begin(), x->dumps.end(),
+                     [slot](const corr_ctx::AsyncDump& d) { return d.slot == slot; }))
+    ++slot;
+  // snapshot and clear the status of the blocks in this integration, in
+  // stream order, then hand the accumulator to the dump stream
+  cudaEvent_t ready = nullptr, done = nullptr;
+  if (cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) != cudaSuccess) return CORR_ECUDA;
+  if (cudaEventCreateWithFlags(&done, cudaEventDisableTiming) != cudaSuccess) {
+    cudaEventDestroy(ready);
+    return CORR_ECUDA;
+  }
+  int st = CORR_OK;
+  if (cudaMemcpyAsync(x->h_dump_status + slot, x->d_status, sizeof(int), cudaMemcpyDeviceToHost,
+                      x->stream) != cudaSuccess ||
+      cudaMemsetAsync(x->d_status, 0, sizeof(int), x->stream) != cudaSuccess ||
+      cudaEventRecord(ready, x->stream) != cudaSuccess ||
+      cudaStreamWaitEvent(x->dump_stream, ready, 0) != cudaSuccess)
+    st = CORR_ECUDA;
+  if (st == CORR_OK) {
+    cudaEvent_t td = phase_begin(x, x->dump_stream);
+    if (cudaMemcpyAsync(vis, x->acc, x->acc_bytes, cudaMemcpyDefault, x->dump_stream) != cudaSuccess)
+      st = CORR_ECUDA;
+    else
+      phase_end(x, kDump, td, x->dump_stream);
+  }
+  if (st == CORR_OK && (cudaEventRecord(x->acc_free[x->cur], x->dump_stream) != cudaSuccess ||
+                        cudaEventRecord(done, x->dump_stream) != cudaSuccess))
+    st = CORR_ECUDA;
+  cudaEventDestroy(ready);  // destruction is deferred until the event completes
+  if (st != CORR_OK) {
+    cudaEventDestroy(done);
+    return st;
+  }
+  x->read_pending[x->cur] = true;
+  x->dumps.push_back({done, slot});
+  ++x->stats.dumps;
+  if (reset) {
+    x->cur ^= 1;
+    x->acc = x->acc_buf[x->cur];
+    x->acc_live = false;
+    x->seq_started = false;
+  }
+  return CORR_OK;
+}
+
+int corr_dump_wait(corr_ctx* x) {
+  TraceRange trace_("corr_dump_wait");
+  if (!x) return CORR_EINVAL;
+  if (x->dumps.empty()) return CORR_ESTATE;
+  const corr_ctx::AsyncDump d = x->dumps.front();
+  x->dumps.erase(x->dumps.begin());
+  const cudaError_t e = cudaEventSynchronize(d.done);
+  cudaEventDestroy(d.done);
+  if (e != cudaSuccess) return CORR_ECUDA;
+  return status_code(x->h_dump_status[d.slot]);
 }
 
 int corr_dump(corr_ctx* x, int64_t* vis, int reset) {
@@ -455,6 +571,7 @@ int corr_dump(corr_ctx* x, int64_t* vis, int reset) {
 int corr_restore(corr_ctx* x, const int64_t* vis) {
   TraceRange trace_("corr_restore");
   if (!x || !vis) return CORR_EINVAL;
+  if (int g = guard_acc_write(x)) return g;
   if (cudaMemcpyAsync(x->acc, vis, x->acc_bytes, cudaMemcpyDefault, x->stream) != cudaSuccess ||
       cudaStreamSynchronize(x->stream) != cudaSuccess)
     return CORR_ECUDA;
@@ -468,6 +585,7 @@ int corr_normalise(corr_ctx* x, double* rho) {
   if (!x || !rho) return CORR_EINVAL;
   const size_t bytes = x->acc_bytes;  // same element count, 8-byte elements
   if (!x->acc_live) {
+    if (int g = guard_acc_write(x)) return g;
     if (cudaMemsetAsync(x->acc, 0, x->acc_bytes, x->stream) != cudaSuccess) return CORR_ECUDA;
     x->acc_live = true;
   }

@@ -63,6 +63,12 @@ _lib.corr_set_timing.argtypes = [_P, _I]
 _lib.corr_restore.argtypes = [_P, _P]
 _lib.corr_restore.restype = _I
 EXPORTS.append("corr_restore")
+_lib.corr_dump_async.argtypes = [_P, _P, _I]
+_lib.corr_dump_async.restype = _I
+_lib.corr_dump_wait.argtypes = [_P]
+_lib.corr_dump_wait.restype = _I
+EXPORTS += ["corr_dump_async", "corr_dump_wait"]
+CORR_MAX_ASYNC_DUMPS = 4
 _lib.corr_correlate_noalloc.argtypes = [_P, _I, _I, _I, _I, _U, _P, _P, _P]
 _lib.corr_correlate_noalloc.restype = _I
 CORR_NOALLOC_SCRATCH_BYTES = 16 << 20
@@ -180,6 +186,26 @@ class Correlator:
         if check and st != CORR_OK:
             raise CorrError(st, "corr_dump")
         return vis
+
+    def dump_async(self, vis, reset=True):
+        """Queue the copy of the integration into ``vis`` (corr_dump_async);
+        ``vis`` holds it once the matching :meth:`dump_wait` returns."""
+        p, n = _ptr_and_size(vis)
+        if n != self.n_chans * self.n_baselines * 16:
+            raise ValueError("vis must hold n_chans * n_baselines * 2 int64")
+        st = _lib.corr_dump_async(self._ctx, _P(p), 1 if reset else 0)
+        if st != CORR_OK:
+            raise CorrError(st, "corr_dump_async")
+        return vis
+
+    def dump_wait(self, check=True):
+        """Wait for the oldest queued dump; returns (and with check, raises
+        on) its deferred device status."""
+        st = _lib.corr_dump_wait(self._ctx)
+        self.last_status = st
+        if check and st != CORR_OK:
+            raise CorrError(st, "corr_dump_wait")
+        return st
 
     def dump(self, reset=True, check=True):
         vis = np.empty((self.n_chans, self.n_baselines, 2), dtype=np.int64)
