@@ -17,7 +17,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libxengine.so")
-SOURCES = ["xe_herk.cu", "xe_turn.cu", "xe_runtime.cu", "xe_noalloc.cu", "xe_batch.cu", "xe_service.cu"]
+SOURCES = ["xe_herk.cu", "xe_turn.cu", "xe_runtime.cu", "xe_noalloc.cu", "xe_batch.cu", "xe_service.cu",
+           "xe_fengine.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -43,7 +44,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
     nvcc = _nvcc()
     os.makedirs(OUT_DIR, exist_ok=True)
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
-    headers.append(os.path.join(ROOT, "include", "xengine.h"))
+    headers += [os.path.join(ROOT, "include", h) for h in ("xengine.h", "fengine.h")]
     flags = ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2",
                     "-I", os.path.join(ROOT, "include"), "-I", CSRC]
     jobs = []

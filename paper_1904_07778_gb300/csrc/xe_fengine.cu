@@ -1,0 +1,500 @@
+// GPU F-engine (Sec. 2.1): polyphase filter bank, the FFT of two real
+// inputs as one complex transform with the Eq. 2 separation, the 18-bit
+// output, and the equaliser / requantiser to packed fix_4_3 codes -- one
+// fused kernel whose output is the X-engine's input.
+//
+// A CTA takes one input pair (2k, 2k+1) and a group of 32 consecutive
+// spectra.  Per spectrum, M/8 threads (an "FFT unit"; a CTA holds
+// 2048/M units for M <= 2048) filter 8 consecutive samples each, store
+// z[n] = y_2k[n] + j y_2k+1[n] in padded shared memory, and run an in-place
+// Stockham FFT (radix-8 passes, then one radix-2 or radix-4 pass).  The
+// separated spectra are rounded to 18 bits, equalised, packed, and staged
+// as [channel][input][spectrum] so that the group leaves as 32-byte runs of
+// the X-engine's [c][i][t] order: the corner turn happens here.
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <vector>
+
+#include "fengine.h"
+#include "xe_internal.h"
+#include "xengine.h"
+
+struct fe_ctx {
+  int n_inputs = 0, n_chans = 0, taps = 0, shift = 0;
+  unsigned flags = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  float* h = nullptr;         // [taps * M] prototype filter
+  float2* w = nullptr;        // [M] exp(-2 pi j n / M)
+  uint32_t* gain = nullptr;   // [C][N]
+};
+
+namespace xe {
+namespace {
+
+constexpr int kFeGroup = 32;  // spectra per CTA
+
+struct FeArgs {
+  const int8_t* adc;
+  long long adc_stride;
+  const float* h;
+  const float2* w;
+  const uint32_t* gain;
+  uint8_t* out;
+  long long out_stride;
+  int32_t* v18;
+  float* spec;
+  unsigned long long* power;
+  int n_inputs, n_spectra, taps, layout;
+  int lo_is_real, vec_in, vec_out;
+  float scale;  // 2^-(shift + 1): Eq. 2's halving and the 18-bit scaling
+};
+
+__host__ __device__ constexpr int fe_threads(int logm) {
+  return (1 << logm) / 8 > 256 ? (1 << logm) / 8 : 256;
+}
+__host__ __device__ constexpr int fe_pad(int n) { return n + (n >> 3); }
+template <int LOGM>
+constexpr size_t fe_smem_bytes() {
+  constexpr int M = 1 << LOGM;
+  constexpr int units = fe_threads(LOGM) / (M / 8);
+  return (size_t)units * fe_pad(M) * sizeof(float2) + (size_t)(M / 2) * 2 * kFeGroup;
+}
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 mul_mj(float2 a) { return make_float2(a.y, -a.x); }  // a * (-j)
+
+// Y[k] = sum_n x[n] (-j)^(nk)
+__device__ __forceinline__ void dft4(float2& x0, float2& x1, float2& x2, float2& x3) {
+  const float2 t0 = cadd(x0, x2), t1 = csub(x0, x2), t2 = cadd(x1, x3), t3 = mul_mj(csub(x1, x3));
+  x0 = cadd(t0, t2);
+  x2 = csub(t0, t2);
+  x1 = cadd(t1, t3);
+  x3 = csub(t1, t3);
+}
+
+// X[k] = sum_n a[n] W8^(nk), W8 = exp(-j pi / 4): two DFT4s of the even and
+// odd samples, joined with W8^k.
+__device__ __forceinline__ void dft8(float2 (&a)[8]) {
+  float2 e0 = a[0], e1 = a[2], e2 = a[4], e3 = a[6];
+  float2 o0 = a[1], o1 = a[3], o2 = a[5], o3 = a[7];
+  dft4(e0, e1, e2, e3);
+  dft4(o0, o1, o2, o3);
+  const float r = 0.70710678118654752f;
+  o1 = make_float2(r * (o1.x + o1.y), r * (o1.y - o1.x));    // * (1 - j) / sqrt2
+  o2 = mul_mj(o2);                                           // * -j
+  o3 = make_float2(r * (o3.y - o3.x), -r * (o3.x + o3.y));   // * (-1 - j) / sqrt2
+  a[0] = cadd(e0, o0);
+  a[4] = csub(e0, o0);
+  a[1] = cadd(e1, o1);
+  a[5] = csub(e1, o1);
+  a[2] = cadd(e2, o2);
+  a[6] = csub(e2, o2);
+  a[3] = cadd(e3, o3);
+  a[7] = csub(e3, o3);
+}
+
+// One Stockham pass of radix R over an M-point transform held in z (padded
+// indices): butterfly b reads z[b + j M/R], twiddles by
+// exp(-2 pi j (b mod Ns) r / (Ns R)), and writes the R outputs to
+// (b div Ns) Ns R + (b mod Ns) + r Ns.  Each of the M/8 threads of a unit
+// runs 8/R butterflies; loads and stores are separated by a CTA barrier.
+template <int M, int R>
+__device__ __forceinline__ void fft_pass(float2* z, int lt, int Ns, const float2* __restrict__ w) {
+  constexpr int B = 8 / R;       // butterflies per thread
+  constexpr int S = M / R;       // input stride
+  float2 v[8];
+#pragma unroll
+  for (int r = 0; r < B; ++r) {
+    const int b = lt + r * (M / 8);
+    const int k = b & (Ns - 1);
+#pragma unroll
+    for (int j = 0; j < R; ++j) v[r * R + j] = z[fe_pad(b + j * S)];
+    if (Ns > 1) {
+      const int step = k * (M / (R * Ns));
+#pragma unroll
+      for (int j = 1; j < R; ++j) v[r * R + j] = cmul(v[r * R + j], __ldg(&w[j * step]));
+    }
+  }
+  if constexpr (R == 8) {
+    dft8(v);
+  } else if constexpr (R == 4) {
+    dft4(v[0], v[1], v[2], v[3]);
+    dft4(v[4], v[5], v[6], v[7]);
+  } else {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const float2 a0 = v[2 * r], a1 = v[2 * r + 1];
+      v[2 * r] = cadd(a0, a1);
+      v[2 * r + 1] = csub(a0, a1);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < B; ++r) {
+    const int b = lt + r * (M / 8);
+    const int k = b & (Ns - 1);
+    const int base = (b - k) * R + k;
+#pragma unroll
+    for (int j = 0; j < R; ++j) z[fe_pad(base + j * Ns)] = v[r * R + j];
+  }
+  __syncthreads();
+}
+
+// p = v g (fix_36_24) -> rne(p / 2^21) clamped to the fix_4_3 range
+__device__ __forceinline__ int equalise(int v, uint32_t g) {
+  const long long p = (long long)v * (long long)g;
+  const long long fl = p >> 21;
+  const long long rem = p - (fl << 21);
+  const long long q = fl + ((rem > (1ll << 20)) || (rem == (1ll << 20) && (fl & 1)) ? 1 : 0);
+  return (int)(q < -7 ? -7 : (q > 7 ? 7 : q));
+}
+
+__device__ __forceinline__ int clamp18(float x) {
+  const int v = __float2int_rn(x);
+  return v < -(1 << 17) ? -(1 << 17) : (v > (1 << 17) - 1 ? (1 << 17) - 1 : v);
+}
+
+template <int LOGM>
+__global__ void __launch_bounds__(fe_threads(LOGM)) fengine_kernel(FeArgs a) {
+  constexpr int M = 1 << LOGM, C = M / 2;
+  constexpr int TPU = M / 8;                 // threads per FFT unit
+  constexpr int NT = fe_threads(LOGM);
+  constexpr int U = NT / TPU;                // units per CTA
+  constexpr int PM = fe_pad(M);
+  constexpr int P8 = LOGM / 3, REM = LOGM % 3;
+  extern __shared__ __align__(16) uint8_t fe_smem[];
+  const int tid = threadIdx.x, u = tid / TPU, lt = tid % TPU;
+  float2* z = reinterpret_cast<float2*>(fe_smem) + u * PM;
+  uint8_t* codes = fe_smem + (size_t)U * PM * sizeof(float2);  // [C][2][kFeGroup]
+  const int i0 = 2 * blockIdx.y;
+  const bool has1 = i0 + 1 < a.n_inputs;
+  const int N = a.n_inputs;
+  const int t0 = blockIdx.x * kFeGroup;
+  const int ng = min(kFeGroup, a.n_spectra - t0);
+
+  uint32_t g[4][2];
+  unsigned long long pw[4][2];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int nu = lt + k * TPU;
+    g[k][0] = a.gain[(long long)nu * N + i0];
+    g[k][1] = has1 ? a.gain[(long long)nu * N + i0 + 1] : 0u;
+    pw[k][0] = pw[k][1] = 0ull;
+  }
+
+  for (int sb = 0; sb < ng; sb += U) {
+    const int s = sb + u;
+    const bool active = s < ng;
+    const long long t = t0 + s;
+    // ---- polyphase filter: y[n] = sum_q h[q M + n] x[(t + q) M + n]
+    float y0[8], y1[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) y0[r] = y1[r] = 0.f;
+    if (active) {
+      const int8_t* x0 = a.adc + (long long)i0 * a.adc_stride + t * M + 8 * lt;
+      const int8_t* x1 = x0 + a.adc_stride;
+      for (int q = 0; q < a.taps; ++q) {
+        const float4 hA = __ldg(reinterpret_cast<const float4*>(a.h + q * M + 8 * lt));
+        const float4 hB = __ldg(reinterpret_cast<const float4*>(a.h + q * M + 8 * lt + 4));
+        const float hq[8] = {hA.x, hA.y, hA.z, hA.w, hB.x, hB.y, hB.z, hB.w};
+        int8_t s0[8], s1[8];
+        if (a.vec_in) {
+          const int2 w0 = __ldg(reinterpret_cast<const int2*>(x0 + (long long)q * M));
+          const int2 w1 = has1 ? __ldg(reinterpret_cast<const int2*>(x1 + (long long)q * M))
+                               : make_int2(0, 0);
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            s0[r] = (int8_t)(w0.x >> (8 * r));
+            s0[r + 4] = (int8_t)(w0.y >> (8 * r));
+            s1[r] = (int8_t)(w1.x >> (8 * r));
+            s1[r + 4] = (int8_t)(w1.y >> (8 * r));
+          }
+        } else {
+#pragma unroll
+          for (int r = 0; r < 8; ++r) {
+            s0[r] = x0[(long long)q * M + r];
+            s1[r] = has1 ? x1[(long long)q * M + r] : (int8_t)0;
+          }
+        }
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+          y0[r] = fmaf(hq[r], (float)s0[r], y0[r]);
+          y1[r] = fmaf(hq[r], (float)s1[r], y1[r]);
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 8; ++r) z[fe_pad(8 * lt + r)] = make_float2(y0[r], y1[r]);
+    __syncthreads();
+    // ---- FFT of y_2k + j y_2k+1 (natural order out)
+#pragma unroll
+    for (int p = 0; p < P8; ++p) fft_pass<M, 8>(z, lt, 1 << (3 * p), a.w);
+    if constexpr (REM == 2) fft_pass<M, 4>(z, lt, 1 << (3 * P8), a.w);
+    if constexpr (REM == 1) fft_pass<M, 2>(z, lt, 1 << (3 * P8), a.w);
+    // ---- Eq. 2 separation, 18-bit rounding, equaliser
+    if (active) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int nu = lt + k * TPU;
+        const float2 zp = z[fe_pad(nu)], zm = z[fe_pad((M - nu) & (M - 1))];
+        const float X[2][2] = {{(zp.x + zm.x) * a.scale, (zp.y - zm.y) * a.scale},
+                               {(zp.y + zm.y) * a.scale, (zm.x - zp.x) * a.scale}};
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          if (j == 1 && !has1) break;
+          const int vr = clamp18(X[j][0]), vi = clamp18(X[j][1]);
+          const long long e = ((t * C + nu) * N + i0 + j) * 2;
+          if (a.spec) *reinterpret_cast<float2*>(a.spec + e) = make_float2(X[j][0], X[j][1]);
+          if (a.v18) *reinterpret_cast<int2*>(a.v18 + e) = make_int2(vr, vi);
+          pw[k][j] += (unsigned long long)((long long)vr * vr + (long long)vi * vi);
+          const int qr = equalise(vr, g[k][j]) & 0xF, qi = equalise(vi, g[k][j]) & 0xF;
+          codes[(nu * 2 + j) * kFeGroup + s] = (uint8_t)(a.lo_is_real ? (qi << 4) | qr : (qr << 4) | qi);
+        }
+      }
+    }
+    __syncthreads();
+  }
+
+  // ---- codes out
+  const int nj = has1 ? 2 : 1;
+  if (a.out) {
+    if (a.layout == CORR_L_CIT) {
+      if (a.vec_out && ng == kFeGroup) {
+        for (int p = tid; p < C * 2 * 2; p += NT) {
+          const int row = p >> 1, half = p & 1, nu = row >> 1, j = row & 1;
+          if (j >= nj) continue;
+          const uint4 v = *reinterpret_cast<const uint4*>(codes + row * kFeGroup + 16 * half);
+          *reinterpret_cast<uint4*>(a.out + ((long long)nu * N + i0 + j) * a.out_stride + t0 +
+                                    16 * half) = v;
+        }
+      } else {
+        for (int e = tid; e < C * 2 * ng; e += NT) {
+          const int row = e / ng, s = e - row * ng, nu = row >> 1, j = row & 1;
+          if (j >= nj) continue;
+          a.out[((long long)nu * N + i0 + j) * a.out_stride + t0 + s] = codes[row * kFeGroup + s];
+        }
+      }
+    } else {  // [t][c][i]
+      for (int e = tid; e < ng * C; e += NT) {
+        const int s = e / C, nu = e - s * C;
+        uint8_t* o = a.out + ((long long)(t0 + s) * C + nu) * N + i0;
+        o[0] = codes[(nu * 2) * kFeGroup + s];
+        if (has1) o[1] = codes[(nu * 2 + 1) * kFeGroup + s];
+      }
+    }
+  }
+  if (a.power) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int nu = lt + k * TPU;
+      // every unit of the CTA summed its own spectra: add them all
+      atomicAdd(a.power + (long long)nu * N + i0, pw[k][0]);
+      if (has1) atomicAdd(a.power + (long long)nu * N + i0 + 1, pw[k][1]);
+    }
+  }
+}
+
+template <int LOGM>
+cudaError_t fe_launch(const FeArgs& a, int n_pairs, cudaStream_t s) {
+  constexpr size_t smem = fe_smem_bytes<LOGM>();
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(fengine_kernel<LOGM>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const dim3 grid((a.n_spectra + kFeGroup - 1) / kFeGroup, n_pairs);
+  fengine_kernel<LOGM><<<grid, fe_threads(LOGM), smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+bool fe_is_device(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+void fe_free(fe_ctx* f) {
+  if (!f) return;
+  if (f->stream) cudaStreamSynchronize(f->stream);
+  cudaFree(f->h);
+  cudaFree(f->w);
+  cudaFree(f->gain);
+  if (f->own_stream && f->stream) cudaStreamDestroy(f->stream);
+  delete f;
+}
+
+}  // namespace
+}  // namespace xe
+
+using namespace xe;
+
+extern "C" {
+
+int fe_create(int n_inputs, int n_chans, int taps, int shift, unsigned flags, void* stream,
+              fe_ctx** out) {
+  TraceRange trace_("fe_create");
+  if (!out) return CORR_EINVAL;
+  *out = nullptr;
+  if (n_inputs < 1 || n_inputs > 131070 || n_chans < 16 || n_chans > 2048 ||
+      (n_chans & (n_chans - 1)) || taps < 1 || taps > 16 || shift < 0 || shift > 24 ||
+      (flags & ~FE_F_LO_IS_REAL))
+    return CORR_EINVAL;
+  fe_ctx* f = new (std::nothrow) fe_ctx;
+  if (!f) return CORR_ENOMEM;
+  f->n_inputs = n_inputs;
+  f->n_chans = n_chans;
+  f->taps = taps;
+  f->shift = shift;
+  f->flags = flags;
+  const int M = 2 * n_chans;
+  const long long L = (long long)taps * M;
+  // prototype: Hamming window times sinc, in FP64, rounded to FP32
+  std::vector<float> h(L);
+  const double pi = 3.14159265358979323846;
+  for (long long m = 0; m < L; ++m) {
+    const double win = 0.54 - 0.46 * std::cos(2.0 * pi * (double)m / (double)(L - 1));
+    const double x = ((double)m - (double)(L - 1) / 2.0) / (double)M;
+    const double sinc = x == 0.0 ? 1.0 : std::sin(pi * x) / (pi * x);
+    h[m] = (float)(win * sinc);
+  }
+  std::vector<float2> w(M);
+  for (int n = 0; n < M; ++n) {
+    const double ang = -2.0 * pi * (double)n / (double)M;
+    w[n] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+  }
+  int st = CORR_OK;
+  do {
+    if (stream) {
+      f->stream = (cudaStream_t)stream;
+    } else {
+      if (cudaStreamCreateWithFlags(&f->stream, cudaStreamNonBlocking) != cudaSuccess) { st = CORR_ECUDA; break; }
+      f->own_stream = true;
+    }
+    if (cudaMalloc(&f->h, L * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&f->w, M * sizeof(float2)) != cudaSuccess ||
+        cudaMalloc(&f->gain, (size_t)n_chans * n_inputs * sizeof(uint32_t)) != cudaSuccess) {
+      st = CORR_ENOMEM;
+      break;
+    }
+    if (cudaMemcpy(f->h, h.data(), L * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(f->w, w.data(), M * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(f->gain, 0, (size_t)n_chans * n_inputs * sizeof(uint32_t)) != cudaSuccess) {
+      st = CORR_ECUDA;
+      break;
+    }
+  } while (0);
+  if (st != CORR_OK) {
+    fe_free(f);
+    return st;
+  }
+  *out = f;
+  return CORR_OK;
+}
+
+int fe_set_gains(fe_ctx* f, const uint32_t* gain) {
+  if (!f || !gain) return CORR_EINVAL;
+  const size_t n = (size_t)f->n_chans * f->n_inputs;
+  if (fe_is_device(gain)) {
+    // checked on the host: a device table is copied back once
+    std::vector<uint32_t> hg(n);
+    if (cudaMemcpy(hg.data(), gain, n * sizeof(uint32_t), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return CORR_ECUDA;
+    for (uint32_t v : hg)
+      if (v >= (1u << 18)) return CORR_EINVAL;
+  } else {
+    for (size_t k = 0; k < n; ++k)
+      if (gain[k] >= (1u << 18)) return CORR_EINVAL;
+  }
+  if (cudaMemcpyAsync(f->gain, gain, n * sizeof(uint32_t), cudaMemcpyDefault, f->stream) != cudaSuccess ||
+      cudaStreamSynchronize(f->stream) != cudaSuccess)
+    return CORR_ECUDA;
+  return CORR_OK;
+}
+
+int fe_channelise(fe_ctx* f, const int8_t* adc, long long adc_stride, int n_spectra, uint8_t* out,
+                  int layout, long long out_stride, int32_t* v18, float* spec, int64_t* power) {
+  TraceRange trace_("fe_channelise");
+  if (!f || !adc || n_spectra < 1) return CORR_EINVAL;
+  const int M = 2 * f->n_chans;
+  if (adc_stride < (long long)(n_spectra + f->taps - 1) * M) return CORR_EINVAL;
+  if (layout != CORR_L_CIT && layout != CORR_L_TCI) return CORR_EINVAL;
+  if (out && layout == CORR_L_CIT && out_stride < n_spectra) return CORR_EINVAL;
+  if (!fe_is_device(adc) || (out && !fe_is_device(out)) || (v18 && !fe_is_device(v18)) ||
+      (spec && !fe_is_device(spec)) || (power && !fe_is_device(power)))
+    return CORR_EINVAL;
+  if ((v18 && reinterpret_cast<uintptr_t>(v18) % 8) || (spec && reinterpret_cast<uintptr_t>(spec) % 8) ||
+      (power && reinterpret_cast<uintptr_t>(power) % 8))
+    return CORR_EINVAL;
+  FeArgs a{};
+  a.adc = adc;
+  a.adc_stride = adc_stride;
+  a.h = f->h;
+  a.w = f->w;
+  a.gain = f->gain;
+  a.out = out;
+  a.out_stride = out_stride;
+  a.v18 = v18;
+  a.spec = spec;
+  a.power = reinterpret_cast<unsigned long long*>(power);
+  a.n_inputs = f->n_inputs;
+  a.n_spectra = n_spectra;
+  a.taps = f->taps;
+  a.layout = layout;
+  a.lo_is_real = (f->flags & FE_F_LO_IS_REAL) ? 1 : 0;
+  a.vec_in = reinterpret_cast<uintptr_t>(adc) % 8 == 0 && adc_stride % 8 == 0;
+  a.vec_out = out && layout == CORR_L_CIT && reinterpret_cast<uintptr_t>(out) % 16 == 0 &&
+              out_stride % 16 == 0;
+  a.scale = std::ldexp(1.0f, -(f->shift + 1));
+  const int pairs = (f->n_inputs + 1) / 2;
+  cudaError_t e;
+  switch (M) {
+    case 32: e = fe_launch<5>(a, pairs, f->stream); break;
+    case 64: e = fe_launch<6>(a, pairs, f->stream); break;
+    case 128: e = fe_launch<7>(a, pairs, f->stream); break;
+    case 256: e = fe_launch<8>(a, pairs, f->stream); break;
+    case 512: e = fe_launch<9>(a, pairs, f->stream); break;
+    case 1024: e = fe_launch<10>(a, pairs, f->stream); break;
+    case 2048: e = fe_launch<11>(a, pairs, f->stream); break;
+    case 4096: e = fe_launch<12>(a, pairs, f->stream); break;
+    default: return CORR_EINVAL;
+  }
+  return e == cudaSuccess ? CORR_OK : CORR_ECUDA;
+}
+
+int fe_gains_from_power(const int64_t* power, int n_chans, int n_inputs, long long n_spectra,
+                        double target_rms, uint32_t* gain) {
+  if (!power || !gain || n_chans < 1 || n_inputs < 1 || n_spectra < 1 || !(target_rms > 0.0))
+    return CORR_EINVAL;
+  const long long n = (long long)n_chans * n_inputs;
+  for (long long k = 0; k < n; ++k) {
+    if (power[k] < 0) return CORR_EINVAL;
+    if (power[k] == 0) {
+      gain[k] = 0;
+      continue;
+    }
+    const double rms = std::sqrt((double)power[k] / (2.0 * (double)n_spectra));
+    const double g = std::nearbyint(target_rms * 2097152.0 / rms);
+    gain[k] = g < 1.0 ? 1u : (g > 262143.0 ? 262143u : (uint32_t)g);
+  }
+  return CORR_OK;
+}
+
+int fe_sync(fe_ctx* f) {
+  if (!f) return CORR_EINVAL;
+  return cudaStreamSynchronize(f->stream) == cudaSuccess ? CORR_OK : CORR_ECUDA;
+}
+
+void fe_destroy(fe_ctx* f) { fe_free(f); }
+
+}  // extern "C"

@@ -171,3 +171,26 @@ def block_device(kind: str, seed: int, n_inputs: int, n_chans: int, n_time: int,
             n = tn * N * C * bps
             out[t0 * N * C * bps: t0 * N * C * bps + n].copy_(flat)
     return out
+
+
+def adc(seed: int, n_inputs: int, n_samples: int, sigma: float = 16.0, tones=(),
+        common: float = 0.0) -> np.ndarray:
+    """Seeded 8-bit ADC streams for the F-engine, int8 [n_inputs][n_samples].
+
+    Each input is receiver noise N(0, sigma^2) plus, when ``common`` > 0, a
+    noise signal N(0, common^2) shared by every input delayed by i samples
+    (a broadband sky source seen through cables of different lengths, as in
+    the paper's delay test, Sec. 3), plus the listed tones: (amplitude,
+    cycles per sample, phase) added to every input.  Rounded half-to-even and
+    clipped to the 8-bit range [-127, 127] of the digitiser.
+    """
+    rng = np.random.default_rng(seed)
+    v = rng.normal(0.0, sigma, (n_inputs, n_samples))
+    if common > 0:
+        s = rng.normal(0.0, common, n_samples + n_inputs)
+        for i in range(n_inputs):
+            v[i] += s[n_inputs - i:n_inputs - i + n_samples]
+    n = np.arange(n_samples, dtype=np.float64)
+    for amp, f, ph in tones:
+        v += amp * np.cos(2 * np.pi * f * n + ph)[None, :]
+    return np.clip(np.rint(v), -127, 127).astype(np.int8)

@@ -1,5 +1,5 @@
 """The C-ABI library builds, loads and exports every function that
-include/xengine.h declares (no GPU needed: no compute call is made)."""
+include/*.h declares (no GPU needed: no compute call is made)."""
 import ctypes
 import os
 import re
@@ -8,13 +8,16 @@ import subprocess
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "xengine.h")
+HEADERS = [os.path.join(ROOT, "include", h) for h in sorted(os.listdir(os.path.join(ROOT, "include")))
+           if h.endswith(".h")]
 
 
 def _declared():
-    src = open(HEADER).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(corr_\w+)\s*\(", src, flags=re.M)))
+    names = set()
+    for h in HEADERS:
+        src = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        names |= set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*((?:corr|fe)_\w+)\s*\(", src, flags=re.M))
+    return sorted(names)
 
 
 @pytest.fixture(scope="module")
@@ -26,7 +29,7 @@ def lib_path():
 def test_header_declares_the_boundary():
     names = _declared()
     for n in ("corr_create", "corr_push", "corr_dump", "corr_normalise", "corr_sync",
-              "corr_destroy", "corr_strerror"):
+              "corr_destroy", "corr_strerror", "fe_create", "fe_channelise", "fe_gains_from_power"):
         assert n in names
 
 
@@ -68,3 +71,26 @@ def test_binding_has_no_cpu_fallback():
         if f.endswith(".py"):
             src = open(os.path.join(pkg, f)).read()
             assert "import oracle" not in src and "from oracle" not in src, f
+
+
+def test_fengine_host_calls(lib_path):
+    """fe_create rejects bad shapes before any device work; the Eq. 3 gain
+    rule (pure host code) equals the oracle's bit for bit."""
+    import numpy as np
+    from oracle import fengine as ofe
+    from paper_1904_07778_gb300 import fengine as fe
+    from paper_1904_07778_gb300 import xengine as xe
+    lib = ctypes.CDLL(lib_path)
+    lib.fe_create.argtypes = [ctypes.c_int] * 4 + [ctypes.c_uint, ctypes.c_void_p, ctypes.c_void_p]
+    f = ctypes.c_void_p()
+    for args in ((0, 64, 4, 0), (4, 100, 4, 0), (4, 8, 4, 0), (4, 4096, 4, 0), (4, 64, 0, 0),
+                 (4, 64, 17, 0), (4, 64, 4, 25), (4, 64, 4, -1)):
+        assert lib.fe_create(*args, 0, None, ctypes.byref(f)) == xe.CORR_EINVAL, args
+    assert lib.fe_create(4, 64, 4, 0, 2, None, ctypes.byref(f)) == xe.CORR_EINVAL
+    rng = np.random.default_rng(8)
+    P = rng.integers(0, 1 << 40, (64, 12))
+    P[3, 4] = 0
+    P[5, 6] = 1
+    for n, target in ((1000, 2.5), (7, 2.0), (123456, 3.0)):
+        got = fe.fe_gains_from_power(P, n, target)
+        assert np.array_equal(got.astype(np.int64), ofe.gains_from_power(P, n, target))
