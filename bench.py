@@ -24,6 +24,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -75,7 +76,28 @@ WORKLOADS["service4"] = dict(
          "blocks, Poisson arrivals at 80% of measured capacity, admitted by an HBM budget",
     service=dict(arrays=[32, 192, 512], C=2048, bits=8, layout=0, kmin=12, kmax=18,
                  block=4096, requests=200, load=0.8, budget_gb=170))
+# The F-engine front end (PFB + FFT + Eq. 2 + equaliser) of the cylinder
+# array on its own, and the whole FX chain per block.
+WORKLOADS["fengine192"] = dict(
+    desc="F-engine, cylinder array: 192 8-bit ADC inputs, 1024 channels (2048-sample spectra), "
+         "4-tap Hamming-sinc PFB, 8192 spectra/block, 4-bit codes out in [c][i][t] order, "
+         "Gaussian ADC noise sigma 16 (2 distinct 3.2 GB blocks cycled)",
+    fengine=dict(N=192, C=1024, taps=4, T=8192))
+WORKLOADS["fengine192s"] = dict(
+    desc="F-engine, cylinder array, 512-spectrum slice: 192 8-bit ADC inputs, 1024 channels, "
+         "4-tap PFB, 512 spectra/block (202 MB blocks, larger than L2; profiling size)",
+    fengine=dict(N=192, C=1024, taps=4, T=512))
+WORKLOADS["fx192"] = dict(
+    desc="FX chain, cylinder array: 192 8-bit ADC inputs -> F-engine (1024 channels, 4-tap PFB, "
+         "equaliser to 4 bits, [c][i][t]) -> X-engine (all baselines, int64) per block of 8192 "
+         "spectra, Gaussian ADC noise plus a common delayed sky signal",
+    fengine=dict(N=192, C=1024, taps=4, T=8192), fx=True, N=192, C=1024, T=8192)
 METRIC = "X-engine correlator Tops/s at 192 inputs (8 int ops per complex MAC, lower triangle incl. autos)"
+FX_METRIC = ("FX correlator Tops/s at 192 inputs: 8-bit ADC samples in, int64 visibilities out "
+             "(X-engine ops: 8 per complex MAC, lower triangle incl. autos)")
+FE_METRIC = ("F-engine throughput: 8-bit ADC samples/s channelised (192 inputs, 1024 channels, "
+             "4-tap PFB, 4-bit codes out)")
+ADC_RATE = 250e6  # real samples per second per input (Sec. 2)
 PAPER_TOPS = 1.2  # xGPU on one GTX 690 core, >= 96 dual-pol stations (Sec. 2.2); context only
 REAL_TIME_RATE = 125e6  # spectra x channels per second per input at 250 MSPS real sampling
 
@@ -615,6 +637,354 @@ def run_service(args, w, world, rank, local):
     return 0
 
 
+def fe_flops_per_spectrum(C, taps):
+    """Algorithmic FLOPs of one input's spectrum: the taps multiply-adds per
+    sample of the filter (2 taps M) and half of one complex M-point FFT at
+    the usual 5 M log2 M."""
+    M = 2 * C
+    return 2 * taps * M + 2.5 * M * math.log2(M)
+
+
+def fp32_peak_tflops(n_sm, sm_mhz):
+    """FP32 CUDA-core peak: SMs x 128 FP32 lanes x 2 FLOPs per FMA x clock."""
+    return n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def adc_device(seed, n_inputs, n_samples, dev, sigma=16.0, common=0.0):
+    """Gaussian 8-bit ADC streams drawn on the device (optionally a common
+    signal delayed by i samples on input i), in 16-input chunks."""
+    import torch
+    g = torch.Generator(device=dev)
+    g.manual_seed(seed)
+    a = torch.empty((n_inputs, n_samples), dtype=torch.int8, device=dev)
+    sky = torch.randn(n_samples + n_inputs, generator=g, device=dev) * common if common > 0 else None
+    for i in range(0, n_inputs, 16):
+        k = min(16, n_inputs - i)
+        v = torch.randn((k, n_samples), generator=g, device=dev) * sigma
+        if sky is not None:
+            for j in range(k):
+                v[j] += sky[n_inputs - (i + j):n_inputs - (i + j) + n_samples]
+        a[i:i + k] = torch.clamp(torch.round(v), -127, 127).to(torch.int8)
+        del v
+    return a
+
+
+def fe_cpu_baseline(cfg, seconds, fx=False):
+    """The F-engine oracle (and the X-engine oracle for the FX chain) on a
+    bounded sample: one input pair (all inputs for FX) and as many spectra as
+    fit in about `seconds`.  numpy: one host core."""
+    import numpy as np
+    import oracle
+    from oracle import fengine as ofe
+    from paper_1904_07778_gb300 import synth
+    C, taps = cfg["C"], cfg["taps"]
+    n = cfg["N"] if fx else 2
+    M = 2 * C
+    gain = np.full((C, n), 3000, dtype=np.int64)
+
+    def one(ts):
+        adc = synth.adc(7, n, (ts + taps - 1) * M)
+        t0 = time.perf_counter()
+        out = ofe.fengine(adc, C, taps, ts, gain)
+        if fx:
+            oracle.correlate(np.ascontiguousarray(out["bytes"]).reshape(-1), n, C, ts,
+                             layout=oracle.L_TCI, threads=1)
+        return time.perf_counter() - t0
+
+    cal = one(4) / 4
+    ts = int(max(4, min(cfg["T"], seconds / max(cal, 1e-9))))
+    el = one(ts)
+    return ts, n, el
+
+
+def run_fengine(args, w, world, rank, local):
+    """The F-engine alone: device-resident ADC blocks in, 4-bit codes out."""
+    import numpy as np
+    import torch
+    from paper_1904_07778_gb300 import build
+    build.build()
+    from paper_1904_07778_gb300.fengine import FEngine, fe_gains_from_power
+
+    cfg = w["fengine"]
+    N, C, taps, T = cfg["N"], cfg["C"], cfg["taps"], cfg["T"]
+    M = 2 * C
+    S = (T + taps - 1) * M
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)  # torch work, events and both engines on one stream
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks = [adc_device(1000 * rank + k, N, S, dev) for k in range(2)]
+    out = torch.empty(C * N * T, dtype=torch.uint8, device=dev)
+    power = torch.zeros((C, N), dtype=torch.int64, device=dev)
+    f = FEngine(N, C, taps, 0, stream=stream.cuda_stream)
+    # calibration pass: Eq. 3 gains from the measured power
+    f.set_gains(np.ones((C, N), dtype=np.uint32))
+    f.channelise(blocks[0], T, power=power)
+    f.sync()
+    f.set_gains(fe_gains_from_power(power.cpu().numpy(), T, 2.5))
+    for k in range(args.warmup):
+        f.channelise(blocks[k % 2], T, out=out)
+    torch.cuda.synchronize()
+    barrier(world)
+    sampler = ClockSampler(local) if not args.no_clocks else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(args.steps):
+        f.channelise(blocks[k % 2], T, out=out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop() if sampler else None
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world)
+
+    # end to end: pinned ADC block in, codes out, every step; step k's copy
+    # in and step k-1's copy out overlap step k's channelisation
+    e2e = None
+    if not args.no_e2e:
+        h_adc = torch.empty((N, S), dtype=torch.int8, pin_memory=True)
+        h_adc.copy_(blocks[0])
+        h_out = [torch.empty(C * N * T, dtype=torch.uint8, pin_memory=True) for _ in range(2)]
+        d_out = [out, torch.empty_like(out)]
+        cin, cout = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+        ev_in = [torch.cuda.Event() for _ in range(2)]
+        ev_used = [torch.cuda.Event() for _ in range(2)]
+        ev_out = [torch.cuda.Event() for _ in range(2)]
+
+        def step(k):
+            s_ = k % 2
+            cin.wait_event(ev_used[s_])
+            with torch.cuda.stream(cin):
+                blocks[s_].copy_(h_adc, non_blocking=True)
+            ev_in[s_].record(cin)
+            stream.wait_event(ev_in[s_])
+            stream.wait_event(ev_out[s_])
+            f.channelise(blocks[s_], T, out=d_out[s_])
+            ev_used[s_].record(stream)
+            cout.wait_event(ev_used[s_])
+            with torch.cuda.stream(cout):
+                h_out[s_].copy_(d_out[s_], non_blocking=True)
+            ev_out[s_].record(cout)
+            if k > 0:
+                ev_out[(k - 1) % 2].synchronize()
+
+        for k in range(3):
+            step(k)
+        torch.cuda.synchronize()
+        ke = max(3, min(args.steps, args.e2e_steps))
+        barrier(world)
+        t0 = time.perf_counter()
+        for k in range(ke):
+            step(k)
+        ev_out[(ke - 1) % 2].synchronize()
+        e2e_ms = max_over_ranks(1e3 * (time.perf_counter() - t0) / ke, world)
+        e2e = {"value": world * N * T * M / (e2e_ms * 1e-3) / 1e9, "unit": "Gsample/s",
+               "h2d_bytes_per_step": N * S, "d2h_bytes_per_step": C * N * T, "ms_per_step": e2e_ms,
+               "steps": ke, "pipeline": "step k's ADC copy-in and step k-1's code copy-out overlap "
+               "step k's channelisation"}
+        del h_adc, h_out
+    f.close()
+    if rank != 0:
+        return 0
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        ts, n_in, el = fe_cpu_baseline(cfg, min(args.cpu_seconds, 20.0))
+        cpu = {"value": n_in * ts * M / el / 1e9, "unit": "Gsample/s", "cores": 1, "kind": "oracle",
+               "sample": "%d of %d inputs x %d of %d spectra (%.1f s, numpy float64, one core)"
+                         % (n_in, N, ts, T, el)}
+    flops = N * T * fe_flops_per_spectrum(C, taps)
+    tflops = flops / (ms * 1e-3) / 1e12
+    mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    peak = fp32_peak_tflops(n_sm, mhz)
+    traffic = kernel_traffic("fengine_kernel", N * T)
+    line = {
+        "metric": FE_METRIC, "value": world * N * T * M / (ms * 1e-3) / 1e9, "unit": "Gsample/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded Gaussian ADC noise, device-generated)",
+        "config": {"workload": w["desc"], "n_inputs": N, "n_chans": C, "taps": taps, "n_spectra": T,
+                   "output": "4-bit codes, [c][i][t]",
+                   "l2": "inputs larger than L2 (2 distinct %.1f GB blocks cycled)" % (N * S / 1e9),
+                   "parallelism": "%d GPU" % world},
+        "x_real_time": T * M / ADC_RATE / (ms * 1e-3),
+        "gpu_launches": args.steps,
+        "roofline": {"bound": "alu", "achieved": tflops, "peak": peak, "unit": "TFLOP/s",
+                     "frac": tflops / peak, "traffic": traffic, "kernel": "fengine_kernel",
+                     "peak_note": "FP32: %d SMs x 128 lanes x 2 x %.0f MHz (median SM clock "
+                                  "under load)" % (n_sm, mhz),
+                     "flops_per_launch": flops,
+                     "hbm_gbs": (N * S + C * N * T) / (ms * 1e-3) / 1e9},
+        "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_reference_fe(args, w, world, rank):
+    """The oracle F-engine (and X-engine, for the FX chain) on the host cores,
+    a bounded sample per step."""
+    if rank != 0:
+        return 0
+    cfg = w["fengine"]
+    fx = "fx" in w
+    budget = max(0.2, min(3.0, args.cpu_seconds, 120.0 / max(1, args.steps + args.warmup)))
+    M = 2 * cfg["C"]
+    for _ in range(args.warmup):
+        fe_cpu_baseline(cfg, budget, fx)
+    runs = [fe_cpu_baseline(cfg, budget, fx) for _ in range(args.steps)]
+    ts, n_in = runs[0][0], runs[0][1]
+    tot = sum(r[2] for r in runs)
+    if fx:
+        v, unit, metric = (8 * n_in * (n_in + 1) // 2 * cfg["C"] * ts * args.steps / tot / 1e12,
+                           "Tops/s", FX_METRIC)
+    else:
+        v, unit, metric = n_in * ts * M * args.steps / tot / 1e9, "Gsample/s", FE_METRIC
+    sample = "%d of %d inputs x %d of %d spectra per step (numpy float64, one core)" % (
+        n_in, cfg["N"], ts, cfg["T"])
+    line = {"impl": "reference", "metric": metric, "value": v, "unit": unit, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": w["desc"], "sample": sample},
+            "cpu_baseline": {"value": v, "unit": unit, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_fx(args, w, world, rank, local):
+    """ADC samples in, visibilities out: F-engine then X-engine per block."""
+    import numpy as np
+    import torch
+    from paper_1904_07778_gb300 import build
+    build.build()
+    from paper_1904_07778_gb300.fengine import FEngine, fe_gains_from_power
+    from paper_1904_07778_gb300.xengine import CORR_L_CIT, Correlator
+
+    cfg = w["fengine"]
+    N, C, taps, T = cfg["N"], cfg["C"], cfg["taps"], cfg["T"]
+    M = 2 * C
+    S = (T + taps - 1) * M
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)  # torch work, events and both engines on one stream
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks = [adc_device(2000 * rank + k, N, S, dev, sigma=14.0, common=8.0) for k in range(2)]
+    codes = torch.empty(C * N * T, dtype=torch.uint8, device=dev)
+    nb = N * (N + 1) // 2
+    vis = torch.empty((C, nb, 2), dtype=torch.int64, device=dev)
+    power = torch.zeros((C, N), dtype=torch.int64, device=dev)
+    f = FEngine(N, C, taps, 0, stream=stream.cuda_stream)
+    cor = Correlator(N, C, T, bits=4, layout=CORR_L_CIT, stream=stream.cuda_stream)
+    f.set_gains(np.ones((C, N), dtype=np.uint32))
+    f.channelise(blocks[0], T, power=power)
+    f.sync()
+    f.set_gains(fe_gains_from_power(power.cpu().numpy(), T, 2.5))
+
+    def step(k, x_only=False, f_only=False):
+        if not x_only:
+            f.channelise(blocks[k % 2], T, out=codes)
+        if not f_only:
+            cor.push(codes)
+            cor.dump_into(vis, reset=True)
+
+    def timed(**kw):
+        for k in range(args.warmup):
+            step(k, **kw)
+        torch.cuda.synchronize()
+        barrier(world)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in range(args.steps):
+            step(k, **kw)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return max_over_ranks(e0.elapsed_time(e1) / args.steps, world)
+
+    sampler = ClockSampler(local) if not args.no_clocks else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    ms = timed()
+    clocks = sampler.stop() if sampler else None
+    ms_f = timed(f_only=True)
+    ms_x = timed(x_only=True)
+
+    e2e = None
+    if not args.no_e2e:
+        h_adc = torch.empty((N, S), dtype=torch.int8, pin_memory=True)
+        h_adc.copy_(blocks[0])
+        hv = [torch.empty((C, nb, 2), dtype=torch.int64, pin_memory=True) for _ in range(2)]
+        cin = torch.cuda.Stream(dev)
+        ev_in = [torch.cuda.Event() for _ in range(2)]
+        ev_used = [torch.cuda.Event() for _ in range(2)]
+
+        def step_host(k):
+            s_ = k % 2
+            cin.wait_event(ev_used[s_])
+            with torch.cuda.stream(cin):
+                blocks[s_].copy_(h_adc, non_blocking=True)
+            ev_in[s_].record(cin)
+            stream.wait_event(ev_in[s_])
+            f.channelise(blocks[s_], T, out=codes)
+            ev_used[s_].record(stream)
+            cor.push(codes)
+            cor.dump_async(hv[s_], reset=True)
+            if k > 0:
+                cor.dump_wait()
+
+        for k in range(3):
+            step_host(k)
+        cor.dump_wait()
+        torch.cuda.synchronize()
+        ke = max(3, min(args.steps, args.e2e_steps))
+        barrier(world)
+        t0 = time.perf_counter()
+        for k in range(ke):
+            step_host(k)
+        cor.dump_wait()
+        e2e_ms = max_over_ranks(1e3 * (time.perf_counter() - t0) / ke, world)
+        e2e = {"value": world * ops_per_block(w) / (e2e_ms * 1e-3) / 1e12, "unit": "Tops/s",
+               "h2d_bytes_per_step": N * S, "d2h_bytes_per_step": C * nb * 16,
+               "ms_per_step": e2e_ms, "steps": ke,
+               "pipeline": "ADC copy-in on its own stream, overlapped dumps (corr_dump_async)"}
+        del h_adc, hv
+    f.close()
+    cor.close()
+    if rank != 0:
+        return 0
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        ts, n_in, el = fe_cpu_baseline(cfg, min(args.cpu_seconds, 20.0), fx=True)
+        cpu = {"value": 8 * n_in * (n_in + 1) // 2 * C * ts / el / 1e12, "unit": "Tops/s", "cores": 1,
+               "kind": "oracle", "sample": "%d inputs x %d of %d spectra (%.1f s, F-engine numpy "
+               "float64 + X-engine C oracle, one core)" % (n_in, ts, T, el)}
+    flops = N * T * fe_flops_per_spectrum(C, taps)
+    mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    fpk = fp32_peak_tflops(n_sm, mhz)
+    line = {
+        "metric": FX_METRIC, "value": world * ops_per_block(w) / (ms * 1e-3) / 1e12, "unit": "Tops/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+u8",
+        "data": "synthetic (seeded Gaussian ADC noise + common delayed signal, device-generated)",
+        "config": {"workload": w["desc"], "n_inputs": N, "n_chans": C, "taps": taps, "n_spectra": T,
+                   "l2": "inputs larger than L2 (2 distinct %.1f GB ADC blocks cycled)" % (N * S / 1e9),
+                   "parallelism": "%d GPU" % world},
+        "x_real_time": T * M / ADC_RATE / (ms * 1e-3),
+        "phase_ms_per_step": {"fengine": ms_f, "xengine_push_dump": ms_x},
+        "gpu_launches": 2 * args.steps,
+        "roofline": {"bound": "alu", "achieved": flops / (ms_f * 1e-3) / 1e12, "peak": fpk,
+                     "unit": "TFLOP/s", "frac": flops / (ms_f * 1e-3) / 1e12 / fpk,
+                     "traffic": kernel_traffic("fengine_kernel", N * T), "kernel": "fengine_kernel",
+                     "peak_note": "FP32: %d SMs x 128 lanes x 2 x %.0f MHz" % (n_sm, mhz)},
+        "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -634,8 +1004,14 @@ def main():
         ap.error("--warmup must be >= 3")
     w = WORKLOADS[args.workload]
     world, rank, local = dist_setup()
-    if args.impl == "reference":
+    if args.impl == "reference" and "fengine" in w:
+        rc = run_reference_fe(args, w, world, rank)
+    elif args.impl == "reference":
         rc = run_reference(args, w, world, rank)
+    elif "fx" in w:
+        rc = run_fx(args, w, world, rank, local)
+    elif "fengine" in w:
+        rc = run_fengine(args, w, world, rank, local)
     elif "batch" in w:
         rc = run_batch(args, w, world, rank, local)
     elif "service" in w:

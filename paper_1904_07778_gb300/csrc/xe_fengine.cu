@@ -99,26 +99,41 @@ __device__ __forceinline__ void dft8(float2 (&a)[8]) {
   a[7] = csub(e3, o3);
 }
 
-// One Stockham pass of radix R over an M-point transform held in z (padded
-// indices): butterfly b reads z[b + j M/R], twiddles by
-// exp(-2 pi j (b mod Ns) r / (Ns R)), and writes the R outputs to
-// (b div Ns) Ns R + (b mod Ns) + r Ns.  Each of the M/8 threads of a unit
-// runs 8/R butterflies; loads and stores are separated by a CTA barrier.
+// Twiddles of one Stockham pass for one thread: butterfly b = lt + r M/8
+// multiplies its input j by exp(-2 pi j (b mod Ns) j / (Ns R)), for
+// j = 1 .. R-1.  They do not depend on the spectrum, so a thread loads them
+// once (from the FP64-rounded table) and keeps them in registers.
 template <int M, int R>
-__device__ __forceinline__ void fft_pass(float2* z, int lt, int Ns, const float2* __restrict__ w) {
+__device__ __forceinline__ void load_twiddles(float2 (&tw)[7], int lt, int Ns,
+                                              const float2* __restrict__ w) {
+  constexpr int B = 8 / R;
+#pragma unroll
+  for (int r = 0; r < B; ++r) {
+    const int k = (lt + r * (M / 8)) & (Ns - 1);
+    const int step = k * (M / (R * Ns));
+#pragma unroll
+    for (int j = 1; j < R; ++j) tw[r * (R - 1) + j - 1] = __ldg(&w[j * step]);
+  }
+}
+
+// One Stockham pass of radix R over an M-point transform held in z (padded
+// indices): butterfly b reads z[b + j M/R], applies its twiddles, and writes
+// the R outputs to (b div Ns) Ns R + (b mod Ns) + r Ns.  Each of the M/8
+// threads of a unit runs 8/R butterflies; loads and stores are separated by
+// a CTA barrier.
+template <int M, int R>
+__device__ __forceinline__ void fft_pass(float2* z, int lt, int Ns, const float2 (&tw)[7]) {
   constexpr int B = 8 / R;       // butterflies per thread
   constexpr int S = M / R;       // input stride
   float2 v[8];
 #pragma unroll
   for (int r = 0; r < B; ++r) {
     const int b = lt + r * (M / 8);
-    const int k = b & (Ns - 1);
 #pragma unroll
     for (int j = 0; j < R; ++j) v[r * R + j] = z[fe_pad(b + j * S)];
     if (Ns > 1) {
-      const int step = k * (M / (R * Ns));
 #pragma unroll
-      for (int j = 1; j < R; ++j) v[r * R + j] = cmul(v[r * R + j], __ldg(&w[j * step]));
+      for (int j = 1; j < R; ++j) v[r * R + j] = cmul(v[r * R + j], tw[r * (R - 1) + j - 1]);
     }
   }
   if constexpr (R == 8) {
@@ -146,22 +161,64 @@ __device__ __forceinline__ void fft_pass(float2* z, int lt, int Ns, const float2
   __syncthreads();
 }
 
-// p = v g (fix_36_24) -> rne(p / 2^21) clamped to the fix_4_3 range
-__device__ __forceinline__ int equalise(int v, uint32_t g) {
-  const long long p = (long long)v * (long long)g;
-  const long long fl = p >> 21;
-  const long long rem = p - (fl << 21);
-  const long long q = fl + ((rem > (1ll << 20)) || (rem == (1ll << 20) && (fl & 1)) ? 1 : 0);
-  return (int)(q < -7 ? -7 : (q > 7 ? 7 : q));
+// p = v g (fix_36_24) -> rne(p / 2^21) clamped to the fix_4_3 range, in
+// 32-bit arithmetic: |v| >= vsat = ceil(7.5 2^21 / g) means |p| >= 7.5 2^21,
+// which rounds to 8 or more and saturates at 7; below it |p| < 2^24.
+__device__ __forceinline__ int equalise(int v, int g, int vsat) {
+  const int av = v < 0 ? -v : v;
+  const int p = (int)((unsigned)v * (unsigned)g);  // used only when it did not wrap
+  const int fl = p >> 21;                           // floor(p / 2^21)
+  const int rem = p & 0x1FFFFF;
+  const int q = fl + ((rem > 0x100000) || (rem == 0x100000 && (fl & 1)) ? 1 : 0);
+  return av >= vsat ? (v < 0 ? -7 : 7) : q;
+}
+__host__ __device__ constexpr int saturation_threshold(uint32_t g) {
+  return g == 0 ? 0x7FFFFFFF : (int)((15728640u + g - 1) / g);  // 7.5 2^21 = 15728640
 }
 
-__device__ __forceinline__ int clamp18(float x) {
-  const int v = __float2int_rn(x);
-  return v < -(1 << 17) ? -(1 << 17) : (v > (1 << 17) - 1 ? (1 << 17) - 1 : v);
+// clamp(rne(x), -2^17, 2^17 - 1): clamping first keeps |x| < 2^22, where
+// adding 1.5 2^23 rounds x to the nearest integer, ties to even, and the
+// sum's low bits hold it.
+__device__ __forceinline__ int round18(float x) {
+  const float c = fminf(fmaxf(x, -131072.0f), 131071.0f);
+  return __float_as_int(c + 12582912.0f) - 0x4B400000;
+}
+
+// Byte r of w (biased: w holds x ^ 0x80 per byte, x the int8 sample) as the
+// float x, exactly: the byte becomes the low mantissa bits of 1.5 * 2^23,
+// and subtracting 1.5 * 2^23 + 128 leaves x (every step exact below 2^24).
+__device__ __forceinline__ float biased_byte_to_float(uint32_t w, int r) {
+  return __int_as_float((int)__byte_perm(w, 0x4B400000u, 0x7650u + (unsigned)r)) - 12583040.0f;
+}
+
+// One tap of the filter for 8 consecutive samples of both inputs of a pair:
+// y += h x, in FP32 fused multiply-adds.
+__device__ __forceinline__ void fir_tap(float (&y0)[8], float (&y1)[8], const float (&h)[8],
+                                        const int8_t* x0, const int8_t* x1, bool has1, int vec_in) {
+  if (vec_in) {
+    const int2 w0 = __ldg(reinterpret_cast<const int2*>(x0));
+    const int2 w1 = has1 ? __ldg(reinterpret_cast<const int2*>(x1)) : make_int2(0, 0);
+    const uint32_t b0[2] = {(uint32_t)w0.x ^ 0x80808080u, (uint32_t)w0.y ^ 0x80808080u};
+    const uint32_t b1[2] = {(uint32_t)w1.x ^ 0x80808080u, (uint32_t)w1.y ^ 0x80808080u};
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      y0[r] = fmaf(h[r], biased_byte_to_float(b0[r >> 2], r & 3), y0[r]);
+      y1[r] = fmaf(h[r], biased_byte_to_float(b1[r >> 2], r & 3), y1[r]);
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      y0[r] = fmaf(h[r], (float)x0[r], y0[r]);
+      y1[r] = fmaf(h[r], has1 ? (float)x1[r] : 0.f, y1[r]);
+    }
+  }
 }
 
 template <int LOGM>
-__global__ void __launch_bounds__(fe_threads(LOGM)) fengine_kernel(FeArgs a) {
+#ifndef XE_FE_MIN_BLOCKS
+#define XE_FE_MIN_BLOCKS 1
+#endif
+__global__ void __launch_bounds__(fe_threads(LOGM), XE_FE_MIN_BLOCKS) fengine_kernel(FeArgs a) {
   constexpr int M = 1 << LOGM, C = M / 2;
   constexpr int TPU = M / 8;                 // threads per FFT unit
   constexpr int NT = fe_threads(LOGM);
@@ -171,21 +228,46 @@ __global__ void __launch_bounds__(fe_threads(LOGM)) fengine_kernel(FeArgs a) {
   extern __shared__ __align__(16) uint8_t fe_smem[];
   const int tid = threadIdx.x, u = tid / TPU, lt = tid % TPU;
   float2* z = reinterpret_cast<float2*>(fe_smem) + u * PM;
-  uint8_t* codes = fe_smem + (size_t)U * PM * sizeof(float2);  // [C][2][kFeGroup]
+  uint8_t* codes = fe_smem + (size_t)U * PM * sizeof(float2);  // [kFeGroup][C][2]
   const int i0 = 2 * blockIdx.y;
   const bool has1 = i0 + 1 < a.n_inputs;
   const int N = a.n_inputs;
   const int t0 = blockIdx.x * kFeGroup;
   const int ng = min(kFeGroup, a.n_spectra - t0);
 
-  uint32_t g[4][2];
+  // per-thread constants: the filter taps of its 8 samples (up to 4 taps in
+  // registers) and the twiddles of every pass
+  float hr[4][8];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    if (q < a.taps) {
+      const float4 hA = __ldg(reinterpret_cast<const float4*>(a.h + q * M + 8 * lt));
+      const float4 hB = __ldg(reinterpret_cast<const float4*>(a.h + q * M + 8 * lt + 4));
+      hr[q][0] = hA.x; hr[q][1] = hA.y; hr[q][2] = hA.z; hr[q][3] = hA.w;
+      hr[q][4] = hB.x; hr[q][5] = hB.y; hr[q][6] = hB.z; hr[q][7] = hB.w;
+    } else {
+#pragma unroll
+      for (int r = 0; r < 8; ++r) hr[q][r] = 0.f;
+    }
+  }
+  float2 tw[P8 > 1 ? P8 - 1 : 1][7], twl[7];
+#pragma unroll
+  for (int p = 1; p < P8; ++p) load_twiddles<M, 8>(tw[p - 1], lt, 1 << (3 * p), a.w);
+  if constexpr (REM == 2) load_twiddles<M, 4>(twl, lt, 1 << (3 * P8), a.w);
+  if constexpr (REM == 1) load_twiddles<M, 2>(twl, lt, 1 << (3 * P8), a.w);
+
+  int g[4][2], vsat[4][2];
   unsigned long long pw[4][2];
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     const int nu = lt + k * TPU;
-    g[k][0] = a.gain[(long long)nu * N + i0];
-    g[k][1] = has1 ? a.gain[(long long)nu * N + i0 + 1] : 0u;
-    pw[k][0] = pw[k][1] = 0ull;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const uint32_t gj = (j == 0 || has1) ? a.gain[(long long)nu * N + i0 + j] : 0u;
+      g[k][j] = (int)gj;
+      vsat[k][j] = saturation_threshold(gj);
+      pw[k][j] = 0ull;
+    }
   }
 
   for (int sb = 0; sb < ng; sb += U) {
@@ -199,44 +281,35 @@ __global__ void __launch_bounds__(fe_threads(LOGM)) fengine_kernel(FeArgs a) {
     if (active) {
       const int8_t* x0 = a.adc + (long long)i0 * a.adc_stride + t * M + 8 * lt;
       const int8_t* x1 = x0 + a.adc_stride;
-      for (int q = 0; q < a.taps; ++q) {
+// taps 0..3 with their coefficients in registers (static indices), then
+      // any further taps with coefficients from the table
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (q < a.taps) fir_tap(y0, y1, hr[q], x0 + (long long)q * M, x1 + (long long)q * M, has1, a.vec_in);
+      for (int q = 4; q < a.taps; ++q) {
+        float hq[8];
         const float4 hA = __ldg(reinterpret_cast<const float4*>(a.h + q * M + 8 * lt));
         const float4 hB = __ldg(reinterpret_cast<const float4*>(a.h + q * M + 8 * lt + 4));
-        const float hq[8] = {hA.x, hA.y, hA.z, hA.w, hB.x, hB.y, hB.z, hB.w};
-        int8_t s0[8], s1[8];
-        if (a.vec_in) {
-          const int2 w0 = __ldg(reinterpret_cast<const int2*>(x0 + (long long)q * M));
-          const int2 w1 = has1 ? __ldg(reinterpret_cast<const int2*>(x1 + (long long)q * M))
-                               : make_int2(0, 0);
-#pragma unroll
-          for (int r = 0; r < 4; ++r) {
-            s0[r] = (int8_t)(w0.x >> (8 * r));
-            s0[r + 4] = (int8_t)(w0.y >> (8 * r));
-            s1[r] = (int8_t)(w1.x >> (8 * r));
-            s1[r + 4] = (int8_t)(w1.y >> (8 * r));
-          }
-        } else {
-#pragma unroll
-          for (int r = 0; r < 8; ++r) {
-            s0[r] = x0[(long long)q * M + r];
-            s1[r] = has1 ? x1[(long long)q * M + r] : (int8_t)0;
-          }
-        }
-#pragma unroll
-        for (int r = 0; r < 8; ++r) {
-          y0[r] = fmaf(hq[r], (float)s0[r], y0[r]);
-          y1[r] = fmaf(hq[r], (float)s1[r], y1[r]);
-        }
+        hq[0] = hA.x; hq[1] = hA.y; hq[2] = hA.z; hq[3] = hA.w;
+        hq[4] = hB.x; hq[5] = hB.y; hq[6] = hB.z; hq[7] = hB.w;
+        fir_tap(y0, y1, hq, x0 + (long long)q * M, x1 + (long long)q * M, has1, a.vec_in);
       }
     }
 #pragma unroll
     for (int r = 0; r < 8; ++r) z[fe_pad(8 * lt + r)] = make_float2(y0[r], y1[r]);
     __syncthreads();
+    // the next iteration's newest frame comes from DRAM: ask for it now
+    if (active && s + U < ng) {
+      const int8_t* nx = a.adc + (long long)i0 * a.adc_stride + (t + U + a.taps - 1) * M + 8 * lt;
+      asm volatile("prefetch.global.L1 [%0];" ::"l"(nx));
+      if (has1) asm volatile("prefetch.global.L1 [%0];" ::"l"(nx + a.adc_stride));
+    }
     // ---- FFT of y_2k + j y_2k+1 (natural order out)
+    fft_pass<M, 8>(z, lt, 1, twl);  // first pass: no twiddles
 #pragma unroll
-    for (int p = 0; p < P8; ++p) fft_pass<M, 8>(z, lt, 1 << (3 * p), a.w);
-    if constexpr (REM == 2) fft_pass<M, 4>(z, lt, 1 << (3 * P8), a.w);
-    if constexpr (REM == 1) fft_pass<M, 2>(z, lt, 1 << (3 * P8), a.w);
+    for (int p = 1; p < P8; ++p) fft_pass<M, 8>(z, lt, 1 << (3 * p), tw[p - 1]);
+    if constexpr (REM == 2) fft_pass<M, 4>(z, lt, 1 << (3 * P8), twl);
+    if constexpr (REM == 1) fft_pass<M, 2>(z, lt, 1 << (3 * P8), twl);
     // ---- Eq. 2 separation, 18-bit rounding, equaliser
     if (active) {
 #pragma unroll
@@ -248,44 +321,53 @@ __global__ void __launch_bounds__(fe_threads(LOGM)) fengine_kernel(FeArgs a) {
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
           if (j == 1 && !has1) break;
-          const int vr = clamp18(X[j][0]), vi = clamp18(X[j][1]);
-          const long long e = ((t * C + nu) * N + i0 + j) * 2;
-          if (a.spec) *reinterpret_cast<float2*>(a.spec + e) = make_float2(X[j][0], X[j][1]);
-          if (a.v18) *reinterpret_cast<int2*>(a.v18 + e) = make_int2(vr, vi);
-          pw[k][j] += (unsigned long long)((long long)vr * vr + (long long)vi * vi);
-          const int qr = equalise(vr, g[k][j]) & 0xF, qi = equalise(vi, g[k][j]) & 0xF;
-          codes[(nu * 2 + j) * kFeGroup + s] = (uint8_t)(a.lo_is_real ? (qi << 4) | qr : (qr << 4) | qi);
+          const int vr = round18(X[j][0]), vi = round18(X[j][1]);
+          if (a.spec || a.v18) {
+            const long long e = ((t * C + nu) * N + i0 + j) * 2;
+            if (a.spec) *reinterpret_cast<float2*>(a.spec + e) = make_float2(X[j][0], X[j][1]);
+            if (a.v18) *reinterpret_cast<int2*>(a.v18 + e) = make_int2(vr, vi);
+          }
+          if (a.power) pw[k][j] += (unsigned long long)((long long)vr * vr + (long long)vi * vi);
+          const int qr = equalise(vr, g[k][j], vsat[k][j]) & 0xF;
+          const int qi = equalise(vi, g[k][j], vsat[k][j]) & 0xF;
+          codes[(s * C + nu) * 2 + j] = (uint8_t)(a.lo_is_real ? (qi << 4) | qr : (qr << 4) | qi);
         }
       }
     }
     __syncthreads();
   }
 
-  // ---- codes out
+  // ---- codes out.  Staging is [spectrum][channel][input], so a thread
+  // gathers one (channel, input) row of 32 spectra with conflict-free byte
+  // loads (consecutive threads, consecutive rows) and stores it as two
+  // 16-byte pieces of the [c][i][t] output.
   const int nj = has1 ? 2 : 1;
   if (a.out) {
     if (a.layout == CORR_L_CIT) {
-      if (a.vec_out && ng == kFeGroup) {
-        for (int p = tid; p < C * 2 * 2; p += NT) {
-          const int row = p >> 1, half = p & 1, nu = row >> 1, j = row & 1;
-          if (j >= nj) continue;
-          const uint4 v = *reinterpret_cast<const uint4*>(codes + row * kFeGroup + 16 * half);
-          *reinterpret_cast<uint4*>(a.out + ((long long)nu * N + i0 + j) * a.out_stride + t0 +
-                                    16 * half) = v;
-        }
-      } else {
-        for (int e = tid; e < C * 2 * ng; e += NT) {
-          const int row = e / ng, s = e - row * ng, nu = row >> 1, j = row & 1;
-          if (j >= nj) continue;
-          a.out[((long long)nu * N + i0 + j) * a.out_stride + t0 + s] = codes[row * kFeGroup + s];
+      for (int row = tid; row < 2 * C; row += NT) {
+        const int nu = row >> 1, j = row & 1;
+        if (j >= nj) continue;
+        uint8_t* o = a.out + ((long long)nu * N + i0 + j) * a.out_stride + t0;
+        if (a.vec_out && ng == kFeGroup) {
+          uint32_t wv[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            wv[q] = (uint32_t)codes[(4 * q) * 2 * C + row] |
+                    ((uint32_t)codes[(4 * q + 1) * 2 * C + row] << 8) |
+                    ((uint32_t)codes[(4 * q + 2) * 2 * C + row] << 16) |
+                    ((uint32_t)codes[(4 * q + 3) * 2 * C + row] << 24);
+          *reinterpret_cast<uint4*>(o) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+          *reinterpret_cast<uint4*>(o + 16) = make_uint4(wv[4], wv[5], wv[6], wv[7]);
+        } else {
+          for (int s = 0; s < ng; ++s) o[s] = codes[s * 2 * C + row];
         }
       }
     } else {  // [t][c][i]
       for (int e = tid; e < ng * C; e += NT) {
         const int s = e / C, nu = e - s * C;
         uint8_t* o = a.out + ((long long)(t0 + s) * C + nu) * N + i0;
-        o[0] = codes[(nu * 2) * kFeGroup + s];
-        if (has1) o[1] = codes[(nu * 2 + 1) * kFeGroup + s];
+        o[0] = codes[(s * C + nu) * 2];
+        if (has1) o[1] = codes[(s * C + nu) * 2 + 1];
       }
     }
   }

@@ -9,8 +9,8 @@ import ctypes
 
 import numpy as np
 
-from .xengine import (CORR_L_CIT, CORR_L_TCI, CORR_OK, CorrError, _lib,  # noqa: F401
-                      _ptr_and_size)
+from .xengine import (_CUDA_STREAM_LEGACY, CORR_L_CIT, CORR_L_TCI, CORR_OK, CorrError,  # noqa: F401
+                      _lib, _ptr_and_size)
 
 FE_F_LO_IS_REAL = 1
 EXPORTS = ["fe_create", "fe_set_gains", "fe_channelise", "fe_gains_from_power", "fe_sync",
@@ -47,10 +47,12 @@ class FEngine:
     """One channeliser: PFB + FFT + Eq. 2 + 18-bit rounding + equaliser."""
 
     def __init__(self, n_inputs, n_chans, taps=4, shift=0, lo_is_real=False, stream=None):
+        if stream is None:  # torch's current stream (its default stream is the legacy one)
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream or _CUDA_STREAM_LEGACY
         out = _P()
         flags = FE_F_LO_IS_REAL if lo_is_real else 0
-        st = _lib.fe_create(n_inputs, n_chans, taps, shift, flags, _P(stream) if stream else None,
-                            ctypes.byref(out))
+        st = _lib.fe_create(n_inputs, n_chans, taps, shift, flags, _P(stream), ctypes.byref(out))
         if st != CORR_OK:
             raise CorrError(st, "fe_create")
         self._f = out
