@@ -194,3 +194,25 @@ def adc(seed: int, n_inputs: int, n_samples: int, sigma: float = 16.0, tones=(),
     for amp, f, ph in tones:
         v += amp * np.cos(2 * np.pi * f * n + ph)[None, :]
     return np.clip(np.rint(v), -127, 127).astype(np.int8)
+
+
+def packets(block: np.ndarray, n_fids: int, n_inputs_pkt: int, n_xids: int, n_chans_pkt: int,
+            block_index: int = 0) -> list:
+    """Cut a [T][C][N] block of packed 4-bit samples into the F-engine's UDP
+    payloads (Sec. 2.3): an 8-byte header (MCNT big-endian in 6 bytes, Fid,
+    Xid), 8 stacked spectra of n_chans_pkt x n_inputs_pkt bytes, and an
+    8-byte trailer (4 zero bytes, then the CRC-32 of header and payload from
+    zlib, big-endian).  Packets come out MCNT by MCNT, Fid-major."""
+    import zlib
+    T = block.shape[0]
+    per = T // 8
+    out = []
+    for slot in range(per):
+        mcnt = block_index * per + slot
+        for fid in range(n_fids):
+            for xid in range(n_xids):
+                pay = block[8 * slot:8 * slot + 8, xid * n_chans_pkt:(xid + 1) * n_chans_pkt,
+                            fid * n_inputs_pkt:(fid + 1) * n_inputs_pkt]
+                body = mcnt.to_bytes(6, "big") + bytes([fid, xid]) + np.ascontiguousarray(pay).tobytes()
+                out.append(body + b"\0\0\0\0" + (zlib.crc32(body) & 0xFFFFFFFF).to_bytes(4, "big"))
+    return out
