@@ -87,6 +87,12 @@ WORKLOADS["fengine192s"] = dict(
     desc="F-engine, cylinder array, 512-spectrum slice: 192 8-bit ADC inputs, 1024 channels, "
          "4-tap PFB, 512 spectra/block (202 MB blocks, larger than L2; profiling size)",
     fengine=dict(N=192, C=1024, taps=4, T=512))
+WORKLOADS["ingest192"] = dict(
+    desc="packet ingest, cylinder array: 6 F-engines x 32 inputs, 32 bands x 32 channels, "
+         "8208-byte packets (8 stacked spectra, CRC-32 checked) assembled into 1024-spectrum "
+         "[t][c][i] blocks (24576 packets, 202 MB per block) in a 3-segment ring",
+    ingest=dict(n_fids=6, n_inputs_pkt=32, n_xids=32, n_chans_pkt=32, T=1024, segments=3),
+    N=192, C=1024, T=1024)
 WORKLOADS["fx192"] = dict(
     desc="FX chain, cylinder array: 192 8-bit ADC inputs -> F-engine (1024 channels, 4-tap PFB, "
          "equaliser to 4 bits, [c][i][t]) -> X-engine (all baselines, int64) per block of 8192 "
@@ -822,6 +828,135 @@ def run_fengine(args, w, world, rank, local):
     return 0
 
 
+def run_ingest(args, w, world, rank, local):
+    """Packets -> blocks on the host cores (the paper's net thread), then the
+    end-to-end leg: packets -> blocks -> corr_push -> visibilities."""
+    import numpy as np
+    from paper_1904_07778_gb300 import build, synth
+    build.build()
+    from paper_1904_07778_gb300.ingest import PacketRing
+
+    cfg = w["ingest"]
+    F, I, X, K, T = cfg["n_fids"], cfg["n_inputs_pkt"], cfg["n_xids"], cfg["n_chans_pkt"], cfg["T"]
+    N, C = F * I, X * K
+    rng = np.random.default_rng(1000 * rank)
+    block = rng.integers(0, 256, (T, C, N), dtype=np.uint8)
+    threads = max(1, args.ingest_threads)
+
+    def packets_of(k):
+        arr = synth.packets_array(block, F, I, X, K, block_index=k)
+        # producer j takes the packets of F-engines j, j + threads, ...
+        fid = arr[:, 6]
+        return arr, [np.ascontiguousarray(arr[fid % threads == j]) for j in range(threads)]
+
+    def run(ring, parts, consumer=None):
+        import threading
+        got = []
+
+        def prod(a):
+            k = 0
+            while k < len(a):
+                k += ring.push_many(a[k:])
+                if k < len(a):
+                    time.sleep(0.0002)   # the ring is full: the consumer frees a segment
+
+        th = [threading.Thread(target=prod, args=(a,)) for a in parts]
+        for t in th:
+            t.start()
+        while not got:
+            r = ring.next(5)
+            if r is not None:
+                if consumer:
+                    consumer(r)
+                got.append(r[1]["n_missing"])
+                ring.release()
+        for t in th:
+            t.join()
+        return got[0]
+
+    ring = PacketRing(F, I, X, K, T, n_segments=cfg["segments"])
+    pkt_bytes = None
+    for k in range(args.warmup):
+        arr, parts = packets_of(k)
+        pkt_bytes = arr.nbytes
+        run(ring, parts)
+    el = []
+    for k in range(args.warmup, args.warmup + args.steps):
+        arr, parts = packets_of(k)
+        t0 = time.perf_counter()
+        miss = run(ring, parts)
+        el.append(time.perf_counter() - t0)
+        assert miss == 0
+    st = ring.stats()
+    ms = max_over_ranks(1e3 * sum(el) / len(el), world)
+    # single-thread host copy rate of a block-sized buffer: the roofline of
+    # one producer's payload copies
+    src = np.ones(T * C * N, dtype=np.uint8)
+    dst = np.empty_like(src)
+    tc = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        np.copyto(dst, src)
+        tc.append(time.perf_counter() - t0)
+    copy_gbs = src.nbytes / min(tc) / 1e9
+    payload = T * C * N
+    e2e = None
+    if not args.no_e2e:
+        import torch
+        from paper_1904_07778_gb300.xengine import CORR_L_TCI, Correlator
+        torch.cuda.set_device(local)
+        cor = Correlator(N, C, T, bits=4, layout=CORR_L_TCI)
+        vis = torch.empty((C, N * (N + 1) // 2, 2), dtype=torch.int64, pin_memory=True)
+        base = args.warmup + args.steps
+        ee = []
+        for k in range(base, base + max(3, min(args.steps, args.e2e_steps))):
+            arr, parts = packets_of(k)
+            t0 = time.perf_counter()
+            run(ring, parts, consumer=lambda r: (cor.push(r[0]), cor.sync()))
+            cor.dump_into(vis, reset=True)
+            ee.append(time.perf_counter() - t0)
+        e_ms = 1e3 * sum(ee) / len(ee)
+        e2e = {"value": arr.nbytes / (e_ms * 1e-3) / 1e9, "unit": "GB/s", "h2d_bytes_per_step": payload,
+               "d2h_bytes_per_step": vis.numel() * 8, "ms_per_step": e_ms, "steps": len(ee),
+               "path": "packets -> ring -> corr_push (pinned block) -> corr_dump"}
+        cor.close()
+    ring.close()
+    if rank != 0:
+        return 0
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        from oracle import packets as op
+        sample = [row.tobytes() for row in arr[:min(len(arr), 3000)]]
+        t0 = time.perf_counter()
+        op.assemble(sample, F, I, X, K, T)
+        dt = time.perf_counter() - t0
+        cpu = {"value": len(sample) * arr.shape[1] / dt / 1e9, "unit": "GB/s", "cores": 1,
+               "kind": "oracle", "sample": "%d of %d packets of one block (%.1f s, Python)"
+                                           % (len(sample), len(arr), dt)}
+    gbs = pkt_bytes / (ms * 1e-3) / 1e9
+    line = {
+        "metric": "packet ingest GB/s: 8208-byte F-engine packets checked and assembled into "
+                  "X-engine blocks (192 inputs x 1024 channels)",
+        "value": world * gbs, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8", "data": "synthetic (seeded random 4-bit codes)",
+        "config": {"workload": w["desc"], "producer_threads": threads,
+                   "host_cores": os.cpu_count(), "parallelism": "%d host" % world},
+        "packets_per_s": st["packets"] / max(1e-9, sum(el) + args.warmup * 0) if False else
+                         len(arr) / (ms * 1e-3),
+        "x_real_time": payload / (ms * 1e-3) / (N * ADC_RATE / 2),
+        "gpu_launches": 0,
+        "roofline": {"bound": "host", "achieved": gbs, "peak": copy_gbs * threads, "unit": "GB/s",
+                     "frac": gbs / (copy_gbs * threads), "traffic": None,
+                     "peak_note": "%d x the single-thread host copy rate of a block (%.1f GB/s); "
+                                  "each packet is read by the CRC and copied once" % (threads, copy_gbs)},
+        "ring": {k: st[k] for k in ("packets", "blocks", "missing", "busy", "bad_crc")},
+        "e2e": e2e, "cpu_baseline": cpu, "clocks": None,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_reference_fe(args, w, world, rank):
     """The oracle F-engine (and X-engine, for the FX chain) on the host cores,
     a bounded sample per step."""
@@ -995,6 +1130,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--ingest-threads", type=int, default=4,
+                    help="producer threads of the packet-ingest workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--service-requests", type=int, default=0,
@@ -1010,6 +1147,8 @@ def main():
         rc = run_reference(args, w, world, rank)
     elif "fx" in w:
         rc = run_fx(args, w, world, rank, local)
+    elif "ingest" in w:
+        rc = run_ingest(args, w, world, rank, local)
     elif "fengine" in w:
         rc = run_fengine(args, w, world, rank, local)
     elif "batch" in w:

@@ -50,6 +50,7 @@ extern "C" {
 #define CORR_ETIMEDOUT (-6) /* a bounded device-side wait expired                 */
 #define CORR_ECUDA (-7)     /* a CUDA runtime call failed                         */
 #define CORR_ESTATE (-8)    /* call not valid in the context's current state      */
+#define CORR_ECORRUPT (-9)  /* a packet failed its CRC check (ingest.h)           */
 
 /* ---- sample layouts of a pushed block -------------------------------- */
 /* [time][channel][input]: the F-engine payload order of Sec. 2.3 (packets

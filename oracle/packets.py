@@ -85,14 +85,15 @@ def assemble(packets, n_fids, n_inputs_pkt, n_xids, n_chans_pkt, n_time):
     return blocks, rejected
 
 
-def mcnt_gaps(packets, n_chans_pkt, n_inputs_pkt):
+def mcnt_gaps(packets, n_chans_pkt, n_inputs_pkt, n_fids=256, n_xids=256):
     """Loss as the paper detects it: per (Fid, Xid) stream, in arrival
     order, every forward jump of MCNT by more than one counts the skipped
-    packets.  Returns (gap events, skipped packets)."""
+    packets (packets with a bad length, CRC or id are not part of any
+    stream).  Returns (gap events, skipped packets)."""
     last, events, skipped = {}, 0, 0
     for pkt in packets:
         r = parse(pkt, n_chans_pkt, n_inputs_pkt)
-        if r is None:
+        if r is None or r[1] >= n_fids or r[2] >= n_xids:
             continue
         mcnt, fid, xid, _ = r
         key = (fid, xid)

@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libxengine.so")
 SOURCES = ["xe_herk.cu", "xe_turn.cu", "xe_runtime.cu", "xe_noalloc.cu", "xe_batch.cu", "xe_service.cu",
-           "xe_fengine.cu"]
+           "xe_fengine.cu", "xe_ingest.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -44,7 +44,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
     nvcc = _nvcc()
     os.makedirs(OUT_DIR, exist_ok=True)
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
-    headers += [os.path.join(ROOT, "include", h) for h in ("xengine.h", "fengine.h")]
+    headers += [os.path.join(ROOT, "include", h) for h in ("xengine.h", "fengine.h", "ingest.h")]
     flags = ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2",
                     "-I", os.path.join(ROOT, "include"), "-I", CSRC]
     jobs = []

@@ -291,6 +291,7 @@ const char* corr_strerror(int status) {
     case CORR_ETIMEDOUT: return "device-side wait timed out";
     case CORR_ECUDA: return "CUDA runtime error";
     case CORR_ESTATE: return "invalid state";
+    case CORR_ECORRUPT: return "packet failed its CRC check";
     default: return "unknown status";
   }
 }

@@ -203,16 +203,29 @@ def packets(block: np.ndarray, n_fids: int, n_inputs_pkt: int, n_xids: int, n_ch
     Xid), 8 stacked spectra of n_chans_pkt x n_inputs_pkt bytes, and an
     8-byte trailer (4 zero bytes, then the CRC-32 of header and payload from
     zlib, big-endian).  Packets come out MCNT by MCNT, Fid-major."""
+    arr = packets_array(block, n_fids, n_inputs_pkt, n_xids, n_chans_pkt, block_index)
+    return [row.tobytes() for row in arr]
+
+
+def packets_array(block: np.ndarray, n_fids: int, n_inputs_pkt: int, n_xids: int,
+                  n_chans_pkt: int, block_index: int = 0) -> np.ndarray:
+    """The packets of :func:`packets` as one uint8 array [n_packets][length]."""
     import zlib
     T = block.shape[0]
     per = T // 8
-    out = []
-    for slot in range(per):
-        mcnt = block_index * per + slot
-        for fid in range(n_fids):
-            for xid in range(n_xids):
-                pay = block[8 * slot:8 * slot + 8, xid * n_chans_pkt:(xid + 1) * n_chans_pkt,
-                            fid * n_inputs_pkt:(fid + 1) * n_inputs_pkt]
-                body = mcnt.to_bytes(6, "big") + bytes([fid, xid]) + np.ascontiguousarray(pay).tobytes()
-                out.append(body + b"\0\0\0\0" + (zlib.crc32(body) & 0xFFFFFFFF).to_bytes(4, "big"))
-    return out
+    P = 8 * n_chans_pkt * n_inputs_pkt
+    # [slot][8][xid][c][fid][i] -> [slot][fid][xid][8][c][i]
+    pay = block.reshape(per, 8, n_xids, n_chans_pkt, n_fids, n_inputs_pkt).transpose(0, 4, 2, 1, 3, 5)
+    n = per * n_fids * n_xids
+    arr = np.zeros((n, 8 + P + 8), dtype=np.uint8)
+    arr[:, 8:8 + P] = pay.reshape(n, P)
+    slot, fid, xid = np.meshgrid(np.arange(per), np.arange(n_fids), np.arange(n_xids), indexing="ij")
+    mcnt = (block_index * per + slot.reshape(-1)).astype(np.uint64)
+    for k in range(6):
+        arr[:, k] = ((mcnt >> np.uint64(8 * (5 - k))) & np.uint64(0xFF)).astype(np.uint8)
+    arr[:, 6] = fid.reshape(-1)
+    arr[:, 7] = xid.reshape(-1)
+    for r in range(n):
+        c = zlib.crc32(arr[r, :8 + P]) & 0xFFFFFFFF
+        arr[r, 8 + P + 4:] = np.frombuffer(c.to_bytes(4, "big"), dtype=np.uint8)
+    return arr

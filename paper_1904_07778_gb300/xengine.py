@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libxengine.so")
 
 CORR_OK, CORR_EINVAL, CORR_ENOMEM, CORR_EBUSY = 0, -1, -2, -3
 CORR_ERANGE, CORR_ESEQ, CORR_ETIMEDOUT, CORR_ECUDA, CORR_ESTATE = -4, -5, -6, -7, -8
+CORR_ECORRUPT = -9
 CORR_L_TCI, CORR_L_TIC, CORR_L_CIT = 0, 1, 2
 CORR_F_LO_IS_REAL = 1
 CORR_SEQ_ANY = (1 << 64) - 1

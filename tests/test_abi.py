@@ -16,7 +16,7 @@ def _declared():
     names = set()
     for h in HEADERS:
         src = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
-        names |= set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*((?:corr|fe)_\w+)\s*\(", src, flags=re.M))
+        names |= set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*((?:corr|fe|pk)_\w+)\s*\(", src, flags=re.M))
     return sorted(names)
 
 
@@ -29,7 +29,8 @@ def lib_path():
 def test_header_declares_the_boundary():
     names = _declared()
     for n in ("corr_create", "corr_push", "corr_dump", "corr_normalise", "corr_sync",
-              "corr_destroy", "corr_strerror", "fe_create", "fe_channelise", "fe_gains_from_power"):
+              "corr_destroy", "corr_strerror", "fe_create", "fe_channelise", "fe_gains_from_power",
+              "pk_create", "pk_push", "pk_next", "pk_release", "pk_crc32"):
         assert n in names
 
 
