@@ -34,6 +34,7 @@ namespace xe {
 namespace {
 
 constexpr int kFeGroup = 32;  // spectra per CTA
+constexpr int kFeNB = 2;      // spectra a unit transforms side by side (shared barriers)
 
 struct FeArgs {
   const int8_t* adc;
@@ -59,7 +60,7 @@ template <int LOGM>
 constexpr size_t fe_smem_bytes() {
   constexpr int M = 1 << LOGM;
   constexpr int units = fe_threads(LOGM) / (M / 8);
-  return (size_t)units * fe_pad(M) * sizeof(float2) + (size_t)(M / 2) * 2 * kFeGroup;
+  return (size_t)kFeNB * units * fe_pad(M) * sizeof(float2) + (size_t)(M / 2) * 2 * kFeGroup;
 }
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
@@ -116,47 +117,55 @@ __device__ __forceinline__ void load_twiddles(float2 (&tw)[7], int lt, int Ns,
   }
 }
 
-// One Stockham pass of radix R over an M-point transform held in z (padded
-// indices): butterfly b reads z[b + j M/R], applies its twiddles, and writes
-// the R outputs to (b div Ns) Ns R + (b mod Ns) + r Ns.  Each of the M/8
-// threads of a unit runs 8/R butterflies; loads and stores are separated by
-// a CTA barrier.
-template <int M, int R>
-__device__ __forceinline__ void fft_pass(float2* z, int lt, int Ns, const float2 (&tw)[7]) {
+// One Stockham pass of radix R over NB independent M-point transforms held
+// in zs[] (padded indices): butterfly b reads z[b + j M/R], applies its
+// twiddles, and writes the R outputs to (b div Ns) Ns R + (b mod Ns) + r Ns.
+// Each of the M/8 threads of a unit runs 8/R butterflies per transform;
+// loads and stores are separated by a CTA barrier that the NB transforms
+// share.
+template <int M, int R, int NB>
+__device__ __forceinline__ void fft_pass(float2* const (&zs)[NB], int lt, int Ns,
+                                         const float2 (&tw)[7]) {
   constexpr int B = 8 / R;       // butterflies per thread
   constexpr int S = M / R;       // input stride
-  float2 v[8];
+  float2 v[NB][8];
 #pragma unroll
-  for (int r = 0; r < B; ++r) {
-    const int b = lt + r * (M / 8);
+  for (int e = 0; e < NB; ++e) {
 #pragma unroll
-    for (int j = 0; j < R; ++j) v[r * R + j] = z[fe_pad(b + j * S)];
-    if (Ns > 1) {
+    for (int r = 0; r < B; ++r) {
+      const int b = lt + r * (M / 8);
 #pragma unroll
-      for (int j = 1; j < R; ++j) v[r * R + j] = cmul(v[r * R + j], tw[r * (R - 1) + j - 1]);
+      for (int j = 0; j < R; ++j) v[e][r * R + j] = zs[e][fe_pad(b + j * S)];
+      if (Ns > 1) {
+#pragma unroll
+        for (int j = 1; j < R; ++j) v[e][r * R + j] = cmul(v[e][r * R + j], tw[r * (R - 1) + j - 1]);
+      }
     }
-  }
-  if constexpr (R == 8) {
-    dft8(v);
-  } else if constexpr (R == 4) {
-    dft4(v[0], v[1], v[2], v[3]);
-    dft4(v[4], v[5], v[6], v[7]);
-  } else {
+    if constexpr (R == 8) {
+      dft8(v[e]);
+    } else if constexpr (R == 4) {
+      dft4(v[e][0], v[e][1], v[e][2], v[e][3]);
+      dft4(v[e][4], v[e][5], v[e][6], v[e][7]);
+    } else {
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      const float2 a0 = v[2 * r], a1 = v[2 * r + 1];
-      v[2 * r] = cadd(a0, a1);
-      v[2 * r + 1] = csub(a0, a1);
+      for (int r = 0; r < 4; ++r) {
+        const float2 a0 = v[e][2 * r], a1 = v[e][2 * r + 1];
+        v[e][2 * r] = cadd(a0, a1);
+        v[e][2 * r + 1] = csub(a0, a1);
+      }
     }
   }
   __syncthreads();
 #pragma unroll
-  for (int r = 0; r < B; ++r) {
-    const int b = lt + r * (M / 8);
-    const int k = b & (Ns - 1);
-    const int base = (b - k) * R + k;
+  for (int e = 0; e < NB; ++e) {
 #pragma unroll
-    for (int j = 0; j < R; ++j) z[fe_pad(base + j * Ns)] = v[r * R + j];
+    for (int r = 0; r < B; ++r) {
+      const int b = lt + r * (M / 8);
+      const int k = b & (Ns - 1);
+      const int base = (b - k) * R + k;
+#pragma unroll
+      for (int j = 0; j < R; ++j) zs[e][fe_pad(base + j * Ns)] = v[e][r * R + j];
+    }
   }
   __syncthreads();
 }
@@ -227,8 +236,9 @@ __global__ void __launch_bounds__(fe_threads(LOGM), XE_FE_MIN_BLOCKS) fengine_ke
   constexpr int P8 = LOGM / 3, REM = LOGM % 3;
   extern __shared__ __align__(16) uint8_t fe_smem[];
   const int tid = threadIdx.x, u = tid / TPU, lt = tid % TPU;
-  float2* z = reinterpret_cast<float2*>(fe_smem) + u * PM;
-  uint8_t* codes = fe_smem + (size_t)U * PM * sizeof(float2);  // [kFeGroup][C][2]
+  float2* const zs[kFeNB] = {reinterpret_cast<float2*>(fe_smem) + u * PM,
+                             reinterpret_cast<float2*>(fe_smem) + (U + u) * PM};
+  uint8_t* codes = fe_smem + (size_t)kFeNB * U * PM * sizeof(float2);  // [kFeGroup][C][2]
   const int i0 = 2 * blockIdx.y;
   const bool has1 = i0 + 1 < a.n_inputs;
   const int N = a.n_inputs;
@@ -270,48 +280,58 @@ __global__ void __launch_bounds__(fe_threads(LOGM), XE_FE_MIN_BLOCKS) fengine_ke
     }
   }
 
-  for (int sb = 0; sb < ng; sb += U) {
-    const int s = sb + u;
-    const bool active = s < ng;
-    const long long t = t0 + s;
-    // ---- polyphase filter: y[n] = sum_q h[q M + n] x[(t + q) M + n]
-    float y0[8], y1[8];
+  for (int sb = 0; sb < ng; sb += kFeNB * U) {
 #pragma unroll
-    for (int r = 0; r < 8; ++r) y0[r] = y1[r] = 0.f;
-    if (active) {
-      const int8_t* x0 = a.adc + (long long)i0 * a.adc_stride + t * M + 8 * lt;
-      const int8_t* x1 = x0 + a.adc_stride;
-// taps 0..3 with their coefficients in registers (static indices), then
-      // any further taps with coefficients from the table
+    for (int e = 0; e < kFeNB; ++e) {
+      const int s = sb + e * U + u;
+      const bool active = s < ng;
+      const long long t = t0 + s;
+      // ---- polyphase filter: y[n] = sum_q h[q M + n] x[(t + q) M + n]
+      float y0[8], y1[8];
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
-        if (q < a.taps) fir_tap(y0, y1, hr[q], x0 + (long long)q * M, x1 + (long long)q * M, has1, a.vec_in);
-      for (int q = 4; q < a.taps; ++q) {
-        float hq[8];
-        const float4 hA = __ldg(reinterpret_cast<const float4*>(a.h + q * M + 8 * lt));
-        const float4 hB = __ldg(reinterpret_cast<const float4*>(a.h + q * M + 8 * lt + 4));
-        hq[0] = hA.x; hq[1] = hA.y; hq[2] = hA.z; hq[3] = hA.w;
-        hq[4] = hB.x; hq[5] = hB.y; hq[6] = hB.z; hq[7] = hB.w;
-        fir_tap(y0, y1, hq, x0 + (long long)q * M, x1 + (long long)q * M, has1, a.vec_in);
+      for (int r = 0; r < 8; ++r) y0[r] = y1[r] = 0.f;
+      if (active) {
+        const int8_t* x0 = a.adc + (long long)i0 * a.adc_stride + t * M + 8 * lt;
+        const int8_t* x1 = x0 + a.adc_stride;
+        // taps 0..3 with their coefficients in registers (static indices),
+        // then any further taps with coefficients from the table
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (q < a.taps)
+            fir_tap(y0, y1, hr[q], x0 + (long long)q * M, x1 + (long long)q * M, has1, a.vec_in);
+        for (int q = 4; q < a.taps; ++q) {
+          float hq[8];
+          const float4 hA = __ldg(reinterpret_cast<const float4*>(a.h + q * M + 8 * lt));
+          const float4 hB = __ldg(reinterpret_cast<const float4*>(a.h + q * M + 8 * lt + 4));
+          hq[0] = hA.x; hq[1] = hA.y; hq[2] = hA.z; hq[3] = hA.w;
+          hq[4] = hB.x; hq[5] = hB.y; hq[6] = hB.z; hq[7] = hB.w;
+          fir_tap(y0, y1, hq, x0 + (long long)q * M, x1 + (long long)q * M, has1, a.vec_in);
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < 8; ++r) zs[e][fe_pad(8 * lt + r)] = make_float2(y0[r], y1[r]);
+      // the next iteration's newest frame comes from DRAM: ask for it now
+      if (active && s + kFeNB * U < ng) {
+        const int8_t* nx =
+            a.adc + (long long)i0 * a.adc_stride + (t + kFeNB * U + a.taps - 1) * M + 8 * lt;
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(nx));
+        if (has1) asm volatile("prefetch.global.L1 [%0];" ::"l"(nx + a.adc_stride));
       }
     }
-#pragma unroll
-    for (int r = 0; r < 8; ++r) z[fe_pad(8 * lt + r)] = make_float2(y0[r], y1[r]);
     __syncthreads();
-    // the next iteration's newest frame comes from DRAM: ask for it now
-    if (active && s + U < ng) {
-      const int8_t* nx = a.adc + (long long)i0 * a.adc_stride + (t + U + a.taps - 1) * M + 8 * lt;
-      asm volatile("prefetch.global.L1 [%0];" ::"l"(nx));
-      if (has1) asm volatile("prefetch.global.L1 [%0];" ::"l"(nx + a.adc_stride));
-    }
-    // ---- FFT of y_2k + j y_2k+1 (natural order out)
-    fft_pass<M, 8>(z, lt, 1, twl);  // first pass: no twiddles
+    // ---- FFTs of y_2k + j y_2k+1 (natural order out), kFeNB side by side
+    fft_pass<M, 8, kFeNB>(zs, lt, 1, twl);  // first pass: no twiddles
 #pragma unroll
-    for (int p = 1; p < P8; ++p) fft_pass<M, 8>(z, lt, 1 << (3 * p), tw[p - 1]);
-    if constexpr (REM == 2) fft_pass<M, 4>(z, lt, 1 << (3 * P8), twl);
-    if constexpr (REM == 1) fft_pass<M, 2>(z, lt, 1 << (3 * P8), twl);
+    for (int p = 1; p < P8; ++p) fft_pass<M, 8, kFeNB>(zs, lt, 1 << (3 * p), tw[p - 1]);
+    if constexpr (REM == 2) fft_pass<M, 4, kFeNB>(zs, lt, 1 << (3 * P8), twl);
+    if constexpr (REM == 1) fft_pass<M, 2, kFeNB>(zs, lt, 1 << (3 * P8), twl);
     // ---- Eq. 2 separation, 18-bit rounding, equaliser
-    if (active) {
+#pragma unroll
+    for (int e = 0; e < kFeNB; ++e) {
+      const int s = sb + e * U + u;
+      if (s >= ng) continue;
+      const long long t = t0 + s;
+      const float2* z = zs[e];
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         const int nu = lt + k * TPU;
@@ -323,9 +343,9 @@ __global__ void __launch_bounds__(fe_threads(LOGM), XE_FE_MIN_BLOCKS) fengine_ke
           if (j == 1 && !has1) break;
           const int vr = round18(X[j][0]), vi = round18(X[j][1]);
           if (a.spec || a.v18) {
-            const long long e = ((t * C + nu) * N + i0 + j) * 2;
-            if (a.spec) *reinterpret_cast<float2*>(a.spec + e) = make_float2(X[j][0], X[j][1]);
-            if (a.v18) *reinterpret_cast<int2*>(a.v18 + e) = make_int2(vr, vi);
+            const long long ei = ((t * C + nu) * N + i0 + j) * 2;
+            if (a.spec) *reinterpret_cast<float2*>(a.spec + ei) = make_float2(X[j][0], X[j][1]);
+            if (a.v18) *reinterpret_cast<int2*>(a.v18 + ei) = make_int2(vr, vi);
           }
           if (a.power) pw[k][j] += (unsigned long long)((long long)vr * vr + (long long)vi * vi);
           const int qr = equalise(vr, g[k][j], vsat[k][j]) & 0xF;
