@@ -294,6 +294,7 @@ def run_gpu(args, w, world, rank, local):
     import torch
     from paper_1904_07778_gb300 import build, synth
     build.build()
+    from paper_1904_07778_gb300.xengine import CORR_ESTATE as xe_estate
     from paper_1904_07778_gb300.xengine import Correlator
 
     torch.cuda.set_device(local)
@@ -310,16 +311,48 @@ def run_gpu(args, w, world, rank, local):
         blocks = [synth.block_device(w["kind"], 1000 * rank + s, N, C, T, w["layout"], dev)
                   for s in range(nalt)]
         vis = torch.empty((C, nb, 2), dtype=torch.int64, device=dev)
+        vis2 = torch.empty_like(vis)
     stream.synchronize()
     cor = Correlator(N, C, T, bits=4, layout=w["layout"], stream=stream.cuda_stream)
 
+    # one step = per_dump pushes and one dump of the integration into device
+    # memory; the dump is overlapped (corr_dump_async) and step k waits for
+    # step k-1's dump, so every dump completes inside the timed region
     def step(k):
         for p in range(per_dump):
             cor.push(blocks[(k * per_dump + p) % nalt])
-        cor.dump_into(vis, reset=True)
+        cor.dump_async(vis if k % 2 == 0 else vis2, reset=True)
+        if k > 0:
+            cor.dump_wait()
+
+    def drain():
+        while cor.dump_wait(check=False) != xe_estate:
+            pass
+
+    # pipelined corner turn: the turn of block k+1 on `turn_sms` SMs overlaps
+    # the cross-multiply of block k on the others; the split is chosen by a
+    # short timed sweep unless given
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    pipe, sweep = 0, {}
+    if args.pipeline_sms != 0 and w["layout"] != 2:
+        cands = [args.pipeline_sms] if args.pipeline_sms > 0 else [0, 32, 40, 44, 48, 52, 56, 60, 64, 72]
+        for cand in cands:
+            cor.set_pipeline(cand)
+            for k in range(2):
+                step(k)
+            drain()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for k in range(12):
+                step(k)
+            drain()
+            sweep[cand] = 1e3 * (time.perf_counter() - t0) / 12
+        pipe = min(sweep, key=sweep.get)
+        cor.set_pipeline(pipe)
 
     for k in range(args.warmup):
         step(k)
+    drain()
     cor.set_timing(True)
     s0 = cor.stats()
     sampler = ClockSampler(local) if not args.no_clocks else None
@@ -333,6 +366,7 @@ def run_gpu(args, w, world, rank, local):
     e0.record(stream)
     for k in range(args.steps):
         step(k)
+    drain()             # the last dump is part of the last step
     e1.record(stream)
     torch.cuda.synchronize()
     wall = time.perf_counter() - w0
@@ -418,7 +452,7 @@ def run_gpu(args, w, world, rank, local):
     fp8_sus = 2 * pk["bf16_sus"]  # fp8 dense = 2 x bf16 (nominal ratio)
     herk = {"kernel": "herk4_kernel", "bound": "tensor", "unit": "TFLOP/s",
             "achieved": herk_ops / (herk_avg * 1e-3) / 1e12, "peak": fp8_sus,
-            "avg_launch_ms": herk_avg, "launches": d["timed_herk"],
+            "avg_launch_ms": herk_avg, "launches": d["timed_herk"], "sms": n_sm - pipe,
             "peak_note": "fp8 dense = 2 x %s bf16 sustained (%.1f TF/s)" % (pk["src"], pk["bf16_sus"]),
             "traffic": kernel_traffic("herk4_kernel", C)}
     herk["frac"] = herk["achieved"] / herk["peak"]
@@ -431,12 +465,15 @@ def run_gpu(args, w, world, rank, local):
     kernels = [herk]
     if d["timed_turn"] > 0:  # the payload order is read directly when its rows suit TMA
         tb = 2 * N * C * T
-        turn = {"kernel": "turn_kernel", "bound": "hbm", "unit": "GB/s",
+        turn = {"kernel": "turn_persist_kernel" if pipe else "turn_kernel", "bound": "hbm",
+                "unit": "GB/s", "sms": pipe or n_sm,
                 "achieved": tb / (turn_avg * 1e-3) / 1e9, "peak": pk["hbm"], "avg_launch_ms": turn_avg,
                 "launches": d["timed_turn"], "peak_note": "%s HBM copy" % pk["src"],
                 "traffic": kernel_traffic("turn_kernel", N * C * T)}
         turn["frac"] = turn["achieved"] / turn["peak"]
         kernels.append(turn)
+    for k_ in kernels:  # a kernel confined to part of the GPU, against that part's share
+        k_["frac_of_its_sms"] = k_["frac"] * n_sm / k_["sms"]
     dom = max(kernels, key=lambda k: k["avg_launch_ms"] * k["launches"])
     roof = {k: dom[k] for k in ("bound", "achieved", "peak", "unit", "frac", "traffic")}
     for k in ("executed_tflops", "executed_frac", "algorithmic_over_executed"):
@@ -455,13 +492,19 @@ def run_gpu(args, w, world, rank, local):
                    "l2": "inputs larger than L2 (%d distinct blocks of %.0f MB cycled)" % (
                        nalt, N * C * T / 1e6),
                    "blocks_per_dump": per_dump,
+                   "pipeline": {"turn_sms": pipe, "herk_sms": n_sm - pipe,
+                                "sweep_ms_per_step": {str(k_): v for k_, v in sweep.items()},
+                                "note": "turn of block k+1 overlaps the cross-multiply of block k "
+                                        "(corr_set_pipeline); 0 = one stream" if pipe else
+                                        "one stream"},
                    "parallelism": "replica per GPU, channels independent" if world > 1 else "1 GPU"},
         "x_real_time": world * C * T * per_dump / REAL_TIME_RATE / (ms_step * 1e-3),
         "wall_ms_per_step": 1e3 * wall / args.steps,
         "gpu_launches": (d["herk_launches"] + d["turn_launches"] + d["norm_launches"]),
         "roofline": roof, "kernels": kernels,
         "phase_ms_per_step": {"turn": d["turn_ms"] / args.steps, "herk": d["herk_ms"] / args.steps,
-                              "dump_copy": d["dump_ms"] / args.steps},
+                              "dump_copy": d["dump_ms"] / args.steps,
+                              "overlapped": bool(pipe)},
         "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,
         "vs_baseline_note": "value / 1.2 Tops/s (xGPU, one GTX 690 core, Sec. 2.2): context only",
     }
@@ -1130,6 +1173,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--pipeline-sms", type=int, default=-1,
+                    help="SMs for the pipelined corner turn (0 = off, -1 = pick by a timed sweep)")
     ap.add_argument("--ingest-threads", type=int, default=4,
                     help="producer threads of the packet-ingest workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")

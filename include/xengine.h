@@ -118,6 +118,24 @@ int corr_create(int n_inputs, int n_chans, int n_time, int bits, int layout, uns
 int corr_push(corr_ctx* ctx, const void* block, size_t nbytes, uint64_t seq);
 
 /*
+ * corr_set_pipeline -- overlap the corner turn of each block with the
+ * cross-multiply of the block pushed before it.
+ *   turn_sms : > 0 -> each push's corner turn runs as turn_sms persistent
+ *              CTAs (one per SM) on an internal stream, and its cross-multiply
+ *              on the other SMs of a second internal stream, so that the turn
+ *              of block k+1 overlaps the cross-multiply of block k; the context
+ *              keeps a second corner-turned buffer (allocated here).
+ *              0 -> one stream again.  Must be below the device's SM count.
+ * Only for configurations that turn their blocks (4-bit and 8-bit CORR_L_TCI,
+ * CORR_L_TIC), else CORR_EINVAL.  Waits for the context's work first.
+ * Stream order while pipelined: work queued on the context's stream after a
+ * corr_push waits for that block's corner turn (the only reader of the
+ * block), not for its cross-multiply; corr_dump, corr_dump_async, corr_sync,
+ * corr_normalise and corr_restore wait for every cross-multiply.
+ */
+int corr_set_pipeline(corr_ctx* ctx, int turn_sms);
+
+/*
  * corr_dump -- copy the integrated visibilities out.
  *   vis   : int64 [C][N(N+1)/2][2], host or device memory; may be NULL to
  *           only reset.

@@ -953,6 +953,7 @@ cudaError_t herk4_launch(const HerkArgs& args, const CUtensorMap* tmap, int n_ta
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
       grid = std::min(n_tasks, nsm);
+      if (a.grid > 0) grid = std::min(grid, a.grid);
     }
     if (grid < 1) return cudaSuccess;
     static const CUtensorMap unused{};  // batched launches read their maps from a.tmaps

@@ -75,7 +75,8 @@ struct HerkArgs {
   int smem_bytes;            // dynamic shared memory of the launch
   int n_tasks;               // tasks in `tasks`
   int max_nblk;              // largest number of resident 128-row blocks of any task
-  int grid;                  // CTAs of a launch with cta_first
+  int grid;                  // CTAs of a launch with cta_first; otherwise, if > 0,
+                             // the most CTAs (SMs) a single-array launch may use
 };
 
 // Largest number of spectra integrated in one tensor-memory accumulation:
@@ -110,8 +111,10 @@ bool make_sample_tmap(CUtensorMap* m, const uint8_t* x, int n_time, long long ro
 // With pair_rows, k = 2 c + p counts (c, p) pairs and output row (k, g) goes
 // to row (c G + g) 2 + p instead of k G + g: 8-bit [t][i][c][re/im] becomes
 // [c][i][re/im][t].
+// With persist_ctas > 0 the turn runs as that many persistent CTAs, one per
+// SM (for overlapping it with a cross-multiply on the remaining SMs).
 cudaError_t turn_launch(const uint8_t* in, uint8_t* out, int T, int G, int K, long long out_stride,
-                        cudaStream_t s, bool pair_rows = false);
+                        cudaStream_t s, bool pair_rows = false, int persist_ctas = 0);
 
 // 8-bit samples already in [row][t][re/im] order (row = channel x input):
 // out[row][p][t] = in[row][t][p], output rows of out_stride bytes.
@@ -123,8 +126,11 @@ cudaError_t split_planes_launch(const uint8_t* in, uint8_t* out, long long rows,
 // Returns false without launching when the layout is already that one
 // (4-bit [c][i][t]): the block itself is then the cross-multiply's input.
 bool needs_turn(int layout, int bits);
+// turn_rows runs turn_launch (and so can take persist_ctas) for this layout
+bool turn_can_persist(int layout, int bits);
 cudaError_t turn_rows(const uint8_t* in, uint8_t* out, int layout, int bits, int n_inputs,
-                      int n_chans, int n_time, long long out_stride, cudaStream_t s);
+                      int n_chans, int n_time, long long out_stride, cudaStream_t s,
+                      int persist_ctas = 0);
 
 // Tasks of one array (see HerkTask): rows_per_chan is set for stacked
 // arrays.  With singles, every task has one column block (128 x 128).

@@ -120,7 +120,17 @@ struct corr_ctx {
   cudaEvent_t stage_free[2] = {nullptr, nullptr};
   cudaEvent_t stage_ready[2] = {nullptr, nullptr};
   int stage_next = 0;
-  uint8_t* turned = nullptr;  // corner-turned copy of the block, [c][i][t]
+  uint8_t* turned = nullptr;  // corner-turned copy of the block, [c][i][t] (= turned_buf[0])
+  // Pipelined corner turn (corr_set_pipeline): the turn of block k+1 runs on
+  // pipe_sms SMs of turn_stream while the cross-multiply of block k holds the
+  // other SMs on herk_stream; the two turned buffers alternate.
+  int pipe_sms = 0;
+  unsigned pipe_k = 0;
+  bool herk_pending = false;   // herk_stream has work the caller's stream has not joined
+  uint8_t* turned_buf[2] = {nullptr, nullptr};
+  cudaStream_t turn_stream = nullptr, herk_stream = nullptr;
+  cudaEvent_t ev_in[2] = {nullptr, nullptr}, turn_done[2] = {nullptr, nullptr};
+  cudaEvent_t herk_done[2] = {nullptr, nullptr}, herk_last = nullptr;
   long long turned_stride = 0;  // bytes per (channel, input) row of `turned`
   HerkTask* tasks = nullptr;
   int n_tasks = 0;
@@ -220,6 +230,15 @@ void free_ctx(corr_ctx* x) {
   if (x->stream) cudaStreamSynchronize(x->stream);
   if (x->copy_stream) cudaStreamSynchronize(x->copy_stream);
   if (x->dump_stream) cudaStreamSynchronize(x->dump_stream);
+  if (x->turn_stream) cudaStreamSynchronize(x->turn_stream);
+  if (x->herk_stream) cudaStreamSynchronize(x->herk_stream);
+  cudaFree(x->turned_buf[1]);
+  for (int i = 0; i < 2; ++i)
+    for (cudaEvent_t e : {x->ev_in[i], x->turn_done[i], x->herk_done[i]})
+      if (e) cudaEventDestroy(e);
+  if (x->herk_last) cudaEventDestroy(x->herk_last);
+  if (x->turn_stream) cudaStreamDestroy(x->turn_stream);
+  if (x->herk_stream) cudaStreamDestroy(x->herk_stream);
   cudaFree(x->acc_buf[0]);
   cudaFree(x->acc_buf[1]);
   for (int i = 0; i < 2; ++i)
@@ -249,10 +268,27 @@ void free_ctx(corr_ctx* x) {
 
 // Before the context's stream writes the current accumulator: wait for an
 // overlapped dump that still reads it.
-int guard_acc_write(corr_ctx* x) {
+int guard_acc_write(corr_ctx* x, cudaStream_t writer) {
   if (!x->read_pending[x->cur]) return CORR_OK;
-  if (cudaStreamWaitEvent(x->stream, x->acc_free[x->cur], 0) != cudaSuccess) return CORR_ECUDA;
+  if (cudaStreamWaitEvent(writer, x->acc_free[x->cur], 0) != cudaSuccess) return CORR_ECUDA;
   x->read_pending[x->cur] = false;
+  return CORR_OK;
+}
+
+// The stream on which the accumulators and the status word are written:
+// the cross-multiply's own stream while the corner turn is pipelined.
+cudaStream_t acc_stream(corr_ctx* x) {
+  return x->pipe_sms > 0 && turn_can_persist(x->layout, x->bits) ? x->herk_stream : x->stream;
+}
+
+// Make the caller's stream wait for the pipelined cross-multiplies before it
+// touches the accumulators or the status word.
+int pipe_join(corr_ctx* x) {
+  if (!x->herk_pending) return CORR_OK;
+  if (cudaEventRecord(x->herk_last, x->herk_stream) != cudaSuccess ||
+      cudaStreamWaitEvent(x->stream, x->herk_last, 0) != cudaSuccess)
+    return CORR_ECUDA;
+  x->herk_pending = false;
   return CORR_OK;
 }
 
@@ -341,6 +377,7 @@ int corr_create(int n_inputs, int n_chans, int n_time, int bits, int layout, uns
     const int byte_rows = n_inputs * (bits / 4);
     if ((layout != CORR_L_CIT || bits == 8) &&
         cudaMalloc(&x->turned, (size_t)x->turned_stride * byte_rows * n_chans) != cudaSuccess) { st = CORR_ENOMEM; break; }
+    x->turned_buf[0] = x->turned;
     if (cudaMalloc(&x->d_status, sizeof(int)) != cudaSuccess) { st = CORR_ENOMEM; break; }
     if (cudaMemset(x->d_status, 0, sizeof(int)) != cudaSuccess) { st = CORR_ECUDA; break; }
     if (cudaMallocHost(&x->h_status, sizeof(int)) != cudaSuccess) { st = CORR_ENOMEM; break; }
@@ -381,6 +418,17 @@ int corr_push(corr_ctx* x, const void* block, size_t nbytes, uint64_t seq) {
     x->next_seq = seq + 1;
   }
   const uint8_t* src = static_cast<const uint8_t*>(block);
+  // Pipelined: the turn runs on turn_stream after the caller's work so far
+  // (the producer of this block) and after the cross-multiply that last read
+  // its turned buffer; the cross-multiply runs on herk_stream.
+  const bool pipe = x->pipe_sms > 0 && turn_can_persist(x->layout, x->bits);
+  const int pk = x->pipe_k & 1;
+  cudaStream_t ts = pipe ? x->turn_stream : x->stream;
+  cudaStream_t hs = pipe ? x->herk_stream : x->stream;
+  if (pipe && (cudaEventRecord(x->ev_in[pk], x->stream) != cudaSuccess ||
+               cudaStreamWaitEvent(ts, x->ev_in[pk], 0) != cudaSuccess ||
+               cudaStreamWaitEvent(ts, x->herk_done[pk], 0) != cudaSuccess))
+    return CORR_ECUDA;
   int slot = -1;
   if (!is_device_ptr(block)) {
     slot = x->stage_next;
@@ -395,7 +443,7 @@ int corr_push(corr_ctx* x, const void* block, size_t nbytes, uint64_t seq) {
       return CORR_ECUDA;
     phase_end(x, kCopyIn, tc, x->copy_stream);
     if (cudaEventRecord(x->stage_ready[slot], x->copy_stream) != cudaSuccess ||
-        cudaStreamWaitEvent(x->stream, x->stage_ready[slot], 0) != cudaSuccess)
+        cudaStreamWaitEvent(ts, x->stage_ready[slot], 0) != cudaSuccess)
       return CORR_ECUDA;
     src = x->stage[slot];
   }
@@ -404,14 +452,23 @@ int corr_push(corr_ctx* x, const void* block, size_t nbytes, uint64_t seq) {
   const int R = eight ? 2 * N : N;  // byte rows per channel
   long long row_stride = T;
   if (needs_turn(x->layout, x->bits)) {
-    cudaEvent_t tt = phase_begin(x, x->stream);
-    cudaError_t e = turn_rows(src, x->turned, x->layout, x->bits, N, C, T, x->turned_stride,
-                              x->stream);
+    uint8_t* turned = pipe ? x->turned_buf[pk] : x->turned;
+    cudaEvent_t tt = phase_begin(x, ts);
+    cudaError_t e = turn_rows(src, turned, x->layout, x->bits, N, C, T, x->turned_stride, ts,
+                              pipe ? x->pipe_sms : 0);
     if (e != cudaSuccess) return cuda_fail(e);
-    phase_end(x, kTurn, tt, x->stream);
+    phase_end(x, kTurn, tt, ts);
     ++x->stats.turn_launches;
-    src = x->turned;
+    src = turned;
     row_stride = x->turned_stride;
+  }
+  if (pipe) {
+    // the caller's stream only waits for the turn, the block's one reader
+    if (cudaEventRecord(x->turn_done[pk], ts) != cudaSuccess ||
+        cudaStreamWaitEvent(x->stream, x->turn_done[pk], 0) != cudaSuccess ||
+        cudaStreamWaitEvent(hs, x->turn_done[pk], 0) != cudaSuccess ||
+        (slot >= 0 && cudaEventRecord(x->stage_free[slot], ts) != cudaSuccess))
+      return CORR_ECUDA;
   }
   HerkArgs a;
   memset(&a, 0, sizeof(a));
@@ -438,27 +495,70 @@ int corr_push(corr_ctx* x, const void* block, size_t nbytes, uint64_t seq) {
       aligned && make_sample_tmap(&tmap, src, T, row_stride, R, C, box_in, box_ch);
   if (eight && !use_tma) return CORR_ECUDA;  // the plane-split copy is always aligned
   const int chunk = eight ? kMaxChunk8 : kMaxChunk4;
-  if (int g = guard_acc_write(x)) return g;
+  if (int g = guard_acc_write(x, hs)) return g;
+  if (pipe) {
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    a.grid = nsm - x->pipe_sms;  // the SMs the next block's turn leaves free
+  }
   for (int t0 = 0; t0 < T; t0 += chunk) {
     a.in.t0 = t0;
     a.in.tn = std::min(chunk, T - t0);
     a.in.accumulate = x->acc_live ? 1 : 0;
     a.in.vec_ok = aligned ? 1 : 0;
-    cudaEvent_t th = phase_begin(x, x->stream);
-    cudaError_t e = herk4_launch(a, use_tma ? &tmap : nullptr, x->n_tasks, x->stream);
+    cudaEvent_t th = phase_begin(x, hs);
+    cudaError_t e = herk4_launch(a, use_tma ? &tmap : nullptr, x->n_tasks, hs);
     if (e != cudaSuccess) return cuda_fail(e);
-    phase_end(x, kHerk, th, x->stream);
+    phase_end(x, kHerk, th, hs);
     ++x->stats.herk_launches;
     x->acc_live = true;
   }
   ++x->stats.blocks;
-  if (slot >= 0 && cudaEventRecord(x->stage_free[slot], x->stream) != cudaSuccess)
+  if (pipe) {
+    if (cudaEventRecord(x->herk_done[pk], hs) != cudaSuccess) return CORR_ECUDA;
+    ++x->pipe_k;
+    x->herk_pending = true;
+  } else if (slot >= 0 && cudaEventRecord(x->stage_free[slot], x->stream) != cudaSuccess) {
     return CORR_ECUDA;
+  }
+  return CORR_OK;
+}
+
+int corr_set_pipeline(corr_ctx* x, int turn_sms) {
+  if (!x || turn_sms < 0) return CORR_EINVAL;
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return CORR_ECUDA;
+  if (turn_sms >= nsm) return CORR_EINVAL;
+  if (turn_sms > 0 && !turn_can_persist(x->layout, x->bits)) return CORR_EINVAL;
+  // switch between modes only with nothing in flight
+  if (pipe_join(x) != CORR_OK || cudaStreamSynchronize(x->stream) != cudaSuccess ||
+      cudaStreamSynchronize(x->copy_stream) != cudaSuccess)
+    return CORR_ECUDA;
+  if (turn_sms > 0 && !x->turn_stream) {
+    if (cudaStreamCreateWithFlags(&x->turn_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&x->herk_stream, cudaStreamNonBlocking) != cudaSuccess)
+      return CORR_ECUDA;
+    for (int i = 0; i < 2; ++i)
+      for (cudaEvent_t* e : {&x->ev_in[i], &x->turn_done[i], &x->herk_done[i]})
+        if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) return CORR_ECUDA;
+    if (cudaEventCreateWithFlags(&x->herk_last, cudaEventDisableTiming) != cudaSuccess)
+      return CORR_ECUDA;
+    const int byte_rows = x->n_inputs * (x->bits / 4);
+    if (cudaMalloc(&x->turned_buf[1], (size_t)x->turned_stride * byte_rows * x->n_chans) !=
+        cudaSuccess)
+      return CORR_ENOMEM;
+  }
+  x->pipe_sms = turn_sms;
+  x->pipe_k = 0;
   return CORR_OK;
 }
 
 int corr_sync(corr_ctx* x) {
   if (!x) return CORR_EINVAL;
+  if (pipe_join(x) != CORR_OK) return CORR_ECUDA;
   if (cudaStreamSynchronize(x->copy_stream) != cudaSuccess) return CORR_ECUDA;
   if (x->dump_stream && cudaStreamSynchronize(x->dump_stream) != cudaSuccess) return CORR_ECUDA;
   return take_status(x);
@@ -468,6 +568,10 @@ int corr_dump_async(corr_ctx* x, int64_t* vis, int reset) {
   TraceRange trace_("corr_dump_async");
   if (!x || !vis) return CORR_EINVAL;
   if ((int)x->dumps.size() >= CORR_MAX_ASYNC_DUMPS) return CORR_EBUSY;
+  // everything below is ordered after the last cross-multiply on its own
+  // stream, so that the caller's stream (and the next block's corner turn)
+  // does not wait for it
+  cudaStream_t as = acc_stream(x);
   if (!x->dump_stream) {
     if (cudaStreamCreateWithFlags(&x->dump_stream, cudaStreamNonBlocking) != cudaSuccess)
       return CORR_ECUDA;
@@ -480,8 +584,8 @@ int corr_dump_async(corr_ctx* x, int64_t* vis, int reset) {
   if (reset && !x->acc_buf[1] && cudaMalloc(&x->acc_buf[1], x->acc_bytes) != cudaSuccess)
     return CORR_ENOMEM;
   if (!x->acc_live) {  // nothing pushed since the last reset: an all-zero integration
-    if (int g = guard_acc_write(x)) return g;
-    if (cudaMemsetAsync(x->acc, 0, x->acc_bytes, x->stream) != cudaSuccess) return CORR_ECUDA;
+    if (int g = guard_acc_write(x, as)) return g;
+    if (cudaMemsetAsync(x->acc, 0, x->acc_bytes, as) != cudaSuccess) return CORR_ECUDA;
     x->acc_live = true;
   }
   // a status slot no outstanding dump uses
@@ -499,9 +603,9 @@ int corr_dump_async(corr_ctx* x, int64_t* vis, int reset) {
   }
   int st = CORR_OK;
   if (cudaMemcpyAsync(x->h_dump_status + slot, x->d_status, sizeof(int), cudaMemcpyDeviceToHost,
-                      x->stream) != cudaSuccess ||
-      cudaMemsetAsync(x->d_status, 0, sizeof(int), x->stream) != cudaSuccess ||
-      cudaEventRecord(ready, x->stream) != cudaSuccess ||
+                      as) != cudaSuccess ||
+      cudaMemsetAsync(x->d_status, 0, sizeof(int), as) != cudaSuccess ||
+      cudaEventRecord(ready, as) != cudaSuccess ||
       cudaStreamWaitEvent(x->dump_stream, ready, 0) != cudaSuccess)
     st = CORR_ECUDA;
   if (st == CORR_OK) {
@@ -546,6 +650,7 @@ int corr_dump_wait(corr_ctx* x) {
 int corr_dump(corr_ctx* x, int64_t* vis, int reset) {
   TraceRange trace_("corr_dump");
   if (!x) return CORR_EINVAL;
+  if (pipe_join(x) != CORR_OK) return CORR_ECUDA;
   if (vis) {
     const bool dev = is_device_ptr(vis);
     if (x->acc_live) {
@@ -572,7 +677,8 @@ int corr_dump(corr_ctx* x, int64_t* vis, int reset) {
 int corr_restore(corr_ctx* x, const int64_t* vis) {
   TraceRange trace_("corr_restore");
   if (!x || !vis) return CORR_EINVAL;
-  if (int g = guard_acc_write(x)) return g;
+  if (pipe_join(x) != CORR_OK) return CORR_ECUDA;
+  if (int g = guard_acc_write(x, x->stream)) return g;
   if (cudaMemcpyAsync(x->acc, vis, x->acc_bytes, cudaMemcpyDefault, x->stream) != cudaSuccess ||
       cudaStreamSynchronize(x->stream) != cudaSuccess)
     return CORR_ECUDA;
@@ -584,9 +690,10 @@ int corr_restore(corr_ctx* x, const int64_t* vis) {
 int corr_normalise(corr_ctx* x, double* rho) {
   TraceRange trace_("corr_normalise");
   if (!x || !rho) return CORR_EINVAL;
+  if (pipe_join(x) != CORR_OK) return CORR_ECUDA;
   const size_t bytes = x->acc_bytes;  // same element count, 8-byte elements
   if (!x->acc_live) {
-    if (int g = guard_acc_write(x)) return g;
+    if (int g = guard_acc_write(x, x->stream)) return g;
     if (cudaMemsetAsync(x->acc, 0, x->acc_bytes, x->stream) != cudaSuccess) return CORR_ECUDA;
     x->acc_live = true;
   }

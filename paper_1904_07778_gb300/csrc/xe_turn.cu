@@ -37,13 +37,18 @@ __device__ __forceinline__ void st32B(uint8_t* p, const uint32_t (&r)[8]) {
 
 __device__ __forceinline__ int tile_word(int row, int w) { return row * 32 + (w ^ ((row >> 5) << 2)); }
 
-__global__ void __launch_bounds__(256, 4) turn_kernel(const uint8_t* __restrict__ in,
-                                                      uint8_t* __restrict__ out, int T, int G,
-                                                      int K, long long os, int vec_ok,
-                                                      int pair_rows) {
-  __shared__ __align__(16) uint32_t tile[kTT * 32];
-  const int t0 = blockIdx.x * kTT, k0 = blockIdx.y * kTK, g = blockIdx.z;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+// barrier of one 256-thread group (id 0 is the whole CTA of a 256-thread launch)
+__device__ __forceinline__ void group_bar(int id) {
+  asm volatile("bar.sync %0, 256;" ::"r"(id) : "memory");
+}
+
+// One tile: 256 threads (tid 0..255) move spectra t0 .. t0+255 of byte rows
+// k0 .. k0+127 of group g through `tile`, meeting at barrier `bar`.
+__device__ __forceinline__ void turn_tile(const uint8_t* __restrict__ in, uint8_t* __restrict__ out,
+                                          int T, int G, int K, long long os, int vec_ok,
+                                          int pair_rows, int t0, int k0, int g, uint32_t* tile,
+                                          int tid, int bar) {
+  const int warp = tid >> 5, lane = tid & 31;
   const bool full = vec_ok && t0 + kTT <= T && k0 + kTK <= K;
   // load: 256 rows x 128 bytes as 32-byte pieces, four per thread, all
   // issued before any of them is stored
@@ -77,7 +82,7 @@ __global__ void __launch_bounds__(256, 4) turn_kernel(const uint8_t* __restrict_
       tile[tile_word(r, w)] = x;
     }
   }
-  __syncthreads();
+  group_bar(bar);
   // store: thread = 4 consecutive k (word kq) x 32 consecutive t (segment ts);
   // the eight lanes of a k-quad cover one 256-byte stretch of each output row
   const int kq = 4 * warp + (lane >> 3), ts = lane & 7;
@@ -102,6 +107,38 @@ __global__ void __launch_bounds__(256, 4) turn_kernel(const uint8_t* __restrict_
       for (int b = 0; b < 32; ++b)
         if (tb + b < T) o[b] = (uint8_t)(a[4 * (b >> 2) + c] >> ((b & 3) * 8));
     }
+  }
+}
+
+__global__ void __launch_bounds__(256, 4) turn_kernel(const uint8_t* __restrict__ in,
+                                                      uint8_t* __restrict__ out, int T, int G,
+                                                      int K, long long os, int vec_ok,
+                                                      int pair_rows) {
+  __shared__ __align__(16) uint32_t tile[kTT * 32];
+  turn_tile(in, out, T, G, K, os, vec_ok, pair_rows, blockIdx.x * kTT, blockIdx.y * kTK,
+            blockIdx.z, tile, threadIdx.x, 0);
+}
+
+// The same tiles from a fixed number of CTAs, one per SM (four 256-thread
+// groups, a 32 KB tile each, so 128 KB of loads are in flight per SM): a
+// corner turn confined to a few SMs while the cross-multiply of the previous
+// block holds the others.
+constexpr int kTurnGroups = 4;
+__global__ void __launch_bounds__(256 * kTurnGroups, 1)
+    turn_persist_kernel(const uint8_t* __restrict__ in, uint8_t* __restrict__ out, int T, int G,
+                        int K, long long os, int vec_ok, int pair_rows) {
+  extern __shared__ __align__(16) uint32_t tiles[];
+  const int grp = threadIdx.x >> 8, tid = threadIdx.x & 255;
+  uint32_t* tile = tiles + grp * (kTT * 32);
+  const int gx = (T + kTT - 1) / kTT, gy = (K + kTK - 1) / kTK;
+  const long long n = (long long)gx * gy * G;
+  for (long long w = (long long)blockIdx.x * kTurnGroups + grp; w < n;
+       w += (long long)gridDim.x * kTurnGroups) {
+    const int x = (int)(w % gx);
+    const long long r = w / gx;
+    const int y = (int)(r % gy), g = (int)(r / gy);
+    turn_tile(in, out, T, G, K, os, vec_ok, pair_rows, x * kTT, y * kTK, g, tile, tid, 1 + grp);
+    group_bar(1 + grp);  // the next tile's loads overwrite this one
   }
 }
 
@@ -167,10 +204,23 @@ __global__ void normalise_kernel(const int64_t* __restrict__ acc, double* __rest
 }  // namespace
 
 cudaError_t turn_launch(const uint8_t* in, uint8_t* out, int T, int G, int K, long long out_stride,
-                        cudaStream_t s, bool pair_rows) {
+                        cudaStream_t s, bool pair_rows, int persist_ctas) {
   const int vec_ok = (K % 32 == 0) && (T % 32 == 0) && (out_stride % 32 == 0) &&
                      (reinterpret_cast<uintptr_t>(in) % 32 == 0) &&
                      (reinterpret_cast<uintptr_t>(out) % 32 == 0);
+  if (persist_ctas > 0) {
+    constexpr int smem = kTurnGroups * kTT * 32 * (int)sizeof(uint32_t);
+    static bool attr = false;
+    if (!attr) {
+      cudaError_t e = cudaFuncSetAttribute(turn_persist_kernel,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      if (e != cudaSuccess) return e;
+      attr = true;
+    }
+    turn_persist_kernel<<<persist_ctas, 256 * kTurnGroups, smem, s>>>(
+        in, out, T, G, K, out_stride, vec_ok, pair_rows ? 1 : 0);
+    return cudaGetLastError();
+  }
   dim3 grid((T + kTT - 1) / kTT, (K + kTK - 1) / kTK, G);
   turn_kernel<<<grid, 256, 0, s>>>(in, out, T, G, K, out_stride, vec_ok, pair_rows ? 1 : 0);
   return cudaGetLastError();
@@ -191,8 +241,11 @@ cudaError_t split_planes_launch(const uint8_t* in, uint8_t* out, long long rows,
 
 bool needs_turn(int layout, int bits) { return layout != 2 || bits == 8; }
 
+bool turn_can_persist(int layout, int bits) { return needs_turn(layout, bits) && layout != 2; }
+
 cudaError_t turn_rows(const uint8_t* in, uint8_t* out, int layout, int bits, int n_inputs,
-                      int n_chans, int n_time, long long out_stride, cudaStream_t s) {
+                      int n_chans, int n_time, long long out_stride, cudaStream_t s,
+                      int persist_ctas) {
   const int N = n_inputs, C = n_chans, T = n_time;
   const bool eight = bits == 8;
   const int R = eight ? 2 * N : N;
@@ -200,10 +253,10 @@ cudaError_t turn_rows(const uint8_t* in, uint8_t* out, int layout, int bits, int
   // transposes of T x C.  8-bit samples are byte pairs: [t][c][i][p] turns as
   // T x (C 2N); [t][i][c][p] as N transposes of T x 2C with each (c, p) row
   // sent to row (c, i, p); [c][i][t][p] only splits the planes.
-  if (layout == 0) return turn_launch(in, out, T, 1, C * R, out_stride, s);
+  if (layout == 0) return turn_launch(in, out, T, 1, C * R, out_stride, s, false, persist_ctas);
   if (layout == 1)
-    return eight ? turn_launch(in, out, T, N, 2 * C, out_stride, s, true)
-                 : turn_launch(in, out, T, N, C, out_stride, s);
+    return eight ? turn_launch(in, out, T, N, 2 * C, out_stride, s, true, persist_ctas)
+                 : turn_launch(in, out, T, N, C, out_stride, s, false, persist_ctas);
   if (eight) return split_planes_launch(in, out, (long long)C * N, T, out_stride, s);
   return cudaSuccess;
 }

@@ -64,6 +64,9 @@ _lib.corr_set_timing.argtypes = [_P, _I]
 _lib.corr_restore.argtypes = [_P, _P]
 _lib.corr_restore.restype = _I
 EXPORTS.append("corr_restore")
+_lib.corr_set_pipeline.argtypes = [_P, _I]
+_lib.corr_set_pipeline.restype = _I
+EXPORTS.append("corr_set_pipeline")
 _lib.corr_dump_async.argtypes = [_P, _P, _I]
 _lib.corr_dump_async.restype = _I
 _lib.corr_dump_wait.argtypes = [_P]
@@ -187,6 +190,13 @@ class Correlator:
         if check and st != CORR_OK:
             raise CorrError(st, "corr_dump")
         return vis
+
+    def set_pipeline(self, turn_sms: int):
+        """Overlap each block's corner turn (on turn_sms SMs) with the previous
+        block's cross-multiply (corr_set_pipeline); 0 turns it off."""
+        st = _lib.corr_set_pipeline(self._ctx, turn_sms)
+        if st != CORR_OK:
+            raise CorrError(st, "corr_set_pipeline")
 
     def dump_async(self, vis, reset=True):
         """Queue the copy of the integration into ``vis`` (corr_dump_async);
