@@ -55,7 +55,9 @@ struct FeArgs {
 __host__ __device__ constexpr int fe_threads(int logm) {
   return (1 << logm) / 8 > 256 ? (1 << logm) / 8 : 256;
 }
-__host__ __device__ constexpr int fe_pad(int n) { return n + (n >> 3); }
+// one float2 of padding per 16: consecutive runs of 16 (half a warp's
+// 8-byte accesses) stay contiguous, stride-8 runs spread over the banks
+__host__ __device__ constexpr int fe_pad(int n) { return n + (n >> 4); }
 template <int LOGM>
 constexpr size_t fe_smem_bytes() {
   constexpr int M = 1 << LOGM;

@@ -42,13 +42,46 @@ __device__ __forceinline__ void group_bar(int id) {
   asm volatile("bar.sync %0, 256;" ::"r"(id) : "memory");
 }
 
+// Store phase of a tile held in `tile`: each thread transposes 4 x 32 bytes
+// in registers and writes 32-byte pieces of [k][g][t] rows.
+__device__ __forceinline__ void turn_tile_store(uint8_t* __restrict__ out, int T, int K, int G,
+                                                long long os, int pair_rows, int t0, int k0,
+                                                int g, const uint32_t* tile, int tid, bool full) {
+  const int warp = tid >> 5, lane = tid & 31;
+  // store: thread = 4 consecutive k (word kq) x 32 consecutive t (segment ts);
+  // the eight lanes of a k-quad cover one 256-byte stretch of each output row
+  const int kq = 4 * warp + (lane >> 3), ts = lane & 7;
+  uint32_t a[32];
+#pragma unroll
+  for (int j = 0; j < 32; ++j) a[j] = tile[tile_word(ts * 32 + j, kq)];
+#pragma unroll
+  for (int j = 0; j < 32; j += 4) transpose4x4(a[j], a[j + 1], a[j + 2], a[j + 3]);
+  // a[4w + c] now holds t = ts*32 + 4w .. +3 of k = 4 kq + c
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const int k = k0 + 4 * kq + c;
+    const int tb = t0 + ts * 32;
+    const long long row =
+        pair_rows ? ((long long)(k >> 1) * G + g) * 2 + (k & 1) : (long long)k * G + g;
+    uint8_t* o = out + row * os + tb;
+    if (full) {
+      const uint32_t r[8] = {a[c], a[4 + c], a[8 + c], a[12 + c],
+                             a[16 + c], a[20 + c], a[24 + c], a[28 + c]};
+      st32B(o, r);
+    } else if (k < K) {
+      for (int b = 0; b < 32; ++b)
+        if (tb + b < T) o[b] = (uint8_t)(a[4 * (b >> 2) + c] >> ((b & 3) * 8));
+    }
+  }
+}
+
+
 // One tile: 256 threads (tid 0..255) move spectra t0 .. t0+255 of byte rows
 // k0 .. k0+127 of group g through `tile`, meeting at barrier `bar`.
 __device__ __forceinline__ void turn_tile(const uint8_t* __restrict__ in, uint8_t* __restrict__ out,
                                           int T, int G, int K, long long os, int vec_ok,
                                           int pair_rows, int t0, int k0, int g, uint32_t* tile,
                                           int tid, int bar) {
-  const int warp = tid >> 5, lane = tid & 31;
   const bool full = vec_ok && t0 + kTT <= T && k0 + kTK <= K;
   // load: 256 rows x 128 bytes as 32-byte pieces, four per thread, all
   // issued before any of them is stored
@@ -83,31 +116,7 @@ __device__ __forceinline__ void turn_tile(const uint8_t* __restrict__ in, uint8_
     }
   }
   group_bar(bar);
-  // store: thread = 4 consecutive k (word kq) x 32 consecutive t (segment ts);
-  // the eight lanes of a k-quad cover one 256-byte stretch of each output row
-  const int kq = 4 * warp + (lane >> 3), ts = lane & 7;
-  uint32_t a[32];
-#pragma unroll
-  for (int j = 0; j < 32; ++j) a[j] = tile[tile_word(ts * 32 + j, kq)];
-#pragma unroll
-  for (int j = 0; j < 32; j += 4) transpose4x4(a[j], a[j + 1], a[j + 2], a[j + 3]);
-  // a[4w + c] now holds t = ts*32 + 4w .. +3 of k = 4 kq + c
-#pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    const int k = k0 + 4 * kq + c;
-    const int tb = t0 + ts * 32;
-    const long long row =
-        pair_rows ? ((long long)(k >> 1) * G + g) * 2 + (k & 1) : (long long)k * G + g;
-    uint8_t* o = out + row * os + tb;
-    if (full) {
-      const uint32_t r[8] = {a[c], a[4 + c], a[8 + c], a[12 + c],
-                             a[16 + c], a[20 + c], a[24 + c], a[28 + c]};
-      st32B(o, r);
-    } else if (k < K) {
-      for (int b = 0; b < 32; ++b)
-        if (tb + b < T) o[b] = (uint8_t)(a[4 * (b >> 2) + c] >> ((b & 3) * 8));
-    }
-  }
+  turn_tile_store(out, T, K, G, os, pair_rows, t0, k0, g, tile, tid, full);
 }
 
 __global__ void __launch_bounds__(256, 4) turn_kernel(const uint8_t* __restrict__ in,
@@ -119,27 +128,78 @@ __global__ void __launch_bounds__(256, 4) turn_kernel(const uint8_t* __restrict_
             blockIdx.z, tile, threadIdx.x, 0);
 }
 
-// The same tiles from a fixed number of CTAs, one per SM (four 256-thread
-// groups, a 32 KB tile each, so 128 KB of loads are in flight per SM): a
-// corner turn confined to a few SMs while the cross-multiply of the previous
-// block holds the others.
-constexpr int kTurnGroups = 4;
+// The same tiles from a fixed number of CTAs, one per SM, for a corner turn
+// confined to a few SMs while the cross-multiply of the previous block holds
+// the others.  Each of the three 256-thread groups of a CTA walks its own
+// tiles with two 32 KB buffers: the 16-byte cp.async copies of tile i+1 are
+// in flight while tile i is transposed and stored, so about 192 KB of loads
+// stay in flight per SM.  Edge tiles take the byte path synchronously.
+constexpr int kTurnGroups = 3;
+constexpr int kTileWords = kTT * 32;
+
+__device__ __forceinline__ void cp_async16(uint32_t* dst, const uint8_t* src) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+
+// Issue the copies of a full tile into `tile`, the same word placement as
+// the register path of turn_tile: bytes 0..15 of a row's 32-byte piece p go
+// to words 8p .. 8p+3, bytes 16..31 to words 8p+4 .. 8p+7.
+__device__ __forceinline__ void tile_prefetch(const uint8_t* __restrict__ in, int G, int K, int t0,
+                                              int k0, int g, uint32_t* tile, int tid) {
+#pragma unroll
+  for (int it = 0; it < 4; ++it) {
+    const int e = it * 256 + tid, r = e >> 2, p = e & 3;
+    const uint8_t* src = in + ((long long)(t0 + r) * G + g) * K + k0 + 32 * p;
+    cp_async16(&tile[tile_word(r, 8 * p)], src);
+    cp_async16(&tile[tile_word(r, 8 * p + 4)], src + 16);
+  }
+}
+
 __global__ void __launch_bounds__(256 * kTurnGroups, 1)
     turn_persist_kernel(const uint8_t* __restrict__ in, uint8_t* __restrict__ out, int T, int G,
                         int K, long long os, int vec_ok, int pair_rows) {
   extern __shared__ __align__(16) uint32_t tiles[];
-  const int grp = threadIdx.x >> 8, tid = threadIdx.x & 255;
-  uint32_t* tile = tiles + grp * (kTT * 32);
+  const int grp = threadIdx.x >> 8, tid = threadIdx.x & 255, bar = 1 + grp;
+  uint32_t* const mine = tiles + 2 * grp * kTileWords;  // this group's two buffers
   const int gx = (T + kTT - 1) / kTT, gy = (K + kTK - 1) / kTK;
   const long long n = (long long)gx * gy * G;
-  for (long long w = (long long)blockIdx.x * kTurnGroups + grp; w < n;
-       w += (long long)gridDim.x * kTurnGroups) {
-    const int x = (int)(w % gx);
+  const long long stride = (long long)gridDim.x * kTurnGroups;
+  auto coords = [&](long long w, int& t0, int& k0, int& g) {
     const long long r = w / gx;
-    const int y = (int)(r % gy), g = (int)(r / gy);
-    turn_tile(in, out, T, G, K, os, vec_ok, pair_rows, x * kTT, y * kTK, g, tile, tid, 1 + grp);
-    group_bar(1 + grp);  // the next tile's loads overwrite this one
+    t0 = (int)(w % gx) * kTT;
+    k0 = (int)(r % gy) * kTK;
+    g = (int)(r / gy);
+  };
+  auto is_full = [&](int t0, int k0) { return vec_ok && t0 + kTT <= T && k0 + kTK <= K; };
+  long long w = (long long)blockIdx.x * kTurnGroups + grp;
+  if (w < n) {
+    int t0, k0, g;
+    coords(w, t0, k0, g);
+    if (is_full(t0, k0)) tile_prefetch(in, G, K, t0, k0, g, mine, tid);
   }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  for (int i = 0; w < n; ++i, w += stride) {
+    const long long wn = w + stride;
+    if (wn < n) {  // the next tile's copies go out before this tile is stored
+      int t1, k1, g1;
+      coords(wn, t1, k1, g1);
+      if (is_full(t1, k1)) tile_prefetch(in, G, K, t1, k1, g1, mine + ((i + 1) & 1) * kTileWords, tid);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.wait_group 1;" ::: "memory");  // this tile's copies are in
+    int t0, k0, g;
+    coords(w, t0, k0, g);
+    uint32_t* tile = mine + (i & 1) * kTileWords;
+    if (is_full(t0, k0)) {
+      group_bar(bar);
+      turn_tile_store(out, T, K, G, os, pair_rows, t0, k0, g, tile, tid, true);
+    } else {
+      turn_tile(in, out, T, G, K, os, vec_ok, pair_rows, t0, k0, g, tile, tid, bar);
+    }
+    group_bar(bar);  // buffer i & 1 is refilled two tiles on
+  }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
 // ---------------------------------------------------------------- plane split
@@ -209,7 +269,7 @@ cudaError_t turn_launch(const uint8_t* in, uint8_t* out, int T, int G, int K, lo
                      (reinterpret_cast<uintptr_t>(in) % 32 == 0) &&
                      (reinterpret_cast<uintptr_t>(out) % 32 == 0);
   if (persist_ctas > 0) {
-    constexpr int smem = kTurnGroups * kTT * 32 * (int)sizeof(uint32_t);
+    constexpr int smem = kTurnGroups * 2 * kTileWords * (int)sizeof(uint32_t);  // 192 KB
     static bool attr = false;
     if (!attr) {
       cudaError_t e = cudaFuncSetAttribute(turn_persist_kernel,

@@ -38,8 +38,12 @@ def _want(blocks, N, C, T, bits, layout, chans=None):
 
 
 @pytest.mark.parametrize("N,C,T,bits,layout,sms", [
+    # byte-path tiles (rows not 32-byte multiples)
     (48, 20, 512, 4, 1, 24), (100, 6, 384, 4, 0, 40), (16, 40, 256, 4, 1, 8),
-    (48, 10, 256, 8, 1, 32), (30, 12, 320, 8, 0, 16), (192, 4, 256, 4, 1, 100)])
+    (48, 10, 256, 8, 1, 32), (30, 12, 320, 8, 0, 16), (192, 4, 256, 4, 1, 100),
+    # full tiles through the prefetching path, with edge tiles beside them
+    (64, 128, 768, 4, 1, 40), (32, 16, 512, 4, 0, 48), (32, 64, 512, 8, 1, 32),
+    (24, 200, 1280, 4, 1, 20)])
 def test_pipelined_pushes_exact(xe, N, C, T, bits, layout, sms):
     blocks = [_blk(700 + k + N, N, C, T, bits) for k in range(5)]
     with xe.Correlator(N, C, T, bits=bits, layout=layout) as cor:
