@@ -142,9 +142,11 @@ def peaks():
     return dict(hbm=6800.0, bf16=1900.0, bf16_sus=1700.0, src="fallback")
 
 
-def kernel_traffic(name, launch_units):
+def kernel_traffic(name, launch_units, **shape):
     """DRAM bytes per launch from a committed ncu summary, if the kernel's
-    source is unchanged since the capture; scaled to this launch's units."""
+    source is unchanged since the capture and the capture's shape (the keys
+    it records, e.g. n_inputs and n_time) matches; scaled to this launch's
+    units."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
@@ -152,6 +154,8 @@ def kernel_traffic(name, launch_units):
         d = json.load(open(path)).get(name)
         src = open(os.path.join(ROOT, d["source"]), "rb").read()
         if hashlib.sha256(src).hexdigest() != d["source_sha256"]:
+            return None
+        if any(k in d.get("shape", {}) and d["shape"][k] != v for k, v in shape.items()):
             return None
         return d["dram_bytes"] * launch_units / d["units"]
     except Exception:
@@ -454,7 +458,7 @@ def run_gpu(args, w, world, rank, local):
             "achieved": herk_ops / (herk_avg * 1e-3) / 1e12, "peak": fp8_sus,
             "avg_launch_ms": herk_avg, "launches": d["timed_herk"], "sms": n_sm - pipe,
             "peak_note": "fp8 dense = 2 x %s bf16 sustained (%.1f TF/s)" % (pk["src"], pk["bf16_sus"]),
-            "traffic": kernel_traffic("herk4_kernel", C)}
+            "traffic": kernel_traffic("herk4_kernel", C, n_inputs=N, n_time=T)}
     herk["frac"] = herk["achieved"] / herk["peak"]
     # what the tensor pipe actually executes (diagonal blocks in full): reported
     # beside the algorithmic rate, never in place of it
@@ -847,7 +851,7 @@ def run_fengine(args, w, world, rank, local):
     tflops = flops / (ms * 1e-3) / 1e12
     mhz = (clocks or {}).get("sm_mhz") or 2070.0
     peak = fp32_peak_tflops(n_sm, mhz)
-    traffic = kernel_traffic("fengine_kernel", N * T)
+    traffic = kernel_traffic("fengine_kernel", N * T, n_chans=C, taps=taps)
     line = {
         "metric": FE_METRIC, "value": world * N * T * M / (ms * 1e-3) / 1e9, "unit": "Gsample/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -932,14 +936,21 @@ def run_ingest(args, w, world, rank, local):
         assert miss == 0
     st = ring.stats()
     ms = max_over_ranks(1e3 * sum(el) / len(el), world)
-    # single-thread host copy rate of a block-sized buffer: the roofline of
-    # one producer's payload copies
+    # host copy rate of a block-sized buffer by the same number of threads
+    # (disjoint slices): the roofline of the producers' payload copies
+    import threading
     src = np.ones(T * C * N, dtype=np.uint8)
     dst = np.empty_like(src)
+    step_ = -(-src.size // threads)
     tc = []
     for _ in range(3):
+        th = [threading.Thread(target=np.copyto, args=(dst[j:j + step_], src[j:j + step_]))
+              for j in range(0, src.size, step_)]
         t0 = time.perf_counter()
-        np.copyto(dst, src)
+        for t_ in th:
+            t_.start()
+        for t_ in th:
+            t_.join()
         tc.append(time.perf_counter() - t0)
     copy_gbs = src.nbytes / min(tc) / 1e9
     payload = T * C * N
@@ -989,10 +1000,10 @@ def run_ingest(args, w, world, rank, local):
                          len(arr) / (ms * 1e-3),
         "x_real_time": payload / (ms * 1e-3) / (N * ADC_RATE / 2),
         "gpu_launches": 0,
-        "roofline": {"bound": "host", "achieved": gbs, "peak": copy_gbs * threads, "unit": "GB/s",
-                     "frac": gbs / (copy_gbs * threads), "traffic": None,
-                     "peak_note": "%d x the single-thread host copy rate of a block (%.1f GB/s); "
-                                  "each packet is read by the CRC and copied once" % (threads, copy_gbs)},
+        "roofline": {"bound": "host", "achieved": gbs, "peak": copy_gbs, "unit": "GB/s",
+                     "frac": gbs / copy_gbs, "traffic": None,
+                     "peak_note": "host copy of a block-sized buffer by %d threads (measured); "
+                                  "each packet is read by the CRC and copied once" % threads},
         "ring": {k: st[k] for k in ("packets", "blocks", "missing", "busy", "bad_crc")},
         "e2e": e2e, "cpu_baseline": cpu, "clocks": None,
     }
@@ -1155,7 +1166,8 @@ def run_fx(args, w, world, rank, local):
         "gpu_launches": 2 * args.steps,
         "roofline": {"bound": "alu", "achieved": flops / (ms_f * 1e-3) / 1e12, "peak": fpk,
                      "unit": "TFLOP/s", "frac": flops / (ms_f * 1e-3) / 1e12 / fpk,
-                     "traffic": kernel_traffic("fengine_kernel", N * T), "kernel": "fengine_kernel",
+                     "traffic": kernel_traffic("fengine_kernel", N * T, n_chans=C, taps=taps),
+                     "kernel": "fengine_kernel",
                      "peak_note": "FP32: %d SMs x 128 lanes x 2 x %.0f MHz" % (n_sm, mhz)},
         "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,
     }

@@ -34,7 +34,9 @@ namespace xe {
 namespace {
 
 constexpr int kFeGroup = 32;  // spectra per CTA
-constexpr int kFeNB = 2;      // spectra a unit transforms side by side (shared barriers)
+// spectra a unit transforms side by side (they share the pass barriers);
+// three measured no faster than two
+__host__ __device__ constexpr int fe_nb(int) { return 2; }
 
 struct FeArgs {
   const int8_t* adc;
@@ -62,7 +64,7 @@ template <int LOGM>
 constexpr size_t fe_smem_bytes() {
   constexpr int M = 1 << LOGM;
   constexpr int units = fe_threads(LOGM) / (M / 8);
-  return (size_t)kFeNB * units * fe_pad(M) * sizeof(float2) + (size_t)(M / 2) * 2 * kFeGroup;
+  return (size_t)fe_nb(LOGM) * units * fe_pad(M) * sizeof(float2) + (size_t)(M / 2) * 2 * kFeGroup;
 }
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
@@ -238,8 +240,10 @@ __global__ void __launch_bounds__(fe_threads(LOGM), XE_FE_MIN_BLOCKS) fengine_ke
   constexpr int P8 = LOGM / 3, REM = LOGM % 3;
   extern __shared__ __align__(16) uint8_t fe_smem[];
   const int tid = threadIdx.x, u = tid / TPU, lt = tid % TPU;
-  float2* const zs[kFeNB] = {reinterpret_cast<float2*>(fe_smem) + u * PM,
-                             reinterpret_cast<float2*>(fe_smem) + (U + u) * PM};
+  constexpr int kFeNB = fe_nb(LOGM);
+  float2* zs[kFeNB];
+#pragma unroll
+  for (int e = 0; e < kFeNB; ++e) zs[e] = reinterpret_cast<float2*>(fe_smem) + (e * U + u) * PM;
   uint8_t* codes = fe_smem + (size_t)kFeNB * U * PM * sizeof(float2);  // [kFeGroup][C][2]
   const int i0 = 2 * blockIdx.y;
   const bool has1 = i0 + 1 < a.n_inputs;
