@@ -921,7 +921,8 @@ def run_ingest(args, w, world, rank, local):
             t.join()
         return got[0]
 
-    ring = PacketRing(F, I, X, K, T, n_segments=cfg["segments"])
+    porder = args.ingest_layout == "packet"
+    ring = PacketRing(F, I, X, K, T, n_segments=cfg["segments"], packet_order=porder)
     pkt_bytes = None
     for k in range(args.warmup):
         arr, parts = packets_of(k)
@@ -958,21 +959,39 @@ def run_ingest(args, w, world, rank, local):
     if not args.no_e2e:
         import torch
         from paper_1904_07778_gb300.xengine import CORR_L_TCI, Correlator
+        from paper_1904_07778_gb300.xengine import CORR_L_CIT
         torch.cuda.set_device(local)
-        cor = Correlator(N, C, T, bits=4, layout=CORR_L_TCI)
         vis = torch.empty((C, N * (N + 1) // 2, 2), dtype=torch.int64, pin_memory=True)
+        if porder:
+            # packet-order block -> device -> pk_turn -> [c][i][t] -> cross-multiply
+            cor = Correlator(N, C, T, bits=4, layout=CORR_L_CIT)
+            dev = torch.empty(T * C * N, dtype=torch.uint8, device="cuda")
+            cit = torch.empty_like(dev)
+
+            def consume(r):
+                dev.copy_(torch.from_numpy(r[0].reshape(-1)), non_blocking=True)
+                ring.turn(dev, cit)
+                cor.push(cit)
+                cor.sync()
+        else:
+            cor = Correlator(N, C, T, bits=4, layout=CORR_L_TCI)
+
+            def consume(r):
+                cor.push(r[0])
+                cor.sync()
         base = args.warmup + args.steps
         ee = []
         for k in range(base, base + max(3, min(args.steps, args.e2e_steps))):
             arr, parts = packets_of(k)
             t0 = time.perf_counter()
-            run(ring, parts, consumer=lambda r: (cor.push(r[0]), cor.sync()))
+            run(ring, parts, consumer=consume)
             cor.dump_into(vis, reset=True)
             ee.append(time.perf_counter() - t0)
         e_ms = 1e3 * sum(ee) / len(ee)
         e2e = {"value": arr.nbytes / (e_ms * 1e-3) / 1e9, "unit": "GB/s", "h2d_bytes_per_step": payload,
                "d2h_bytes_per_step": vis.numel() * 8, "ms_per_step": e_ms, "steps": len(ee),
-               "path": "packets -> ring -> corr_push (pinned block) -> corr_dump"}
+               "path": ("packets -> ring (packet order) -> device -> pk_turn -> corr_push -> corr_dump"
+                        if porder else "packets -> ring -> corr_push (pinned block) -> corr_dump")}
         cor.close()
     ring.close()
     if rank != 0:
@@ -995,6 +1014,8 @@ def run_ingest(args, w, world, rank, local):
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u8", "data": "synthetic (seeded random 4-bit codes)",
         "config": {"workload": w["desc"], "producer_threads": threads,
+                   "block_layout": "packet order (reordered by pk_turn on the GPU)" if porder
+                                   else "[t][c][i] assembled on the host",
                    "host_cores": os.cpu_count(), "parallelism": "%d host" % world},
         "packets_per_s": st["packets"] / max(1e-9, sum(el) + args.warmup * 0) if False else
                          len(arr) / (ms * 1e-3),
@@ -1187,8 +1208,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--pipeline-sms", type=int, default=-1,
                     help="SMs for the pipelined corner turn (0 = off, -1 = pick by a timed sweep)")
-    ap.add_argument("--ingest-threads", type=int, default=4,
+    ap.add_argument("--ingest-threads", type=int, default=8,
                     help="producer threads of the packet-ingest workload")
+    ap.add_argument("--ingest-layout", choices=["packet", "tci"], default="packet",
+                    help="ring blocks in packet order (reordered on the GPU) or [t][c][i]")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--service-requests", type=int, default=0,

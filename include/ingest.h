@@ -19,7 +19,9 @@
  * stream as one [t][c][i] byte array (CORR_L_TCI of xengine.h) of T spectra,
  * C = n_xids n_chans_pkt channels and N = n_fids n_inputs_pkt inputs -- the
  * block corr_push takes.  A packet that never arrives leaves zeros (integrated
- * as nothing) and is reported.
+ * as nothing) and is reported.  With PK_F_PACKET_ORDER each payload is instead
+ * copied whole, in arrival-slot order, and pk_turn reorders the block on the
+ * GPU: one 8 KB copy per packet on the host instead of 8 n_chans_pkt rows.
  *
  * Ring: n_segments block buffers (3 in the paper's Hashpipe setup), each
  * free, open (filling), closed (complete or given up) or handed out.  A block
@@ -51,10 +53,14 @@ typedef struct pk_layout {
   int n_time;        /* spectra per block, a positive multiple of 8       */
 } pk_layout;
 
-#define PK_F_NO_CRC 0x1u /* accept packets without checking the CRC */
+#define PK_F_NO_CRC 0x1u        /* accept packets without checking the CRC     */
+#define PK_F_PACKET_ORDER 0x2u  /* blocks in packet order (see pk_turn)         */
 
 typedef struct pk_block {
-  const uint8_t* data;      /* [T][C][N] bytes, owned by the ring (page-locked
+  const uint8_t* data;      /* [T][C][N] bytes -- or, with PK_F_PACKET_ORDER,
+                               [T/8][n_fids][n_xids][8][n_chans_pkt][n_inputs_pkt]:
+                               each payload as it arrived, one contiguous copy --
+                               owned by the ring (page-locked
                                when a CUDA device is present); valid until
                                pk_release                                    */
   uint64_t index;           /* block number b                                */
@@ -117,6 +123,18 @@ int pk_release(pk_ring* ring);
 int pk_flush(pk_ring* ring);
 
 int pk_get_stats(pk_ring* ring, pk_stats* out);
+
+/*
+ * pk_turn -- GPU: a block in packet order (device memory, as a
+ * PK_F_PACKET_ORDER ring hands it out, copied to the device) into the
+ * X-engine's [c][i][t] order (CORR_L_CIT): out[(c N + i) out_stride + t]
+ * with c = Xid n_chans_pkt + cc, i = Fid n_inputs_pkt + ii, t = 8 slot + tt.
+ * out_stride >= n_time.  Queued on `stream` (a cudaStream_t, or NULL for the
+ * legacy stream).  CORR_EINVAL for a bad layout, a host pointer, or
+ * n_fids * n_xids > 65535.
+ */
+int pk_turn(const pk_layout* layout, const void* packets, void* out, long long out_stride,
+            void* stream);
 
 /* pk_crc32 -- IEEE 802.3 CRC-32 (reflected polynomial 0xEDB88320, initial and
  * final XOR 0xFFFFFFFF): the value a packet's trailer carries. */

@@ -103,3 +103,18 @@ def mcnt_gaps(packets, n_chans_pkt, n_inputs_pkt, n_fids=256, n_xids=256):
         if key not in last or mcnt > last[key]:
             last[key] = mcnt
     return events, skipped
+
+
+def packet_order(data_tci, n_fids, n_inputs_pkt, n_xids, n_chans_pkt):
+    """A [T][C][N] block rearranged as the packets carry it, slot by slot:
+    [T/8][fid][xid][8][n_chans_pkt][n_inputs_pkt] -- each payload whole, the
+    layout of a packet-order ring (written out packet by packet)."""
+    T = data_tci.shape[0]
+    out = np.zeros((T // STACK, n_fids, n_xids, STACK, n_chans_pkt, n_inputs_pkt), dtype=np.uint8)
+    for slot in range(T // STACK):
+        for fid in range(n_fids):
+            for xid in range(n_xids):
+                out[slot, fid, xid] = data_tci[STACK * slot:STACK * slot + STACK,
+                                               xid * n_chans_pkt:(xid + 1) * n_chans_pkt,
+                                               fid * n_inputs_pkt:(fid + 1) * n_inputs_pkt]
+    return out

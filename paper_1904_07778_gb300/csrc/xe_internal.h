@@ -116,6 +116,12 @@ bool make_sample_tmap(CUtensorMap* m, const uint8_t* x, int n_time, long long ro
 cudaError_t turn_launch(const uint8_t* in, uint8_t* out, int T, int G, int K, long long out_stride,
                         cudaStream_t s, bool pair_rows = false, int persist_ctas = 0);
 
+// A block in packet order, [slot][fid][xid][8][chans_pkt][inputs_pkt] bytes,
+// becomes [c][i][t] rows of out_stride bytes (c = xid chans_pkt + cc,
+// i = fid inputs_pkt + ii, t = 8 slot + tt).
+cudaError_t pkt_turn_launch(const uint8_t* in, uint8_t* out, int n_fids, int inputs_pkt, int n_xids,
+                            int chans_pkt, int T, long long out_stride, cudaStream_t s);
+
 // 8-bit samples already in [row][t][re/im] order (row = channel x input):
 // out[row][p][t] = in[row][t][p], output rows of out_stride bytes.
 cudaError_t split_planes_launch(const uint8_t* in, uint8_t* out, long long rows, int T,

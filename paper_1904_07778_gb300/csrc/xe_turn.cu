@@ -202,6 +202,85 @@ __global__ void __launch_bounds__(256 * kTurnGroups, 1)
   asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
+// ---------------------------------------------------------------- packet turn
+// A block assembled in packet order -- [slot][fid][xid][8 spectra][chans_pkt
+// x inputs_pkt bytes] -- becomes the X-engine's [c][i][t] rows.  For one
+// (fid, xid) and 128 consecutive bytes k of a packet row, the spectra
+// t = 8 slot + tt form a 256 x 128 tile like the corner turn's, except that
+// a tile row's address steps by the packet stream stride every 8 spectra and
+// each byte k names its own output row: channel xid chans_pkt + k / inputs_pkt,
+// input fid inputs_pkt + k mod inputs_pkt.
+struct PktGeom {
+  int n_fids, inputs_pkt, n_xids, chans_pkt, T;
+  long long os;
+  int vec_ok;
+};
+
+__global__ void __launch_bounds__(256, 4) pkt_turn_kernel(const uint8_t* __restrict__ in,
+                                                          uint8_t* __restrict__ out, PktGeom q) {
+  __shared__ __align__(16) uint32_t tile[kTT * 32];
+  const int rowb = q.chans_pkt * q.inputs_pkt;           // bytes of one spectrum of a packet
+  const long long P = 8LL * rowb;                        // payload bytes
+  const long long slot_stride = (long long)q.n_fids * q.n_xids * P;
+  const int t0 = blockIdx.x * kTT, k0 = blockIdx.y * kTK;
+  const int stream = blockIdx.z, fid = stream / q.n_xids, xid = stream % q.n_xids;
+  const int N = q.n_fids * q.inputs_pkt;
+  const uint8_t* base = in + ((long long)fid * q.n_xids + xid) * P;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool full = q.vec_ok && t0 + kTT <= q.T && k0 + kTK <= rowb;
+  if (full) {
+    uint32_t v[4][8];
+#pragma unroll
+    for (int it = 0; it < 4; ++it) {
+      const int e = it * 256 + tid, r = e >> 2, p = e & 3, t = t0 + r;
+      ld32B(base + (long long)(t >> 3) * slot_stride + (long long)(t & 7) * rowb + k0 + 32 * p, v[it]);
+    }
+#pragma unroll
+    for (int it = 0; it < 4; ++it) {
+      const int e = it * 256 + tid, r = e >> 2, p = e & 3;
+      const bool odd = r & 1;
+      const uint4 lo = make_uint4(v[it][0], v[it][1], v[it][2], v[it][3]);
+      const uint4 hi = make_uint4(v[it][4], v[it][5], v[it][6], v[it][7]);
+      *reinterpret_cast<uint4*>(&tile[tile_word(r, 8 * p + (odd ? 4 : 0))]) = odd ? hi : lo;
+      *reinterpret_cast<uint4*>(&tile[tile_word(r, 8 * p + (odd ? 0 : 4))]) = odd ? lo : hi;
+    }
+  } else {
+    for (int e = tid; e < kTT * 32; e += 256) {
+      const int r = e >> 5, w = e & 31, t = t0 + r;
+      uint32_t x = 0;
+      if (t < q.T) {
+        const uint8_t* src = base + (long long)(t >> 3) * slot_stride + (long long)(t & 7) * rowb;
+        for (int b = 0; b < 4; ++b)
+          if (k0 + 4 * w + b < rowb) x |= (uint32_t)src[k0 + 4 * w + b] << (8 * b);
+      }
+      tile[tile_word(r, w)] = x;
+    }
+  }
+  __syncthreads();
+  const int kq = 4 * warp + (lane >> 3), ts = lane & 7;
+  uint32_t a[32];
+#pragma unroll
+  for (int j = 0; j < 32; ++j) a[j] = tile[tile_word(ts * 32 + j, kq)];
+#pragma unroll
+  for (int j = 0; j < 32; j += 4) transpose4x4(a[j], a[j + 1], a[j + 2], a[j + 3]);
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const int k = k0 + 4 * kq + c;
+    if (k >= rowb) continue;
+    const int ch = xid * q.chans_pkt + k / q.inputs_pkt, inp = fid * q.inputs_pkt + k % q.inputs_pkt;
+    const int tb = t0 + ts * 32;
+    uint8_t* o = out + ((long long)ch * N + inp) * q.os + tb;
+    if (full) {
+      const uint32_t r[8] = {a[c], a[4 + c], a[8 + c], a[12 + c],
+                             a[16 + c], a[20 + c], a[24 + c], a[28 + c]};
+      st32B(o, r);
+    } else {
+      for (int b = 0; b < 32; ++b)
+        if (tb + b < q.T) o[b] = (uint8_t)(a[4 * (b >> 2) + c] >> ((b & 3) * 8));
+    }
+  }
+}
+
 // ---------------------------------------------------------------- plane split
 // out[r][p][t] = in[r][t][p] for 8-bit complex samples: 16 samples (32 bytes)
 // per thread become 16 real and 16 imaginary bytes.
@@ -296,6 +375,17 @@ cudaError_t split_planes_launch(const uint8_t* in, uint8_t* out, long long rows,
   if (blocks > 152 * 16) blocks = 152 * 16;
   if (blocks < 1) blocks = 1;
   split_planes_kernel<<<(unsigned)blocks, 256, 0, s>>>(in, out, rows, T, out_stride, vec_ok);
+  return cudaGetLastError();
+}
+
+cudaError_t pkt_turn_launch(const uint8_t* in, uint8_t* out, int n_fids, int inputs_pkt, int n_xids,
+                            int chans_pkt, int T, long long out_stride, cudaStream_t s) {
+  PktGeom q{n_fids, inputs_pkt, n_xids, chans_pkt, T, out_stride, 0};
+  const int rowb = chans_pkt * inputs_pkt;
+  q.vec_ok = rowb % 32 == 0 && out_stride % 32 == 0 && T % 32 == 0 &&
+             reinterpret_cast<uintptr_t>(in) % 32 == 0 && reinterpret_cast<uintptr_t>(out) % 32 == 0;
+  dim3 grid((T + kTT - 1) / kTT, (rowb + kTK - 1) / kTK, n_fids * n_xids);
+  pkt_turn_kernel<<<grid, 256, 0, s>>>(in, out, q);
   return cudaGetLastError();
 }
 

@@ -12,7 +12,8 @@ import numpy as np
 from .xengine import CORR_EBUSY, CORR_OK, CORR_ETIMEDOUT, CorrError, _lib  # noqa: F401
 
 PK_F_NO_CRC = 1
-EXPORTS = ["pk_create", "pk_push", "pk_push_many", "pk_next", "pk_release", "pk_flush", "pk_get_stats",
+PK_F_PACKET_ORDER = 2
+EXPORTS = ["pk_create", "pk_push", "pk_push_many", "pk_turn", "pk_next", "pk_release", "pk_flush", "pk_get_stats",
            "pk_crc32", "pk_destroy"]
 
 
@@ -44,6 +45,8 @@ _lib.pk_crc32.argtypes = [ctypes.c_char_p, _SZ]
 _lib.pk_crc32.restype = ctypes.c_uint32
 _lib.pk_push_many.argtypes = [_P, _P, _SZ, _SZ, _SZ, _P]
 _lib.pk_push_many.restype = _SZ
+_lib.pk_turn.argtypes = [ctypes.POINTER(PkLayout), _P, _P, ctypes.c_longlong, _P]
+_lib.pk_turn.restype = _I
 _lib.pk_destroy.argtypes = [_P]
 _lib.pk_destroy.restype = None
 for _f in ("pk_create", "pk_push", "pk_next", "pk_release", "pk_flush", "pk_get_stats"):
@@ -58,12 +61,16 @@ class PacketRing:
     """F-engine packets in, [t][c][i] blocks out (in block order)."""
 
     def __init__(self, n_fids, n_inputs_pkt, n_xids, n_chans_pkt, n_time, n_segments=3,
-                 check_crc=True):
+                 check_crc=True, packet_order=False):
         self.layout = PkLayout(n_fids, n_inputs_pkt, n_xids, n_chans_pkt, n_time)
-        self.shape = (n_time, n_xids * n_chans_pkt, n_fids * n_inputs_pkt)
+        self.packet_order = packet_order
+        if packet_order:
+            self.shape = (n_time // 8, n_fids, n_xids, 8, n_chans_pkt, n_inputs_pkt)
+        else:
+            self.shape = (n_time, n_xids * n_chans_pkt, n_fids * n_inputs_pkt)
+        flags = (0 if check_crc else PK_F_NO_CRC) | (PK_F_PACKET_ORDER if packet_order else 0)
         out = _P()
-        st = _lib.pk_create(ctypes.byref(self.layout), n_segments, 0 if check_crc else PK_F_NO_CRC,
-                            ctypes.byref(out))
+        st = _lib.pk_create(ctypes.byref(self.layout), n_segments, flags, ctypes.byref(out))
         if st != CORR_OK:
             raise CorrError(st, "pk_create")
         self._r = out
@@ -88,14 +95,27 @@ class PacketRing:
             return None
         if st != CORR_OK:
             raise CorrError(st, "pk_next")
-        T, C, N = self.shape
-        buf = (ctypes.c_uint8 * (T * C * N)).from_address(b.data)
-        data = np.frombuffer(buf, dtype=np.uint8).reshape(T, C, N)
         L = self.layout
+        nbytes = L.n_time * L.n_xids * L.n_chans_pkt * L.n_fids * L.n_inputs_pkt
+        buf = (ctypes.c_uint8 * nbytes).from_address(b.data)
+        data = np.frombuffer(buf, dtype=np.uint8).reshape(self.shape)
         rbuf = (ctypes.c_uint8 * b.n_packets).from_address(b.received)
-        received = np.frombuffer(rbuf, dtype=np.uint8).reshape(T // 8, L.n_fids, L.n_xids)
+        received = np.frombuffer(rbuf, dtype=np.uint8).reshape(L.n_time // 8, L.n_fids, L.n_xids)
         return data, {"index": b.index, "mcnt0": b.mcnt0, "n_packets": b.n_packets,
                       "n_missing": b.n_missing, "received": received.astype(bool)}
+
+    def turn(self, packets_dev, out_dev, out_stride=None, stream=None):
+        """pk_turn: a packet-order block on the device -> [c][i][t] rows."""
+        from .xengine import _ptr_and_size
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        st = _lib.pk_turn(ctypes.byref(self.layout), _P(_ptr_and_size(packets_dev)[0]),
+                          _P(_ptr_and_size(out_dev)[0]),
+                          out_stride if out_stride is not None else self.layout.n_time,
+                          _P(stream) if stream else None)
+        if st != CORR_OK:
+            raise CorrError(st, "pk_turn")
 
     def release(self):
         st = _lib.pk_release(self._r)

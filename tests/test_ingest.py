@@ -198,6 +198,25 @@ def test_push_many_equals_single_pushes():
     assert all(np.array_equal(g[1], b) for g, b in zip(got[1:], blocks[1:]))
 
 
+def test_packet_order_ring_matches_the_oracle():
+    """The same faulty stream into a packet-order ring: every block equals the
+    oracle's assembly rearranged into packet order, losses zero."""
+    rng = np.random.default_rng(21)
+    blocks = _blocks(3, seed=22)
+    clean = _stream(blocks)
+    stream = [p for p in clean if rng.random() > 0.1]
+    stream += stream[:5]                                   # duplicates
+    with _ring(packet_order=True) as ring:
+        _feed(ring, stream)
+        ring.flush()
+        got = _drain(ring)
+    want, _ = op.assemble(stream, 3, 4, 2, 8, T)
+    assert [g[0] for g in got] == sorted(want)
+    for idx, data, info in got:
+        assert np.array_equal(data, op.packet_order(want[idx][0], 3, 4, 2, 8))
+        assert np.array_equal(info["received"], want[idx][1])
+
+
 def test_no_crc_mode_accepts_corrupt_packets():
     pk = _stream(_blocks(1, seed=6))
     bad = bytearray(pk[0])
@@ -250,6 +269,66 @@ def test_bad_layouts_rejected():
                        lay["n_time"])
     with pytest.raises(CorrError):
         _ring(n_segments=1)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("geom,T,pad", [
+    ((6, 32, 32, 32), 1024, 0),      # the cylinder's packets
+    ((6, 32, 32, 32), 264, 0),       # a ragged last tile of spectra
+    ((3, 12, 5, 10), 72, 8),         # rows of 120 bytes: the byte path; padded output rows
+    ((1, 16, 3, 8), 512, 32)])
+def test_pk_turn_reorders_exactly(geom, T, pad):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    F, I, X, K = geom
+    N, C = F * I, X * K
+    rng = np.random.default_rng(T + F)
+    data = rng.integers(0, 256, (T, C, N), dtype=np.uint8)           # [t][c][i]
+    po = op.packet_order(data, F, I, X, K)
+    ring = PacketRing(F, I, X, K, T)
+    dev_in = torch.from_numpy(np.ascontiguousarray(po).reshape(-1)).cuda()
+    os_ = T + pad
+    out = torch.full((C * N * os_,), 0x5A, dtype=torch.uint8, device="cuda")
+    ring.turn(dev_in, out, out_stride=os_)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().reshape(C, N, os_)
+    assert np.array_equal(got[:, :, :T], data.transpose(1, 2, 0))
+    assert np.all(got[:, :, T:] == 0x5A)
+    ring.close()
+
+
+@pytest.mark.gpu
+def test_packet_order_to_visibilities():
+    """Packets -> packet-order ring -> device -> pk_turn -> corr_push ([c][i][t])."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import oracle
+    from paper_1904_07778_gb300.xengine import CORR_L_CIT, Correlator
+    rng = np.random.default_rng(23)
+    blocks = _blocks(2, seed=24)
+    pk = _stream(blocks, first=3)
+    keep = [p for p in pk if rng.random() > 0.1]
+    assembled, _ = op.assemble(keep, 3, 4, 2, 8, T)
+    with _ring(packet_order=True) as ring, Correlator(N, C, T, bits=4, layout=CORR_L_CIT) as cor:
+        for p in keep:
+            assert ring.push(p) == CORR_OK
+        ring.flush()
+        dev = torch.empty(T * C * N, dtype=torch.uint8, device="cuda")
+        cit = torch.empty(T * C * N, dtype=torch.uint8, device="cuda")
+        want = None
+        for _ in range(2):
+            data, info = ring.next(0)
+            dev.copy_(torch.from_numpy(data.reshape(-1)))
+            ring.turn(dev, cit)
+            cor.push(cit, seq=info["index"])
+            cor.sync()
+            ring.release()
+            want = oracle.correlate(assembled[info["index"]][0].reshape(-1), N, C, T,
+                                    layout=oracle.L_TCI, out=want)
+        vis = cor.dump()
+    assert np.array_equal(vis, want)
 
 
 @pytest.mark.gpu

@@ -82,3 +82,13 @@ def test_mcnt_gap_counting_by_hand():
     pk = [_pkt(0, 0, 0, bytes(8)), _pkt(0, 1, 0, bytes(8)), _pkt(2, 0, 0, bytes(8)),
           _pkt(1, 0, 0, bytes(8)), _pkt(1, 1, 0, bytes(8))]
     assert op.mcnt_gaps(pk, 1, 1) == (1, 1)
+
+
+def test_packet_order_by_hand():
+    # 2 Fids x 1 input, 2 Xids x 1 channel, T = 16: payload (slot, fid, xid) holds
+    # spectra 8 slot .. 8 slot + 7 of channel xid, input fid
+    data = np.arange(16 * 2 * 2, dtype=np.uint8).reshape(16, 2, 2)
+    po = op.packet_order(data, 2, 1, 2, 1)
+    assert po.shape == (2, 2, 2, 8, 1, 1)
+    assert po[1, 0, 1, 3, 0, 0] == data[11, 1, 0]
+    assert po[0, 1, 0, 7, 0, 0] == data[7, 0, 1]
