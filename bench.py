@@ -484,6 +484,13 @@ def run_gpu(args, w, world, rank, local):
         if k in dom:
             roof[k] = dom[k]
     roof["kernel"] = dom["kernel"]
+    roof["sms"] = dom["sms"]
+    roof["frac_of_its_sms"] = dom["frac_of_its_sms"]
+    if pipe:
+        roof["note"] = ("runs on %d of %d SMs beside the pipelined corner turn (which holds the "
+                        "other %d); frac is against the whole GPU's peak, frac_of_its_sms against "
+                        "the peak of its SMs; --pipeline-sms 0 runs it alone on every SM"
+                        % (dom["sms"], n_sm, n_sm - dom["sms"]))
     ms_step = ms_max / args.steps
     value = world * ops_per_step(w) / (ms_step * 1e-3) / 1e12
     line = {
