@@ -227,11 +227,12 @@ __device__ __forceinline__ void fir_tap(float (&y0)[8], float (&y1)[8], const fl
   }
 }
 
+// Two CTAs per SM where 256-thread CTAs fit twice (registers capped at 128,
+// with a few spills): measured 10% faster than one CTA at 217 registers.
+__host__ __device__ constexpr int fe_min_blocks(int logm) { return logm <= 11 ? 2 : 1; }
+
 template <int LOGM>
-#ifndef XE_FE_MIN_BLOCKS
-#define XE_FE_MIN_BLOCKS 1
-#endif
-__global__ void __launch_bounds__(fe_threads(LOGM), XE_FE_MIN_BLOCKS) fengine_kernel(FeArgs a) {
+__global__ void __launch_bounds__(fe_threads(LOGM), fe_min_blocks(LOGM)) fengine_kernel(FeArgs a) {
   constexpr int M = 1 << LOGM, C = M / 2;
   constexpr int TPU = M / 8;                 // threads per FFT unit
   constexpr int NT = fe_threads(LOGM);
