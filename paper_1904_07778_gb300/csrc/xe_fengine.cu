@@ -204,6 +204,37 @@ __device__ __forceinline__ float biased_byte_to_float(uint32_t w, int r) {
   return __int_as_float((int)__byte_perm(w, 0x4B400000u, 0x7650u + (unsigned)r)) - 12583040.0f;
 }
 
+// Taps 0..3 of the filter for 8 consecutive samples of both inputs of a
+// pair, with aligned 8-byte rows: every tap's loads are issued before any
+// arithmetic (taps past `taps` load nothing and add nothing), then
+// y += h x in FP32 fused multiply-adds.
+__device__ __forceinline__ void fir_taps4(float (&y0)[8], float (&y1)[8], const float (&h)[4][8],
+                                          const int8_t* x0, const int8_t* x1, long long M,
+                                          int taps, bool has1) {
+  uint32_t w[4][4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    int2 a = make_int2(0, 0), b = make_int2(0, 0);
+    if (q < taps) {
+      a = __ldg(reinterpret_cast<const int2*>(x0 + q * M));
+      if (has1) b = __ldg(reinterpret_cast<const int2*>(x1 + q * M));
+    }
+    w[q][0] = (uint32_t)a.x ^ 0x80808080u;
+    w[q][1] = (uint32_t)a.y ^ 0x80808080u;
+    w[q][2] = (uint32_t)b.x ^ 0x80808080u;
+    w[q][3] = (uint32_t)b.y ^ 0x80808080u;
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    if (q >= taps) break;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      y0[r] = fmaf(h[q][r], biased_byte_to_float(w[q][r >> 2], r & 3), y0[r]);
+      y1[r] = fmaf(h[q][r], biased_byte_to_float(w[q][2 + (r >> 2)], r & 3), y1[r]);
+    }
+  }
+}
+
 // One tap of the filter for 8 consecutive samples of both inputs of a pair:
 // y += h x, in FP32 fused multiply-adds.
 __device__ __forceinline__ void fir_tap(float (&y0)[8], float (&y1)[8], const float (&h)[8],
@@ -302,10 +333,14 @@ __global__ void __launch_bounds__(fe_threads(LOGM), fe_min_blocks(LOGM)) fengine
         const int8_t* x1 = x0 + a.adc_stride;
         // taps 0..3 with their coefficients in registers (static indices),
         // then any further taps with coefficients from the table
+        if (a.vec_in) {
+          fir_taps4(y0, y1, hr, x0, x1, M, a.taps, has1);
+        } else {
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-          if (q < a.taps)
-            fir_tap(y0, y1, hr[q], x0 + (long long)q * M, x1 + (long long)q * M, has1, a.vec_in);
+          for (int q = 0; q < 4; ++q)
+            if (q < a.taps)
+              fir_tap(y0, y1, hr[q], x0 + (long long)q * M, x1 + (long long)q * M, has1, 0);
+        }
         for (int q = 4; q < a.taps; ++q) {
           float hq[8];
           const float4 hA = __ldg(reinterpret_cast<const float4*>(a.h + q * M + 8 * lt));
