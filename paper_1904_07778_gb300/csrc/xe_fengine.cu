@@ -174,27 +174,27 @@ __device__ __forceinline__ void fft_pass(float2* const (&zs)[NB], int lt, int Ns
   __syncthreads();
 }
 
-// p = v g (fix_36_24) -> rne(p / 2^21) clamped to the fix_4_3 range, in
-// 32-bit arithmetic: |v| >= vsat = ceil(7.5 2^21 / g) means |p| >= 7.5 2^21,
-// which rounds to 8 or more and saturates at 7; below it |p| < 2^24.
-__device__ __forceinline__ int equalise(int v, int g, int vsat) {
-  const int av = v < 0 ? -v : v;
-  const int p = (int)((unsigned)v * (unsigned)g);  // used only when it did not wrap
-  const int fl = p >> 21;                           // floor(p / 2^21)
-  const int rem = p & 0x1FFFFF;
-  const int q = fl + ((rem > 0x100000) || (rem == 0x100000 && (fl & 1)) ? 1 : 0);
-  return av >= vsat ? (v < 0 ? -7 : 7) : q;
+// The equaliser in FP32, exactly: with |v| below vsat = ceil(7.5 2^21 / g)
+// the fix_36_24 product p = v g is an integer below 7.5 2^21 < 2^24, so
+// v (g 2^-21) is exact in FP32, and one fused multiply-add with 1.5 2^23
+// rounds it half to even; the sum's low four bits are the fix_4_3 code in
+// two's complement.  At or above vsat, |p| rounds to 8 or more and the code
+// saturates at +-7.
+__host__ __device__ inline float saturation_threshold(uint32_t g) {
+  return g == 0 ? 3.0e38f : (float)((15728640u + g - 1) / g);  // 7.5 2^21 = 15728640
 }
-__host__ __device__ constexpr int saturation_threshold(uint32_t g) {
-  return g == 0 ? 0x7FFFFFFF : (int)((15728640u + g - 1) / g);  // 7.5 2^21 = 15728640
+__device__ __forceinline__ int equalise_nibble(float vf, float gs, float vsat) {
+  const int code = __float_as_int(fmaf(vf, gs, 12582912.0f)) & 0xF;
+  return fabsf(vf) >= vsat ? (vf < 0.f ? 0x9 : 0x7) : code;
 }
 
 // clamp(rne(x), -2^17, 2^17 - 1): clamping first keeps |x| < 2^22, where
-// adding 1.5 2^23 rounds x to the nearest integer, ties to even, and the
-// sum's low bits hold it.
-__device__ __forceinline__ int round18(float x) {
+// adding 1.5 2^23 rounds x to the nearest integer, ties to even.  Returns
+// the sum; its low bits hold the integer, and subtracting 1.5 2^23 gives it
+// back exactly as a float.
+__device__ __forceinline__ float round18_biased(float x) {
   const float c = fminf(fmaxf(x, -131072.0f), 131071.0f);
-  return __float_as_int(c + 12582912.0f) - 0x4B400000;
+  return c + 12582912.0f;
 }
 
 // Byte r of w (biased: w holds x ^ 0x80 per byte, x the int8 sample) as the
@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(fe_threads(LOGM), fe_min_blocks(LOGM)) fengine
   if constexpr (REM == 2) load_twiddles<M, 4>(twl, lt, 1 << (3 * P8), a.w);
   if constexpr (REM == 1) load_twiddles<M, 2>(twl, lt, 1 << (3 * P8), a.w);
 
-  int g[4][2], vsat[4][2];
+  float gs[4][2], vsat[4][2];  // gain as g 2^-21 (exact) and its saturation threshold
   unsigned long long pw[4][2];
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
@@ -312,7 +312,7 @@ __global__ void __launch_bounds__(fe_threads(LOGM), fe_min_blocks(LOGM)) fengine
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
       const uint32_t gj = (j == 0 || has1) ? a.gain[(long long)nu * N + i0 + j] : 0u;
-      g[k][j] = (int)gj;
+      gs[k][j] = (float)gj * 4.76837158203125e-07f;  // 2^-21
       vsat[k][j] = saturation_threshold(gj);
       pw[k][j] = 0ull;
     }
@@ -383,15 +383,16 @@ __global__ void __launch_bounds__(fe_threads(LOGM), fe_min_blocks(LOGM)) fengine
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
           if (j == 1 && !has1) break;
-          const int vr = round18(X[j][0]), vi = round18(X[j][1]);
+          const float sr = round18_biased(X[j][0]), si = round18_biased(X[j][1]);
+          const int vr = __float_as_int(sr) - 0x4B400000, vi = __float_as_int(si) - 0x4B400000;
           if (a.spec || a.v18) {
             const long long ei = ((t * C + nu) * N + i0 + j) * 2;
             if (a.spec) *reinterpret_cast<float2*>(a.spec + ei) = make_float2(X[j][0], X[j][1]);
             if (a.v18) *reinterpret_cast<int2*>(a.v18 + ei) = make_int2(vr, vi);
           }
           if (a.power) pw[k][j] += (unsigned long long)((long long)vr * vr + (long long)vi * vi);
-          const int qr = equalise(vr, g[k][j], vsat[k][j]) & 0xF;
-          const int qi = equalise(vi, g[k][j], vsat[k][j]) & 0xF;
+          const int qr = equalise_nibble(sr - 12582912.0f, gs[k][j], vsat[k][j]);
+          const int qi = equalise_nibble(si - 12582912.0f, gs[k][j], vsat[k][j]);
           codes[(s * C + nu) * 2 + j] = (uint8_t)(a.lo_is_real ? (qi << 4) | qr : (qr << 4) | qi);
         }
       }
