@@ -319,12 +319,64 @@ __global__ void __launch_bounds__(fe_threads(LOGM), fe_min_blocks(LOGM)) fengine
   }
 
   for (int sb = 0; sb < ng; sb += kFeNB * U) {
+    // ---- polyphase filter: y[n] = sum_q h[q M + n] x[(t + q) M + n]
+    if (U == 1 && a.vec_in && a.taps <= 4) {
+      // One unit per CTA: the unit's spectra sb, sb + 1, ... are adjacent and
+      // share frames, so each frame is loaded and converted once and added
+      // into every spectrum that uses it (static tap indices).
+      constexpr int NF = kFeNB + 3;  // frames of kFeNB spectra at up to 4 taps
+      const int8_t* xb = a.adc + (long long)i0 * a.adc_stride + (long long)(t0 + sb) * M + 8 * lt;
+      const int last = min(ng - 1 - sb, kFeNB - 1);  // last active spectrum of the iteration
+      float y[kFeNB][2][8];
+#pragma unroll
+      for (int e = 0; e < kFeNB; ++e)
+#pragma unroll
+        for (int r = 0; r < 8; ++r) y[e][0][r] = y[e][1][r] = 0.f;
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        if (f > last + a.taps - 1) break;  // frames past the last active spectrum's taps
+        const int2 w0 = __ldg(reinterpret_cast<const int2*>(xb + (long long)f * M));
+        const int2 w1 = has1 ? __ldg(reinterpret_cast<const int2*>(xb + a.adc_stride + (long long)f * M))
+                             : make_int2(0, 0);
+        const uint32_t b[4] = {(uint32_t)w0.x ^ 0x80808080u, (uint32_t)w0.y ^ 0x80808080u,
+                               (uint32_t)w1.x ^ 0x80808080u, (uint32_t)w1.y ^ 0x80808080u};
+        float x[2][8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+          x[0][r] = biased_byte_to_float(b[r >> 2], r & 3);
+          x[1][r] = biased_byte_to_float(b[2 + (r >> 2)], r & 3);
+        }
+#pragma unroll
+        for (int e = 0; e < kFeNB; ++e) {
+          const int q = f - e;  // this frame is tap q of spectrum e
+          if (q < 0 || q > 3 || q >= a.taps || e > last) continue;
+#pragma unroll
+          for (int r = 0; r < 8; ++r) {
+            y[e][0][r] = fmaf(hr[q][r], x[0][r], y[e][0][r]);
+            y[e][1][r] = fmaf(hr[q][r], x[1][r], y[e][1][r]);
+          }
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < kFeNB; ++e) {
+#pragma unroll
+        for (int r = 0; r < 8; ++r) zs[e][fe_pad(8 * lt + r)] = make_float2(y[e][0][r], y[e][1][r]);
+      }
+      // the next iteration's newest frames come from DRAM: ask for those of
+      // its active spectra now
+#pragma unroll
+      for (int e = 0; e < kFeNB; ++e) {
+        if (sb + kFeNB + e >= ng) break;
+        const int8_t* nx = xb + (long long)(kFeNB + e + a.taps - 1) * M;
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(nx));
+        if (has1) asm volatile("prefetch.global.L1 [%0];" ::"l"(nx + a.adc_stride));
+      }
+    } else {
 #pragma unroll
     for (int e = 0; e < kFeNB; ++e) {
       const int s = sb + e * U + u;
       const bool active = s < ng;
       const long long t = t0 + s;
-      // ---- polyphase filter: y[n] = sum_q h[q M + n] x[(t + q) M + n]
       float y0[8], y1[8];
 #pragma unroll
       for (int r = 0; r < 8; ++r) y0[r] = y1[r] = 0.f;
@@ -359,6 +411,7 @@ __global__ void __launch_bounds__(fe_threads(LOGM), fe_min_blocks(LOGM)) fengine
         asm volatile("prefetch.global.L1 [%0];" ::"l"(nx));
         if (has1) asm volatile("prefetch.global.L1 [%0];" ::"l"(nx + a.adc_stride));
       }
+    }
     }
     __syncthreads();
     // ---- FFTs of y_2k + j y_2k+1 (natural order out), kFeNB side by side

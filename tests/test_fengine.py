@@ -121,6 +121,8 @@ CASES = [  # (N, C, taps, T, shift)
     (2, 16, 1, 32, 0), (2, 16, 4, 33, 0), (3, 32, 4, 40, 1), (4, 64, 2, 64, 0),
     (5, 128, 8, 17, 2), (8, 256, 4, 96, 0), (6, 512, 4, 70, 1), (4, 1024, 4, 64, 0),
     (2, 2048, 4, 33, 3), (1, 64, 3, 5, 0),
+    # one FFT unit per CTA (frame-major filter) with fewer taps and ragged groups
+    (3, 1024, 2, 41, 0), (2, 2048, 1, 9, 1), (4, 1024, 3, 35, 0),
 ]
 
 
