@@ -143,76 +143,42 @@ void free_ring(pk_ring* r) {
   delete r;
 }
 
-}  // namespace
+// ---------------------------------------------------------------- push steps
+// A packet whose slot is claimed: what its copy and its finish need.
+struct Claim {
+  const uint8_t* src;
+  Segment* seg;
+  uint8_t* dst;
+  int slot, fid, xid;
+};
 
-extern "C" {
-
-uint32_t pk_crc32(const void* data, size_t n) {
-  return crc32(static_cast<const uint8_t*>(data), n);
-}
-
-int pk_create(const pk_layout* L, int n_segments, unsigned flags, pk_ring** out) {
-  if (!out) return CORR_EINVAL;
-  *out = nullptr;
-  if (!L || L->n_fids < 1 || L->n_fids > 256 || L->n_xids < 1 || L->n_xids > 256 ||
-      L->n_inputs_pkt < 1 || L->n_chans_pkt < 1 || L->n_time < 8 || L->n_time % 8 ||
-      n_segments < 2 || n_segments > 64 || (flags & ~(PK_F_NO_CRC | PK_F_PACKET_ORDER)))
-    return CORR_EINVAL;
-  pk_ring* r = new (std::nothrow) pk_ring;
-  if (!r) return CORR_ENOMEM;
-  r->L = *L;
-  r->n_seg = n_segments;
-  r->flags = flags;
-  r->C = L->n_xids * L->n_chans_pkt;
-  r->N = L->n_fids * L->n_inputs_pkt;
-  r->slots = L->n_time / 8;
-  r->per_block = r->slots * L->n_fids * L->n_xids;
-  r->payload = (size_t)8 * L->n_chans_pkt * L->n_inputs_pkt;
-  r->pkt_len = 8 + r->payload + 8;
-  r->block_bytes = (size_t)L->n_time * r->C * r->N;
-  r->last_mcnt.assign((size_t)L->n_fids * L->n_xids, -1);
-  r->seg.resize(n_segments);
-  for (Segment& s : r->seg) {
-    // page-locked when a device is present, so corr_push copies it
-    // asynchronously; plain memory otherwise
-    if (cudaMallocHost(&s.data, r->block_bytes) == cudaSuccess) {
-      s.pinned = true;
-    } else {
-      cudaGetLastError();
-      s.data = static_cast<uint8_t*>(aligned_alloc(64, (r->block_bytes + 63) / 64 * 64));
-    }
-    if (!s.data) {
-      free_ring(r);
-      return CORR_ENOMEM;
-    }
-    s.received.assign((size_t)r->per_block, 0);
+// Length and CRC, without the lock.
+int precheck(pk_ring* r, const uint8_t* p, size_t len) {
+  if (len != r->pkt_len) return CORR_EINVAL;
+  if (!(r->flags & PK_F_NO_CRC)) {
+    const uint8_t* t = p + 8 + r->payload;
+    const uint32_t want = (uint32_t)t[4] << 24 | (uint32_t)t[5] << 16 | (uint32_t)t[6] << 8 | t[7];
+    if (t[0] | t[1] | t[2] | t[3] || crc32(p, 8 + r->payload) != want) return CORR_ECORRUPT;
   }
-  *out = r;
   return CORR_OK;
 }
 
-int pk_push(pk_ring* r, const void* packet, size_t len) {
-  if (!r || !packet) return CORR_EINVAL;
-  const uint8_t* p = static_cast<const uint8_t*>(packet);
-  const pk_layout& L = r->L;
-  if (len != r->pkt_len) {
-    std::lock_guard<std::mutex> g(r->mu);
+// Under the lock: count a packet that failed precheck.
+int count_bad(pk_ring* r, int st, size_t len) {
+  if (st == CORR_ECORRUPT)
+    ++r->st.bad_crc;
+  else if (len != r->pkt_len)
     ++r->st.bad_length;
-    return CORR_EINVAL;
-  }
-  if (!(r->flags & PK_F_NO_CRC)) {  // outside the lock: producers may run in parallel
-    const uint8_t* t = p + 8 + r->payload;
-    const uint32_t want = (uint32_t)t[4] << 24 | (uint32_t)t[5] << 16 | (uint32_t)t[6] << 8 | t[7];
-    if (t[0] | t[1] | t[2] | t[3] || crc32(p, 8 + r->payload) != want) {
-      std::lock_guard<std::mutex> g(r->mu);
-      ++r->st.bad_crc;
-      return CORR_ECORRUPT;
-    }
-  }
+  return st;
+}
+
+// Under the lock: ids, MCNT gaps, the block's segment (opening or closing
+// blocks as the ring policy says), and the packet's slot.
+int claim_locked(pk_ring* r, const uint8_t* p, Claim* c) {
+  const pk_layout& L = r->L;
   uint64_t mcnt = 0;
   for (int k = 0; k < 6; ++k) mcnt = mcnt << 8 | p[k];
   const int fid = p[6], xid = p[7];
-  std::unique_lock<std::mutex> g(r->mu);
   if (fid >= L.n_fids || xid >= L.n_xids) {
     ++r->st.bad_id;
     return CORR_EINVAL;
@@ -268,39 +234,135 @@ int pk_push(pk_ring* r, const void* packet, size_t len) {
     ++r->st.duplicate;
     return CORR_ESEQ;
   }
-  // claim the slot, copy without the lock (producers copy in parallel; the
-  // segment cannot be handed out or reused while a copy is in flight)
+  // claimed: the segment cannot be handed out or reused while the copy is
+  // in flight
   got = 1;
   ++s.count;
   ++s.inflight;
   ++r->st.packets;
-  uint8_t* dst = s.data;
-  g.unlock();
+  *c = Claim{p, &s, s.data, slot, fid, xid};
+  return CORR_OK;
+}
+
+// Without the lock: the payload into its place in the block.
+void copy_payload(pk_ring* r, const uint8_t* p, const Claim& c) {
+  const pk_layout& L = r->L;
   const uint8_t* pay = p + 8;
   if (r->flags & PK_F_PACKET_ORDER) {
-    memcpy(dst + (((size_t)slot * L.n_fids + fid) * L.n_xids + xid) * r->payload, pay, r->payload);
+    memcpy(c.dst + (((size_t)c.slot * L.n_fids + c.fid) * L.n_xids + c.xid) * r->payload, pay,
+           r->payload);
   } else {
     for (int tt = 0; tt < 8; ++tt)
       for (int cc = 0; cc < L.n_chans_pkt; ++cc)
-        memcpy(dst + (((size_t)slot * 8 + tt) * r->C + (size_t)xid * L.n_chans_pkt + cc) * r->N +
-                   (size_t)fid * L.n_inputs_pkt,
+        memcpy(c.dst + (((size_t)c.slot * 8 + tt) * r->C + (size_t)c.xid * L.n_chans_pkt + cc) * r->N +
+                   (size_t)c.fid * L.n_inputs_pkt,
                pay + ((size_t)tt * L.n_chans_pkt + cc) * L.n_inputs_pkt, L.n_inputs_pkt);
   }
-  g.lock();
+}
+
+// Under the lock: the copy has landed; the last copy of a complete or given-up
+// block closes it.
+void finish_locked(pk_ring* r, const Claim& c) {
+  Segment& s = *c.seg;
   --s.inflight;
   if (s.inflight == 0 && (s.state == kClosing || (s.state == kOpen && s.count == r->per_block)))
     close_segment(r, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+uint32_t pk_crc32(const void* data, size_t n) {
+  return crc32(static_cast<const uint8_t*>(data), n);
+}
+
+int pk_create(const pk_layout* L, int n_segments, unsigned flags, pk_ring** out) {
+  if (!out) return CORR_EINVAL;
+  *out = nullptr;
+  if (!L || L->n_fids < 1 || L->n_fids > 256 || L->n_xids < 1 || L->n_xids > 256 ||
+      L->n_inputs_pkt < 1 || L->n_chans_pkt < 1 || L->n_time < 8 || L->n_time % 8 ||
+      n_segments < 2 || n_segments > 64 || (flags & ~(PK_F_NO_CRC | PK_F_PACKET_ORDER)))
+    return CORR_EINVAL;
+  pk_ring* r = new (std::nothrow) pk_ring;
+  if (!r) return CORR_ENOMEM;
+  r->L = *L;
+  r->n_seg = n_segments;
+  r->flags = flags;
+  r->C = L->n_xids * L->n_chans_pkt;
+  r->N = L->n_fids * L->n_inputs_pkt;
+  r->slots = L->n_time / 8;
+  r->per_block = r->slots * L->n_fids * L->n_xids;
+  r->payload = (size_t)8 * L->n_chans_pkt * L->n_inputs_pkt;
+  r->pkt_len = 8 + r->payload + 8;
+  r->block_bytes = (size_t)L->n_time * r->C * r->N;
+  r->last_mcnt.assign((size_t)L->n_fids * L->n_xids, -1);
+  r->seg.resize(n_segments);
+  for (Segment& s : r->seg) {
+    // page-locked when a device is present, so corr_push copies it
+    // asynchronously; plain memory otherwise
+    if (cudaMallocHost(&s.data, r->block_bytes) == cudaSuccess) {
+      s.pinned = true;
+    } else {
+      cudaGetLastError();
+      s.data = static_cast<uint8_t*>(aligned_alloc(64, (r->block_bytes + 63) / 64 * 64));
+    }
+    if (!s.data) {
+      free_ring(r);
+      return CORR_ENOMEM;
+    }
+    s.received.assign((size_t)r->per_block, 0);
+  }
+  *out = r;
+  return CORR_OK;
+}
+
+int pk_push(pk_ring* r, const void* packet, size_t len) {
+  if (!r || !packet) return CORR_EINVAL;
+  const uint8_t* p = static_cast<const uint8_t*>(packet);
+  const int pre = precheck(r, p, len);  // outside the lock: producers may run in parallel
+  std::unique_lock<std::mutex> g(r->mu);
+  if (pre != CORR_OK) return count_bad(r, pre, len);
+  Claim c;
+  const int st = claim_locked(r, p, &c);
+  if (st != CORR_OK) return st;
+  g.unlock();
+  copy_payload(r, p, c);
+  g.lock();
+  finish_locked(r, c);
   return CORR_OK;
 }
 
 size_t pk_push_many(pk_ring* r, const void* packets, size_t n, size_t stride, size_t len,
                     int* codes) {
   if (!r || !packets) return 0;
-  const uint8_t* p = static_cast<const uint8_t*>(packets);
-  for (size_t k = 0; k < n; ++k) {
-    const int st = pk_push(r, p + k * stride, len);
-    if (st == CORR_EBUSY) return k;
-    if (codes) codes[k] = st;
+  const uint8_t* base = static_cast<const uint8_t*>(packets);
+  constexpr size_t kBatch = 64;  // packets per lock acquisition
+  int pre[kBatch];
+  Claim claims[kBatch];
+  for (size_t k0 = 0; k0 < n; k0 += kBatch) {
+    const size_t nb = std::min(kBatch, n - k0);
+    for (size_t i = 0; i < nb; ++i) pre[i] = precheck(r, base + (k0 + i) * stride, len);
+    size_t nc = 0, stop = nb;
+    {
+      std::lock_guard<std::mutex> g(r->mu);
+      for (size_t i = 0; i < nb; ++i) {
+        const uint8_t* p = base + (k0 + i) * stride;
+        int st = pre[i] != CORR_OK ? count_bad(r, pre[i], len) : claim_locked(r, p, &claims[nc]);
+        if (st == CORR_EBUSY) {
+          stop = i;
+          break;
+        }
+        if (st == CORR_OK) claims[nc++].src = p;
+        if (codes) codes[k0 + i] = st;
+      }
+    }
+    for (size_t i = 0; i < nc; ++i) copy_payload(r, claims[i].src, claims[i]);
+    {
+      std::lock_guard<std::mutex> g(r->mu);
+      for (size_t i = 0; i < nc; ++i) finish_locked(r, claims[i]);
+    }
+    if (stop < nb) return k0 + stop;
   }
   return n;
 }
