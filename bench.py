@@ -99,6 +99,8 @@ WORKLOADS["fx192"] = dict(
          "spectra, Gaussian ADC noise plus a common delayed sky signal",
     fengine=dict(N=192, C=1024, taps=4, T=8192), fx=True, N=192, C=1024, T=8192)
 METRIC = "X-engine correlator Tops/s at 192 inputs (8 int ops per complex MAC, lower triangle incl. autos)"
+INGEST_METRIC = ("packet ingest GB/s: 8208-byte F-engine packets checked and assembled into "
+                 "X-engine blocks (192 inputs x 1024 channels)")
 FX_METRIC = ("FX correlator Tops/s at 192 inputs: 8-bit ADC samples in, int64 visibilities out "
              "(X-engine ops: 8 per complex MAC, lower triangle incl. autos)")
 FE_METRIC = ("F-engine throughput: 8-bit ADC samples/s channelised (192 inputs, 1024 channels, "
@@ -1015,8 +1017,7 @@ def run_ingest(args, w, world, rank, local):
                                            % (len(sample), len(arr), dt)}
     gbs = pkt_bytes / (ms * 1e-3) / 1e9
     line = {
-        "metric": "packet ingest GB/s: 8208-byte F-engine packets checked and assembled into "
-                  "X-engine blocks (192 inputs x 1024 channels)",
+        "metric": INGEST_METRIC,
         "value": world * gbs, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u8", "data": "synthetic (seeded random 4-bit codes)",
@@ -1035,6 +1036,44 @@ def run_ingest(args, w, world, rank, local):
         "ring": {k: st[k] for k in ("packets", "blocks", "missing", "busy", "bad_crc")},
         "e2e": e2e, "cpu_baseline": cpu, "clocks": None,
     }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_reference_ingest(args, w, world, rank):
+    """The packet oracle's block assembly (plain Python) on a bounded sample of
+    each step's packets: GB/s of packets assembled."""
+    if rank != 0:
+        return 0
+    import numpy as np
+    from oracle import packets as op
+    from paper_1904_07778_gb300 import synth
+    cfg = w["ingest"]
+    F, I, X, K, T = cfg["n_fids"], cfg["n_inputs_pkt"], cfg["n_xids"], cfg["n_chans_pkt"], cfg["T"]
+    block = np.random.default_rng(0).integers(0, 256, (T, X * K, F * I), dtype=np.uint8)
+    arr = synth.packets_array(block, F, I, X, K)
+    budget = max(0.2, min(3.0, args.cpu_seconds, 120.0 / max(1, args.steps + args.warmup)))
+    t0 = time.perf_counter()
+    op.assemble([row.tobytes() for row in arr[:200]], F, I, X, K, T)
+    n = int(max(50, min(len(arr), 200 * budget / max(time.perf_counter() - t0, 1e-6))))
+    sample = [row.tobytes() for row in arr[:n]]
+    for _ in range(args.warmup):
+        op.assemble(sample, F, I, X, K, T)
+    el = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        op.assemble(sample, F, I, X, K, T)
+        el.append(time.perf_counter() - t0)
+    tot = sum(el)
+    v = n * arr.shape[1] * args.steps / tot / 1e9
+    desc = "%d of %d packets of a block per step (Python, one core)" % (n, len(arr))
+    line = {"impl": "reference", "metric": INGEST_METRIC, "value": v, "unit": "GB/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": w["desc"], "sample": desc},
+            "cpu_baseline": {"value": v, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -1230,6 +1269,8 @@ def main():
     world, rank, local = dist_setup()
     if args.impl == "reference" and "fengine" in w:
         rc = run_reference_fe(args, w, world, rank)
+    elif args.impl == "reference" and "ingest" in w:
+        rc = run_reference_ingest(args, w, world, rank)
     elif args.impl == "reference":
         rc = run_reference(args, w, world, rank)
     elif "fx" in w:
