@@ -546,10 +546,14 @@ int corr_set_pipeline(corr_ctx* x, int turn_sms) {
         if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) return CORR_ECUDA;
     if (cudaEventCreateWithFlags(&x->herk_last, cudaEventDisableTiming) != cudaSuccess)
       return CORR_ECUDA;
+  }
+  if (turn_sms > 0 && !x->turned_buf[1]) {  // (also retried after an earlier failure)
     const int byte_rows = x->n_inputs * (x->bits / 4);
     if (cudaMalloc(&x->turned_buf[1], (size_t)x->turned_stride * byte_rows * x->n_chans) !=
-        cudaSuccess)
+        cudaSuccess) {
+      x->turned_buf[1] = nullptr;
       return CORR_ENOMEM;
+    }
   }
   x->pipe_sms = turn_sms;
   x->pipe_k = 0;
