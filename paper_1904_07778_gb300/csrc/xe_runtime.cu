@@ -537,15 +537,18 @@ int corr_set_pipeline(corr_ctx* x, int turn_sms) {
   if (pipe_join(x) != CORR_OK || cudaStreamSynchronize(x->stream) != cudaSuccess ||
       cudaStreamSynchronize(x->copy_stream) != cudaSuccess)
     return CORR_ECUDA;
-  if (turn_sms > 0 && !x->turn_stream) {
-    if (cudaStreamCreateWithFlags(&x->turn_stream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&x->herk_stream, cudaStreamNonBlocking) != cudaSuccess)
-      return CORR_ECUDA;
-    for (int i = 0; i < 2; ++i)
-      for (cudaEvent_t* e : {&x->ev_in[i], &x->turn_done[i], &x->herk_done[i]})
-        if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) return CORR_ECUDA;
-    if (cudaEventCreateWithFlags(&x->herk_last, cudaEventDisableTiming) != cudaSuccess)
-      return CORR_ECUDA;
+  if (turn_sms > 0) {  // create what is missing (a failed earlier call may have left some)
+    for (cudaStream_t* st : {&x->turn_stream, &x->herk_stream})
+      if (!*st && cudaStreamCreateWithFlags(st, cudaStreamNonBlocking) != cudaSuccess) {
+        *st = nullptr;
+        return CORR_ECUDA;
+      }
+    for (cudaEvent_t* e : {&x->ev_in[0], &x->ev_in[1], &x->turn_done[0], &x->turn_done[1],
+                           &x->herk_done[0], &x->herk_done[1], &x->herk_last})
+      if (!*e && cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) {
+        *e = nullptr;
+        return CORR_ECUDA;
+      }
   }
   if (turn_sms > 0 && !x->turned_buf[1]) {  // (also retried after an earlier failure)
     const int byte_rows = x->n_inputs * (x->bits / 4);
