@@ -579,14 +579,20 @@ int corr_dump_async(corr_ctx* x, int64_t* vis, int reset) {
   // stream, so that the caller's stream (and the next block's corner turn)
   // does not wait for it
   cudaStream_t as = acc_stream(x);
-  if (!x->dump_stream) {
-    if (cudaStreamCreateWithFlags(&x->dump_stream, cudaStreamNonBlocking) != cudaSuccess)
+  // first use: create what is missing (a failed earlier call may have left some)
+  if (!x->dump_stream && cudaStreamCreateWithFlags(&x->dump_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    x->dump_stream = nullptr;
+    return CORR_ECUDA;
+  }
+  for (int i = 0; i < 2; ++i)
+    if (!x->acc_free[i] && cudaEventCreateWithFlags(&x->acc_free[i], cudaEventDisableTiming) != cudaSuccess) {
+      x->acc_free[i] = nullptr;
       return CORR_ECUDA;
-    for (int i = 0; i < 2; ++i)
-      if (cudaEventCreateWithFlags(&x->acc_free[i], cudaEventDisableTiming) != cudaSuccess)
-        return CORR_ECUDA;
-    if (cudaMallocHost(&x->h_dump_status, CORR_MAX_ASYNC_DUMPS * sizeof(int)) != cudaSuccess)
-      return CORR_ENOMEM;
+    }
+  if (!x->h_dump_status &&
+      cudaMallocHost(&x->h_dump_status, CORR_MAX_ASYNC_DUMPS * sizeof(int)) != cudaSuccess) {
+    x->h_dump_status = nullptr;
+    return CORR_ENOMEM;
   }
   if (reset && !x->acc_buf[1] && cudaMalloc(&x->acc_buf[1], x->acc_bytes) != cudaSuccess)
     return CORR_ENOMEM;
