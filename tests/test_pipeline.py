@@ -54,6 +54,21 @@ def test_pipelined_pushes_exact(xe, N, C, T, bits, layout, sms):
     assert np.array_equal(got, _want(blocks, N, C, T, bits, layout))
 
 
+@pytest.mark.parametrize("bits", [4, 8])
+def test_pipelined_blocks_longer_than_one_accumulation(xe, bits):
+    """T above the FP32-exact accumulation length: each push issues several
+    cross-multiply launches on the pipelined stream, all into one integration."""
+    N, C = 12, 3
+    T = 70000 if bits == 4 else 40000
+    blocks = [_blk(950 + k + bits, N, C, T, bits) for k in range(2)]
+    with xe.Correlator(N, C, T, bits=bits, layout=1) as cor:
+        cor.set_pipeline(20)
+        for b in blocks:
+            cor.push(b)
+        got = cor.dump()
+    assert np.array_equal(got, _want(blocks, N, C, T, bits, 1))
+
+
 def test_caller_stream_may_overwrite_after_push(xe):
     """One device buffer reused for every block: the next block is written
     into it on the context's stream right after corr_push returns."""
