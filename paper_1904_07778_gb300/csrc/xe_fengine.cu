@@ -60,11 +60,17 @@ __host__ __device__ constexpr int fe_threads(int logm) {
 // one float2 of padding per 16: consecutive runs of 16 (half a warp's
 // 8-byte accesses) stay contiguous, stride-8 runs spread over the banks
 __host__ __device__ constexpr int fe_pad(int n) { return n + (n >> 4); }
+// Twiddles of the radix-8 passes at Ns = 8 and Ns = 64 in shared memory,
+// [k][j-1] for k < Ns: they depend only on lt mod Ns, so the table is small
+// (threads with equal k read the same entry) and frees the registers they
+// would take.
+constexpr int kTwTable = (8 + 64) * 7;
 template <int LOGM>
 constexpr size_t fe_smem_bytes() {
   constexpr int M = 1 << LOGM;
   constexpr int units = fe_threads(LOGM) / (M / 8);
-  return (size_t)fe_nb(LOGM) * units * fe_pad(M) * sizeof(float2) + (size_t)(M / 2) * 2 * kFeGroup;
+  return (size_t)fe_nb(LOGM) * units * fe_pad(M) * sizeof(float2) + (size_t)(M / 2) * 2 * kFeGroup +
+         kTwTable * sizeof(float2);
 }
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
@@ -127,9 +133,9 @@ __device__ __forceinline__ void load_twiddles(float2 (&tw)[7], int lt, int Ns,
 // Each of the M/8 threads of a unit runs 8/R butterflies per transform;
 // loads and stores are separated by a CTA barrier that the NB transforms
 // share.
-template <int M, int R, int NB>
+template <int M, int R, int NB, bool STW = false>
 __device__ __forceinline__ void fft_pass(float2* const (&zs)[NB], int lt, int Ns,
-                                         const float2 (&tw)[7]) {
+                                         const float2 (&tw)[7], const float2* stw = nullptr) {
   constexpr int B = 8 / R;       // butterflies per thread
   constexpr int S = M / R;       // input stride
   float2 v[NB][8];
@@ -141,8 +147,14 @@ __device__ __forceinline__ void fft_pass(float2* const (&zs)[NB], int lt, int Ns
 #pragma unroll
       for (int j = 0; j < R; ++j) v[e][r * R + j] = zs[e][fe_pad(b + j * S)];
       if (Ns > 1) {
+        if constexpr (STW) {  // radix 8, one butterfly per thread: this thread's row of the table
+          const float2* row = stw + (b & (Ns - 1)) * 7;
 #pragma unroll
-        for (int j = 1; j < R; ++j) v[e][r * R + j] = cmul(v[e][r * R + j], tw[r * (R - 1) + j - 1]);
+          for (int j = 1; j < R; ++j) v[e][r * R + j] = cmul(v[e][r * R + j], row[j - 1]);
+        } else {
+#pragma unroll
+          for (int j = 1; j < R; ++j) v[e][r * R + j] = cmul(v[e][r * R + j], tw[r * (R - 1) + j - 1]);
+        }
       }
     }
     if constexpr (R == 8) {
@@ -277,6 +289,7 @@ __global__ void __launch_bounds__(fe_threads(LOGM), fe_min_blocks(LOGM)) fengine
 #pragma unroll
   for (int e = 0; e < kFeNB; ++e) zs[e] = reinterpret_cast<float2*>(fe_smem) + (e * U + u) * PM;
   uint8_t* codes = fe_smem + (size_t)kFeNB * U * PM * sizeof(float2);  // [kFeGroup][C][2]
+  float2* ttab = reinterpret_cast<float2*>(codes + (size_t)C * 2 * kFeGroup);  // [Ns=8 | Ns=64][k][7]
   const int i0 = 2 * blockIdx.y;
   const bool has1 = i0 + 1 < a.n_inputs;
   const int N = a.n_inputs;
@@ -298,9 +311,15 @@ __global__ void __launch_bounds__(fe_threads(LOGM), fe_min_blocks(LOGM)) fengine
       for (int r = 0; r < 8; ++r) hr[q][r] = 0.f;
     }
   }
-  float2 tw[P8 > 1 ? P8 - 1 : 1][7], twl[7];
-#pragma unroll
-  for (int p = 1; p < P8; ++p) load_twiddles<M, 8>(tw[p - 1], lt, 1 << (3 * p), a.w);
+  // passes at Ns = 8 and 64 read the shared table (filled here, first read
+  // after the filter's barrier); a pass at Ns = 512 (M = 4096) keeps registers
+  for (int e = tid; e < kTwTable; e += NT) {
+    const int big = e >= 56, q = big ? e - 56 : e, k = q / 7, j = q % 7 + 1;
+    const int Ns = big ? 64 : 8;
+    if (M >= 8 * Ns) ttab[e] = __ldg(&a.w[j * k * (M / (8 * Ns))]);
+  }
+  float2 tw[1][7], twl[7];
+  if constexpr (P8 >= 4) load_twiddles<M, 8>(tw[0], lt, 512, a.w);
   if constexpr (REM == 2) load_twiddles<M, 4>(twl, lt, 1 << (3 * P8), a.w);
   if constexpr (REM == 1) load_twiddles<M, 2>(twl, lt, 1 << (3 * P8), a.w);
 
@@ -416,8 +435,9 @@ __global__ void __launch_bounds__(fe_threads(LOGM), fe_min_blocks(LOGM)) fengine
     __syncthreads();
     // ---- FFTs of y_2k + j y_2k+1 (natural order out), kFeNB side by side
     fft_pass<M, 8, kFeNB>(zs, lt, 1, twl);  // first pass: no twiddles
-#pragma unroll
-    for (int p = 1; p < P8; ++p) fft_pass<M, 8, kFeNB>(zs, lt, 1 << (3 * p), tw[p - 1]);
+    if constexpr (P8 >= 2) fft_pass<M, 8, kFeNB, true>(zs, lt, 8, twl, ttab);
+    if constexpr (P8 >= 3) fft_pass<M, 8, kFeNB, true>(zs, lt, 64, twl, ttab + 56);
+    if constexpr (P8 >= 4) fft_pass<M, 8, kFeNB>(zs, lt, 512, tw[0]);
     if constexpr (REM == 2) fft_pass<M, 4, kFeNB>(zs, lt, 1 << (3 * P8), twl);
     if constexpr (REM == 1) fft_pass<M, 2, kFeNB>(zs, lt, 1 << (3 * P8), twl);
     // ---- Eq. 2 separation, 18-bit rounding, equaliser
