@@ -274,7 +274,9 @@ __device__ __forceinline__ void fir_tap(float (&y0)[8], float (&y1)[8], const fl
 // with a few spills): measured 10% faster than one CTA at 217 registers.
 __host__ __device__ constexpr int fe_min_blocks(int logm) { return logm <= 11 ? 2 : 1; }
 
-template <int LOGM>
+// POWER: accumulate Eq. 3's power sums (a separate instance, so that the
+// common launch without them keeps those registers free).
+template <int LOGM, bool POWER>
 __global__ void __launch_bounds__(fe_threads(LOGM), fe_min_blocks(LOGM)) fengine_kernel(FeArgs a) {
   constexpr int M = 1 << LOGM, C = M / 2;
   constexpr int TPU = M / 8;                 // threads per FFT unit
@@ -324,7 +326,7 @@ __global__ void __launch_bounds__(fe_threads(LOGM), fe_min_blocks(LOGM)) fengine
   if constexpr (REM == 1) load_twiddles<M, 2>(twl, lt, 1 << (3 * P8), a.w);
 
   float gs[4][2], vsat[4][2];  // gain as g 2^-21 (exact) and its saturation threshold
-  unsigned long long pw[4][2];
+  unsigned long long pw[4][2];  // only used by the POWER instance
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     const int nu = lt + k * TPU;
@@ -463,7 +465,7 @@ __global__ void __launch_bounds__(fe_threads(LOGM), fe_min_blocks(LOGM)) fengine
             if (a.spec) *reinterpret_cast<float2*>(a.spec + ei) = make_float2(X[j][0], X[j][1]);
             if (a.v18) *reinterpret_cast<int2*>(a.v18 + ei) = make_int2(vr, vi);
           }
-          if (a.power) pw[k][j] += (unsigned long long)((long long)vr * vr + (long long)vi * vi);
+          if constexpr (POWER) pw[k][j] += (unsigned long long)((long long)vr * vr + (long long)vi * vi);
           const int qr = equalise_nibble(sr - 12582912.0f, gs[k][j], vsat[k][j]);
           const int qi = equalise_nibble(si - 12582912.0f, gs[k][j], vsat[k][j]);
           codes[(s * C + nu) * 2 + j] = (uint8_t)(a.lo_is_real ? (qi << 4) | qr : (qr << 4) | qi);
@@ -507,7 +509,7 @@ __global__ void __launch_bounds__(fe_threads(LOGM), fe_min_blocks(LOGM)) fengine
       }
     }
   }
-  if (a.power) {
+  if constexpr (POWER) {
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const int nu = lt + k * TPU;
@@ -518,19 +520,24 @@ __global__ void __launch_bounds__(fe_threads(LOGM), fe_min_blocks(LOGM)) fengine
   }
 }
 
-template <int LOGM>
-cudaError_t fe_launch(const FeArgs& a, int n_pairs, cudaStream_t s) {
+template <int LOGM, bool POWER>
+cudaError_t fe_launch_one(const FeArgs& a, int n_pairs, cudaStream_t s) {
   constexpr size_t smem = fe_smem_bytes<LOGM>();
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(fengine_kernel<LOGM>,
+    cudaError_t e = cudaFuncSetAttribute(fengine_kernel<LOGM, POWER>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   const dim3 grid((a.n_spectra + kFeGroup - 1) / kFeGroup, n_pairs);
-  fengine_kernel<LOGM><<<grid, fe_threads(LOGM), smem, s>>>(a);
+  fengine_kernel<LOGM, POWER><<<grid, fe_threads(LOGM), smem, s>>>(a);
   return cudaGetLastError();
+}
+
+template <int LOGM>
+cudaError_t fe_launch(const FeArgs& a, int n_pairs, cudaStream_t s) {
+  return a.power ? fe_launch_one<LOGM, true>(a, n_pairs, s) : fe_launch_one<LOGM, false>(a, n_pairs, s);
 }
 
 bool fe_is_device(const void* p) {

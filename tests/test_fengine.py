@@ -61,7 +61,7 @@ def _bound(adc, C, taps, T, shift):
 
 
 def _run(fe, adc, C, taps, T, shift, gain, layout=2, lo_is_real=False, out_stride=None,
-         adc_stride=None):
+         adc_stride=None, with_power=True):
     N = adc.shape[0]
     dev = torch.device("cuda")
     S = adc_stride or adc.shape[1]
@@ -75,7 +75,7 @@ def _run(fe, adc, C, taps, T, shift, gain, layout=2, lo_is_real=False, out_strid
         out = torch.full((T * C * N,), 0xEE, dtype=torch.uint8, device=dev)
     v18 = torch.zeros((T, C, N, 2), dtype=torch.int32, device=dev)
     spec = torch.zeros((T, C, N, 2), dtype=torch.float32, device=dev)
-    power = torch.zeros((C, N), dtype=torch.int64, device=dev)
+    power = torch.zeros((C, N), dtype=torch.int64, device=dev) if with_power else None
     with fe.FEngine(N, C, taps, shift, lo_is_real=lo_is_real) as f:
         f.set_gains(gain)
         f.channelise(a.view(-1), T, out=out, layout=layout, out_stride=os_, v18=v18, spec=spec,
@@ -88,7 +88,8 @@ def _run(fe, adc, C, taps, T, shift, gain, layout=2, lo_is_real=False, out_strid
     else:
         codes, pad = out.reshape(T, C, N), np.zeros(0)
     return {"codes": codes, "pad": pad, "v18": v18.cpu().numpy().astype(np.int64),
-            "spec": spec.cpu().numpy().astype(np.float64), "power": power.cpu().numpy()}
+            "spec": spec.cpu().numpy().astype(np.float64),
+            "power": power.cpu().numpy() if power is not None else None}
 
 
 def _check(got, adc, C, taps, T, shift, gain, lo_is_real=False):
@@ -103,7 +104,8 @@ def _check(got, adc, C, taps, T, shift, gain, lo_is_real=False):
     v = got["v18"]
     assert np.array_equal(v, np.clip(np.rint(got["spec"]), -(1 << 17), (1 << 17) - 1).astype(np.int64))
     assert np.array_equal(got["codes"], ofe.pack(ofe.equalise(v, gain), lo_is_real))
-    assert np.array_equal(got["power"], ofe.power(v))
+    if got["power"] is not None:
+        assert np.array_equal(got["power"], ofe.power(v))
     # the 18-bit values against the oracle's where they are unique
     vo = ofe.to_fix18(X, shift)
     frac = Xs - np.floor(Xs)
@@ -132,7 +134,8 @@ def test_fengine_parity(fe, N, C, taps, T, shift):
     adc = synth.adc(N * 31 + C, N, (T + taps - 1) * 2 * C, sigma=20.0,
                     tones=[(30.0, 5.25 / (2 * C), 0.4)], common=8.0)
     gain = _gains(rng, C, N)
-    got = _run(fe, adc, C, taps, T, shift, gain)
+    # the kernel has an instance with Eq. 3's power sums and one without
+    got = _run(fe, adc, C, taps, T, shift, gain, with_power=T % 2 == 0)
     assert _check(got, adc, C, taps, T, shift, gain) > 0.99
 
 
