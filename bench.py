@@ -323,11 +323,17 @@ def run_gpu(args, w, world, rank, local):
 
     # one step = per_dump pushes and one dump of the integration into device
     # memory; the dump is overlapped (corr_dump_async) and step k waits for
-    # step k-1's dump, so every dump completes inside the timed region
+    # step k-1's dump, so every dump completes inside the timed region.  By
+    # default each integration is bound to its output buffer (corr_bind), so
+    # the visibilities are written there directly and the dump copies nothing;
+    # --dump-copy integrates in the context's accumulator and copies out.
     def step(k):
+        out = vis if k % 2 == 0 else vis2
+        if not args.dump_copy:
+            cor.bind(out)   # free: its last dump (step k-2) was waited for in step k-1
         for p in range(per_dump):
             cor.push(blocks[(k * per_dump + p) % nalt])
-        cor.dump_async(vis if k % 2 == 0 else vis2, reset=True)
+        cor.dump_async(out, reset=True)
         if k > 0:
             cor.dump_wait()
 
@@ -341,7 +347,7 @@ def run_gpu(args, w, world, rank, local):
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     pipe, sweep = 0, {}
     if args.pipeline_sms != 0 and w["layout"] != 2:
-        cands = [args.pipeline_sms] if args.pipeline_sms > 0 else [0, 32, 40, 44, 48, 52, 56, 60, 64, 72]
+        cands = [args.pipeline_sms] if args.pipeline_sms > 0 else [0, 16, 20, 24, 28, 32, 36, 40, 44, 48, 52, 56, 64]
         for cand in cands:
             cor.set_pipeline(cand)
             for k in range(2):
@@ -505,6 +511,9 @@ def run_gpu(args, w, world, rank, local):
                    "l2": "inputs larger than L2 (%d distinct blocks of %.0f MB cycled)" % (
                        nalt, N * C * T / 1e6),
                    "blocks_per_dump": per_dump,
+                   "dump": ("copied out of the context's accumulator" if args.dump_copy else
+                            "in place: each integration bound to its device output buffer "
+                            "(corr_bind), the dump copies nothing"),
                    "pipeline": {"turn_sms": pipe, "herk_sms": n_sm - pipe,
                                 "sweep_ms_per_step": {str(k_): v for k_, v in sweep.items()},
                                 "note": "turn of block k+1 overlaps the cross-multiply of block k "
@@ -1143,6 +1152,8 @@ def run_fx(args, w, world, rank, local):
         if not x_only:
             f.channelise(blocks[k % 2], T, out=codes)
         if not f_only:
+            if not args.dump_copy:
+                cor.bind(vis)   # integrate in place: the dump copies nothing
             cor.push(codes)
             cor.dump_into(vis, reset=True)
 
@@ -1227,6 +1238,8 @@ def run_fx(args, w, world, rank, local):
         "data": "synthetic (seeded Gaussian ADC noise + common delayed signal, device-generated)",
         "config": {"workload": w["desc"], "n_inputs": N, "n_chans": C, "taps": taps, "n_spectra": T,
                    "l2": "inputs larger than L2 (2 distinct %.1f GB ADC blocks cycled)" % (N * S / 1e9),
+                   "dump": ("copied out of the context's accumulator" if args.dump_copy else
+                            "in place (corr_bind): the dump copies nothing"),
                    "parallelism": "%d GPU" % world},
         "x_real_time": T * M / ADC_RATE / (ms * 1e-3),
         "phase_ms_per_step": {"fengine": ms_f, "xengine_push_dump": ms_x},
@@ -1259,6 +1272,9 @@ def main():
     ap.add_argument("--ingest-layout", choices=["packet", "tci"], default="packet",
                     help="ring blocks in packet order (reordered on the GPU) or [t][c][i]")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--dump-copy", action="store_true",
+                    help="X-engine workloads: copy each dump out of the context's accumulator "
+                         "instead of integrating in place in the output buffer")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--service-requests", type=int, default=0,
                     help="requests of the service workload (default: its configured count)")

@@ -173,6 +173,26 @@ int corr_dump_async(corr_ctx* ctx, int64_t* vis, int reset);
 int corr_dump_wait(corr_ctx* ctx);
 
 /*
+ * corr_bind -- integrate in place in the caller's device buffer.  The next
+ * integration is accumulated directly in vis instead of the context's own
+ * accumulator, so that a dump into vis copies nothing: the long integration
+ * of Sec. 2 lands where the caller reads it.
+ *   vis : int64 [C][N(N+1)/2][2] in device memory (the layout corr_dump
+ *         writes), owned by the caller, who must neither read nor write it
+ *         until the integration's dump (corr_dump, or the corr_dump_wait of
+ *         a corr_dump_async) has returned.  Work queued on the context's
+ *         stream before the first push is ordered before the first write.
+ * Call between integrations: after corr_create, or after a dump with reset
+ * and before the next push.  corr_dump / corr_dump_async into vis itself
+ * then copy nothing (with reset = 0, vis simply goes on accumulating); a dump
+ * into another buffer copies from vis as usual.  The binding ends with the
+ * next dump with reset; corr_restore and corr_normalise act on vis while it
+ * is bound.  CORR_EINVAL for NULL or a host pointer, CORR_ESTATE after a
+ * push into the current integration.
+ */
+int corr_bind(corr_ctx* ctx, int64_t* vis);
+
+/*
  * corr_normalise -- correlation coefficients of the current integration:
  * rho_ij = V_ij / sqrt(V_ii * V_jj) computed in FP64 on the GPU as
  * double(V_ij) / sqrt(double(V_ii) * double(V_jj)); rho = 0 where

@@ -100,9 +100,10 @@ struct corr_ctx {
   bool own_stream = false;
   cudaStream_t copy_stream = nullptr;
   size_t block_bytes = 0;
-  int64_t* acc = nullptr;  // int64 [C][B][2] long integration (= acc_buf[cur])
+  int64_t* acc = nullptr;  // int64 [C][B][2] long integration (acc_buf[cur] or bound)
   size_t acc_bytes = 0;
   bool acc_live = false;   // false: next push stores instead of adding
+  int64_t* bound = nullptr;  // the caller's buffer of this integration (corr_bind)
   // Overlapped dumps (corr_dump_async): a reset switches to the other
   // accumulator while the copy of the finished one runs on dump_stream.
   int64_t* acc_buf[2] = {nullptr, nullptr};
@@ -273,6 +274,13 @@ int guard_acc_write(corr_ctx* x, cudaStream_t writer) {
   if (cudaStreamWaitEvent(writer, x->acc_free[x->cur], 0) != cudaSuccess) return CORR_ECUDA;
   x->read_pending[x->cur] = false;
   return CORR_OK;
+}
+
+// End of an integration: the next one starts in the context's own accumulator.
+void unbind(corr_ctx* x) {
+  if (!x->bound) return;
+  x->bound = nullptr;
+  x->acc = x->acc_buf[x->cur];
 }
 
 // The stream on which the accumulators and the status word are written:
@@ -621,27 +629,32 @@ int corr_dump_async(corr_ctx* x, int64_t* vis, int reset) {
       cudaEventRecord(ready, as) != cudaSuccess ||
       cudaStreamWaitEvent(x->dump_stream, ready, 0) != cudaSuccess)
     st = CORR_ECUDA;
-  if (st == CORR_OK) {
+  // a buffer bound with corr_bind already holds the sums: nothing to copy
+  const bool copy = vis != x->acc;
+  if (st == CORR_OK && copy) {
     cudaEvent_t td = phase_begin(x, x->dump_stream);
-    if (cudaMemcpyAsync(vis, x->acc, x->acc_bytes, cudaMemcpyDefault, x->dump_stream) != cudaSuccess)
+    if (cudaMemcpyAsync(vis, x->acc, x->acc_bytes, cudaMemcpyDefault, x->dump_stream) != cudaSuccess ||
+        cudaEventRecord(x->acc_free[x->cur], x->dump_stream) != cudaSuccess)
       st = CORR_ECUDA;
     else
       phase_end(x, kDump, td, x->dump_stream);
   }
-  if (st == CORR_OK && (cudaEventRecord(x->acc_free[x->cur], x->dump_stream) != cudaSuccess ||
-                        cudaEventRecord(done, x->dump_stream) != cudaSuccess))
-    st = CORR_ECUDA;
+  if (st == CORR_OK && cudaEventRecord(done, x->dump_stream) != cudaSuccess) st = CORR_ECUDA;
   cudaEventDestroy(ready);  // destruction is deferred until the event completes
   if (st != CORR_OK) {
     cudaEventDestroy(done);
     return st;
   }
-  x->read_pending[x->cur] = true;
+  if (copy) x->read_pending[x->cur] = true;
   x->dumps.push_back({done, slot});
   ++x->stats.dumps;
   if (reset) {
-    x->cur ^= 1;
-    x->acc = x->acc_buf[x->cur];
+    if (x->bound) {  // the context's own accumulator was not used
+      unbind(x);
+    } else {
+      x->cur ^= 1;
+      x->acc = x->acc_buf[x->cur];
+    }
     x->acc_live = false;
     x->seq_started = false;
   }
@@ -667,10 +680,12 @@ int corr_dump(corr_ctx* x, int64_t* vis, int reset) {
   if (vis) {
     const bool dev = is_device_ptr(vis);
     if (x->acc_live) {
-      cudaEvent_t td = phase_begin(x, x->stream);
-      if (cudaMemcpyAsync(vis, x->acc, x->acc_bytes, cudaMemcpyDefault, x->stream) != cudaSuccess)
-        return CORR_ECUDA;
-      phase_end(x, kDump, td, x->stream);
+      if (vis != x->acc) {  // a bound buffer already holds the sums
+        cudaEvent_t td = phase_begin(x, x->stream);
+        if (cudaMemcpyAsync(vis, x->acc, x->acc_bytes, cudaMemcpyDefault, x->stream) != cudaSuccess)
+          return CORR_ECUDA;
+        phase_end(x, kDump, td, x->stream);
+      }
     } else if (dev) {
       if (cudaMemsetAsync(vis, 0, x->acc_bytes, x->stream) != cudaSuccess) return CORR_ECUDA;
     } else {
@@ -683,8 +698,18 @@ int corr_dump(corr_ctx* x, int64_t* vis, int reset) {
   if (reset) {
     x->acc_live = false;
     x->seq_started = false;
+    unbind(x);
   }
   return st;
+}
+
+int corr_bind(corr_ctx* x, int64_t* vis) {
+  TraceRange trace_("corr_bind");
+  if (!x || !vis || !is_device_ptr(vis)) return CORR_EINVAL;
+  if (x->acc_live) return CORR_ESTATE;  // blocks already went into this integration
+  x->bound = vis;
+  x->acc = vis;
+  return CORR_OK;
 }
 
 int corr_restore(corr_ctx* x, const int64_t* vis) {

@@ -130,12 +130,29 @@ __global__ void __launch_bounds__(256, 4) turn_kernel(const uint8_t* __restrict_
 
 // The same tiles from a fixed number of CTAs, one per SM, for a corner turn
 // confined to a few SMs while the cross-multiply of the previous block holds
-// the others.  Each of the three 256-thread groups of a CTA walks its own
-// tiles with two 32 KB buffers: the 16-byte cp.async copies of tile i+1 are
-// in flight while tile i is transposed and stored, so about 192 KB of loads
-// stay in flight per SM.  Edge tiles take the byte path synchronously.
-constexpr int kTurnGroups = 3;
+// the others.  Confined to a few SMs, the turn is bound by the bytes each SM
+// keeps in flight, not by HBM: each of the kTurnGroups 256-thread groups of a
+// CTA walks its own tiles through kTurnBufs 32 KB buffers, with the 16-byte
+// cp.async copies of the next kTurnBufs - 1 tiles in flight while one tile is
+// transposed and stored.  Edge tiles take the byte path synchronously.
+#ifndef XE_TURN_GROUPS
+#define XE_TURN_GROUPS 2
+#endif
+#ifndef XE_TURN_BUFS
+#define XE_TURN_BUFS 3
+#endif
+constexpr int kTurnGroups = XE_TURN_GROUPS;
+constexpr int kTurnBufs = XE_TURN_BUFS;
+constexpr int kTurnAhead = kTurnBufs - 1;  // tiles in flight per group
 constexpr int kTileWords = kTT * 32;
+static_assert(kTurnBufs >= 2 && kTurnAhead <= 7, "cp.async.wait_group takes 0..7 here");
+static_assert(kTurnGroups * kTurnBufs * kTileWords * 4 <= 227 * 1024,
+              "the buffers must fit in one CTA's shared memory");
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 
 __device__ __forceinline__ void cp_async16(uint32_t* dst, const uint8_t* src) {
   const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
@@ -161,7 +178,7 @@ __global__ void __launch_bounds__(256 * kTurnGroups, 1)
                         int K, long long os, int vec_ok, int pair_rows) {
   extern __shared__ __align__(16) uint32_t tiles[];
   const int grp = threadIdx.x >> 8, tid = threadIdx.x & 255, bar = 1 + grp;
-  uint32_t* const mine = tiles + 2 * grp * kTileWords;  // this group's two buffers
+  uint32_t* const mine = tiles + kTurnBufs * grp * kTileWords;  // this group's buffers
   const int gx = (T + kTT - 1) / kTT, gy = (K + kTK - 1) / kTK;
   const long long n = (long long)gx * gy * G;
   const long long stride = (long long)gridDim.x * kTurnGroups;
@@ -172,34 +189,38 @@ __global__ void __launch_bounds__(256 * kTurnGroups, 1)
     g = (int)(r / gy);
   };
   auto is_full = [&](int t0, int k0) { return vec_ok && t0 + kTT <= T && k0 + kTK <= K; };
-  long long w = (long long)blockIdx.x * kTurnGroups + grp;
-  if (w < n) {
-    int t0, k0, g;
-    coords(w, t0, k0, g);
-    if (is_full(t0, k0)) tile_prefetch(in, G, K, t0, k0, g, mine, tid);
-  }
-  asm volatile("cp.async.commit_group;" ::: "memory");
-  for (int i = 0; w < n; ++i, w += stride) {
-    const long long wn = w + stride;
-    if (wn < n) {  // the next tile's copies go out before this tile is stored
-      int t1, k1, g1;
-      coords(wn, t1, k1, g1);
-      if (is_full(t1, k1)) tile_prefetch(in, G, K, t1, k1, g1, mine + ((i + 1) & 1) * kTileWords, tid);
+  // copies of full tile w into buffer b; one commit group per tile, empty
+  // for edge tiles and past the end, so that group i is always tile i
+  auto prefetch = [&](long long w, int b) {
+    if (w < n) {
+      int t0, k0, g;
+      coords(w, t0, k0, g);
+      if (is_full(t0, k0)) tile_prefetch(in, G, K, t0, k0, g, mine + b * kTileWords, tid);
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
-    asm volatile("cp.async.wait_group 1;" ::: "memory");  // this tile's copies are in
+  };
+  long long w = (long long)blockIdx.x * kTurnGroups + grp;
+#pragma unroll
+  for (int d = 0; d < kTurnAhead; ++d) prefetch(w + d * stride, d);
+  // tile i sits in buffer i mod kTurnBufs; tile i + kTurnAhead goes into the
+  // buffer of tile i - 1, released by the barrier that ended its iteration
+  for (int b = 0; w < n; w += stride) {
+    const int bn = b == 0 ? kTurnBufs - 1 : b - 1;
+    prefetch(w + kTurnAhead * stride, bn);
+    cp_async_wait<kTurnAhead>();  // the copies of this tile are in
     int t0, k0, g;
     coords(w, t0, k0, g);
-    uint32_t* tile = mine + (i & 1) * kTileWords;
+    uint32_t* tile = mine + b * kTileWords;
     if (is_full(t0, k0)) {
       group_bar(bar);
       turn_tile_store(out, T, K, G, os, pair_rows, t0, k0, g, tile, tid, true);
     } else {
       turn_tile(in, out, T, G, K, os, vec_ok, pair_rows, t0, k0, g, tile, tid, bar);
     }
-    group_bar(bar);  // buffer i & 1 is refilled two tiles on
+    group_bar(bar);
+    if (++b == kTurnBufs) b = 0;
   }
-  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  cp_async_wait<0>();
 }
 
 // ---------------------------------------------------------------- packet turn
@@ -348,7 +369,7 @@ cudaError_t turn_launch(const uint8_t* in, uint8_t* out, int T, int G, int K, lo
                      (reinterpret_cast<uintptr_t>(in) % 32 == 0) &&
                      (reinterpret_cast<uintptr_t>(out) % 32 == 0);
   if (persist_ctas > 0) {
-    constexpr int smem = kTurnGroups * 2 * kTileWords * (int)sizeof(uint32_t);  // 192 KB
+    constexpr int smem = kTurnGroups * kTurnBufs * kTileWords * (int)sizeof(uint32_t);
     static bool attr = false;
     if (!attr) {
       cudaError_t e = cudaFuncSetAttribute(turn_persist_kernel,

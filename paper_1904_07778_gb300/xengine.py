@@ -71,6 +71,8 @@ _lib.corr_dump_async.argtypes = [_P, _P, _I]
 _lib.corr_dump_async.restype = _I
 _lib.corr_dump_wait.argtypes = [_P]
 _lib.corr_dump_wait.restype = _I
+_lib.corr_bind.argtypes = [_P, _P]
+_lib.corr_bind.restype = _I
 EXPORTS += ["corr_dump_async", "corr_dump_wait"]
 CORR_MAX_ASYNC_DUMPS = 4
 _lib.corr_correlate_noalloc.argtypes = [_P, _I, _I, _I, _I, _U, _P, _P, _P]
@@ -207,6 +209,18 @@ class Correlator:
         st = _lib.corr_dump_async(self._ctx, _P(p), 1 if reset else 0)
         if st != CORR_OK:
             raise CorrError(st, "corr_dump_async")
+        return vis
+
+    def bind(self, vis):
+        """Accumulate the next integration in place in the device tensor
+        ``vis`` (corr_bind); a dump into ``vis`` then copies nothing.  The
+        binding ends with the next dump with reset."""
+        p, n = _ptr_and_size(vis)
+        if n != self.n_chans * self.n_baselines * 16:
+            raise ValueError("vis must hold n_chans * n_baselines * 2 int64")
+        st = _lib.corr_bind(self._ctx, _P(p))
+        if st != CORR_OK:
+            raise CorrError(st, "corr_bind")
         return vis
 
     def dump_wait(self, check=True):
