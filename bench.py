@@ -484,21 +484,29 @@ def run_gpu(args, w, world, rank, local):
                 "traffic": kernel_traffic("turn_persist_kernel" if pipe else "turn_kernel", N * C * T)}
         turn["frac"] = turn["achieved"] / turn["peak"]
         kernels.append(turn)
-    for k_ in kernels:  # a kernel confined to part of the GPU, against that part's share
-        k_["frac_of_its_sms"] = k_["frac"] * n_sm / k_["sms"]
+    # a tensor-bound kernel confined to part of the GPU, also against that
+    # part's share of the peak (HBM bandwidth does not divide by SMs)
+    herk["frac_of_its_sms"] = herk["frac"] * n_sm / herk["sms"]
     dom = max(kernels, key=lambda k: k["avg_launch_ms"] * k["launches"])
     roof = {k: dom[k] for k in ("bound", "achieved", "peak", "unit", "frac", "traffic")}
-    for k in ("executed_tflops", "executed_frac", "algorithmic_over_executed"):
+    for k in ("executed_tflops", "executed_frac", "algorithmic_over_executed", "frac_of_its_sms"):
         if k in dom:
             roof[k] = dom[k]
     roof["kernel"] = dom["kernel"]
     roof["sms"] = dom["sms"]
-    roof["frac_of_its_sms"] = dom["frac_of_its_sms"]
     if pipe:
-        roof["note"] = ("runs on %d of %d SMs beside the pipelined corner turn (which holds the "
-                        "other %d); frac is against the whole GPU's peak, frac_of_its_sms against "
-                        "the peak of its SMs; --pipeline-sms 0 runs it alone on every SM"
-                        % (dom["sms"], n_sm, n_sm - dom["sms"]))
+        # the overlapped kernels share HBM: the algorithmic bytes of both
+        # (turn read + write, cross-multiply read of the turned block) per step
+        step_bytes = (2 * N * C * T + N * C * T) * per_dump
+        ms_step_ = ms_max / args.steps
+        roof["step_hbm"] = {"bytes_per_step": step_bytes,
+                            "achieved_gbs": step_bytes / (ms_step_ * 1e-3) / 1e9,
+                            "frac": step_bytes / (ms_step_ * 1e-3) / 1e9 / pk["hbm"]}
+        roof["note"] = ("the corner turn of block k+1 on %d SMs overlaps the cross-multiply of "
+                        "block k on the other %d; frac is against the whole GPU's peak; step_hbm "
+                        "counts both kernels' algorithmic HBM bytes over the step; "
+                        "--pipeline-sms 0 runs each alone on every SM"
+                        % (pipe, n_sm - pipe))
     ms_step = ms_max / args.steps
     value = world * ops_per_step(w) / (ms_step * 1e-3) / 1e12
     line = {

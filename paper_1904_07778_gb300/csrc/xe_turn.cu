@@ -136,10 +136,10 @@ __global__ void __launch_bounds__(256, 4) turn_kernel(const uint8_t* __restrict_
 // cp.async copies of the next kTurnBufs - 1 tiles in flight while one tile is
 // transposed and stored.  Edge tiles take the byte path synchronously.
 #ifndef XE_TURN_GROUPS
-#define XE_TURN_GROUPS 2
+#define XE_TURN_GROUPS 3
 #endif
 #ifndef XE_TURN_BUFS
-#define XE_TURN_BUFS 3
+#define XE_TURN_BUFS 2
 #endif
 constexpr int kTurnGroups = XE_TURN_GROUPS;
 constexpr int kTurnBufs = XE_TURN_BUFS;
@@ -160,16 +160,16 @@ __device__ __forceinline__ void cp_async16(uint32_t* dst, const uint8_t* src) {
 }
 
 // Issue the copies of a full tile into `tile`, the same word placement as
-// the register path of turn_tile: bytes 0..15 of a row's 32-byte piece p go
-// to words 8p .. 8p+3, bytes 16..31 to words 8p+4 .. 8p+7.
+// the register path of turn_tile: bytes 16c .. 16c+15 of a row go to words
+// 4c .. 4c+3.  Consecutive threads take consecutive 16-byte chunks, so each
+// warp instruction covers four whole 128-byte rows (every sector requested
+// once, not half of it by each of two instructions).
 __device__ __forceinline__ void tile_prefetch(const uint8_t* __restrict__ in, int G, int K, int t0,
                                               int k0, int g, uint32_t* tile, int tid) {
 #pragma unroll
-  for (int it = 0; it < 4; ++it) {
-    const int e = it * 256 + tid, r = e >> 2, p = e & 3;
-    const uint8_t* src = in + ((long long)(t0 + r) * G + g) * K + k0 + 32 * p;
-    cp_async16(&tile[tile_word(r, 8 * p)], src);
-    cp_async16(&tile[tile_word(r, 8 * p + 4)], src + 16);
+  for (int it = 0; it < 8; ++it) {
+    const int e = it * 256 + tid, r = e >> 3, c = e & 7;
+    cp_async16(&tile[tile_word(r, 4 * c)], in + ((long long)(t0 + r) * G + g) * K + k0 + 16 * c);
   }
 }
 
