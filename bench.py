@@ -348,7 +348,8 @@ def run_gpu(args, w, world, rank, local):
     pipe, sweep = 0, {}
     if args.pipeline_sms != 0 and w["layout"] != 2:
         cands = [args.pipeline_sms] if args.pipeline_sms > 0 else [0, 16, 20, 24, 28, 32, 36, 40, 44, 48, 52, 56, 64]
-        for cand in cands:
+
+        def try_split(cand):
             cor.set_pipeline(cand)
             for k in range(2):
                 step(k)
@@ -359,6 +360,14 @@ def run_gpu(args, w, world, rank, local):
                 step(k)
             drain()
             sweep[cand] = 1e3 * (time.perf_counter() - t0) / 12
+
+        for cand in cands:
+            try_split(cand)
+        if args.pipeline_sms < 0:  # refine around the best split
+            best = min(sweep, key=sweep.get)
+            for cand in (best - 2, best + 2):
+                if best > 0 and 0 < cand < n_sm and cand not in sweep:
+                    try_split(cand)
         pipe = min(sweep, key=sweep.get)
         cor.set_pipeline(pipe)
 

@@ -179,19 +179,21 @@ __global__ void __launch_bounds__(256 * kTurnGroups, 1)
   extern __shared__ __align__(16) uint32_t tiles[];
   const int grp = threadIdx.x >> 8, tid = threadIdx.x & 255, bar = 1 + grp;
   uint32_t* const mine = tiles + kTurnBufs * grp * kTileWords;  // this group's buffers
-  const int gx = (T + kTT - 1) / kTT, gy = (K + kTK - 1) / kTK;
-  const long long n = (long long)gx * gy * G;
-  const long long stride = (long long)gridDim.x * kTurnGroups;
-  auto coords = [&](long long w, int& t0, int& k0, int& g) {
-    const long long r = w / gx;
-    t0 = (int)(w % gx) * kTT;
-    k0 = (int)(r % gy) * kTK;
-    g = (int)(r / gy);
+  // tile indices in 32 bits (the host keeps their count below 2^31): the
+  // per-tile index arithmetic is a visible share of this kernel's issue slots
+  const unsigned gx = (unsigned)(T + kTT - 1) / kTT, gy = (unsigned)(K + kTK - 1) / kTK;
+  const unsigned n = gx * gy * (unsigned)G;
+  const unsigned stride = gridDim.x * kTurnGroups;
+  auto coords = [&](unsigned w, int& t0, int& k0, int& g) {
+    const unsigned r = w / gx, q = r / gy;
+    t0 = (int)(w - r * gx) * kTT;
+    k0 = (int)(r - q * gy) * kTK;
+    g = (int)q;
   };
   auto is_full = [&](int t0, int k0) { return vec_ok && t0 + kTT <= T && k0 + kTK <= K; };
   // copies of full tile w into buffer b; one commit group per tile, empty
   // for edge tiles and past the end, so that group i is always tile i
-  auto prefetch = [&](long long w, int b) {
+  auto prefetch = [&](unsigned w, int b) {
     if (w < n) {
       int t0, k0, g;
       coords(w, t0, k0, g);
@@ -199,7 +201,7 @@ __global__ void __launch_bounds__(256 * kTurnGroups, 1)
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
   };
-  long long w = (long long)blockIdx.x * kTurnGroups + grp;
+  unsigned w = blockIdx.x * kTurnGroups + grp;
 #pragma unroll
   for (int d = 0; d < kTurnAhead; ++d) prefetch(w + d * stride, d);
   // tile i sits in buffer i mod kTurnBufs; tile i + kTurnAhead goes into the
@@ -368,7 +370,8 @@ cudaError_t turn_launch(const uint8_t* in, uint8_t* out, int T, int G, int K, lo
   const int vec_ok = (K % 32 == 0) && (T % 32 == 0) && (out_stride % 32 == 0) &&
                      (reinterpret_cast<uintptr_t>(in) % 32 == 0) &&
                      (reinterpret_cast<uintptr_t>(out) % 32 == 0);
-  if (persist_ctas > 0) {
+  const long long n_tiles = (long long)((T + kTT - 1) / kTT) * ((K + kTK - 1) / kTK) * G;
+  if (persist_ctas > 0 && n_tiles + (long long)persist_ctas * kTurnGroups * kTurnBufs < (1LL << 31)) {
     constexpr int smem = kTurnGroups * kTurnBufs * kTileWords * (int)sizeof(uint32_t);
     static bool attr = false;
     if (!attr) {
