@@ -927,9 +927,10 @@ def run_ingest(args, w, world, rank, local):
 
     def packets_of(k):
         arr = synth.packets_array(block, F, I, X, K, block_index=k)
-        # producer j takes the packets of F-engines j, j + threads, ...
-        fid = arr[:, 6]
-        return arr, [np.ascontiguousarray(arr[fid % threads == j]) for j in range(threads)]
+        # producer j takes the (Fid, Xid) streams j, j + threads, ... (one
+        # receive queue per thread); each stream stays in MCNT order
+        stream = arr[:, 6].astype(np.int64) * X + arr[:, 7]
+        return arr, [np.ascontiguousarray(arr[stream % threads == j]) for j in range(threads)]
 
     def run(ring, parts, consumer=None):
         import threading
@@ -1284,7 +1285,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--pipeline-sms", type=int, default=-1,
                     help="SMs for the pipelined corner turn (0 = off, -1 = pick by a timed sweep)")
-    ap.add_argument("--ingest-threads", type=int, default=8,
+    ap.add_argument("--ingest-threads", type=int, default=16,
                     help="producer threads of the packet-ingest workload")
     ap.add_argument("--ingest-layout", choices=["packet", "tci"], default="packet",
                     help="ring blocks in packet order (reordered on the GPU) or [t][c][i]")

@@ -24,7 +24,15 @@ namespace {
 // Table-driven IEEE 802.3 CRC-32 (reflected polynomial 0xEDB88320),
 // eight bytes per step with eight tables ("slicing by 8"): table t maps a
 // byte to the CRC contribution of that byte followed by t zero bytes.
-// (Sixteen tables measured no faster.)
+//
+// One slicing chain is a serial dependency (each step needs the previous
+// register), so a long message is cut into four equal segments whose
+// registers advance in lockstep, and the four are joined afterwards.  The
+// raw register (no initial or final inversion) is linear over GF(2):
+// running segment B from register x gives R(B, 0) ^ x * x^(8|B|) mod P, so
+//   R(S0 S1 S2 S3, init) = ((R(S0, init) X ^ R(S1, 0)) X ^ R(S2, 0)) X ^ R(S3, 0)
+// with X = x^(8L) mod P for segments of L bytes; the remaining tail bytes
+// continue from that register.
 uint32_t g_crc[8][256];
 std::once_flag g_crc_once;
 
@@ -39,15 +47,62 @@ void crc_tables() {
       g_crc[t][n] = (g_crc[t - 1][n] >> 8) ^ g_crc[0][g_crc[t - 1][n] & 0xFFu];
 }
 
+inline uint32_t load_le32(const uint8_t* p) {
+  return (uint32_t)p[0] | (uint32_t)p[1] << 8 | (uint32_t)p[2] << 16 | (uint32_t)p[3] << 24;
+}
+
+// One slicing-by-8 step: register c after the 8 bytes at p.
+inline uint32_t crc_step8(uint32_t c, const uint8_t* p) {
+  const uint32_t a = c ^ load_le32(p);
+  return g_crc[7][a & 0xFFu] ^ g_crc[6][(a >> 8) & 0xFFu] ^ g_crc[5][(a >> 16) & 0xFFu] ^
+         g_crc[4][a >> 24] ^ g_crc[3][p[4]] ^ g_crc[2][p[5]] ^ g_crc[1][p[6]] ^ g_crc[0][p[7]];
+}
+
+// a * b mod P for polynomials in the reflected representation (bit 31 is
+// the coefficient of x^0): the schoolbook product, reduced as it goes.
+uint32_t gf2_mulmod(uint32_t a, uint32_t b) {
+  uint32_t p = 0;
+  for (int i = 0; i < 32; ++i, a <<= 1) {
+    if (a & 0x80000000u) p ^= b;
+    b = (b & 1u) ? (b >> 1) ^ 0xEDB88320u : b >> 1;  // b *= x
+  }
+  return p;
+}
+
+// x^(8 n) mod P by square and multiply.
+uint32_t x8n_mod(uint64_t n) {
+  uint32_t r = 0x80000000u, base = 0x00800000u;  // 1 and x^8
+  for (; n; n >>= 1, base = gf2_mulmod(base, base))
+    if (n & 1u) r = gf2_mulmod(r, base);
+  return r;
+}
+
 uint32_t crc32(const uint8_t* p, size_t n) {
   std::call_once(g_crc_once, crc_tables);
   uint32_t c = 0xFFFFFFFFu;
-  for (; n >= 8; p += 8, n -= 8) {
-    const uint32_t a = c ^ ((uint32_t)p[0] | (uint32_t)p[1] << 8 | (uint32_t)p[2] << 16 |
-                            (uint32_t)p[3] << 24);
-    c = g_crc[7][a & 0xFFu] ^ g_crc[6][(a >> 8) & 0xFFu] ^ g_crc[5][(a >> 16) & 0xFFu] ^
-        g_crc[4][a >> 24] ^ g_crc[3][p[4]] ^ g_crc[2][p[5]] ^ g_crc[1][p[6]] ^ g_crc[0][p[7]];
+  if (n >= 256) {
+    const size_t L = (n / 4) & ~(size_t)7;  // bytes per segment, whole steps
+    // every packet of a ring has the same length: keep the last constant
+    thread_local size_t cached_L = 0;
+    thread_local uint32_t cached_X = 0;
+    if (cached_L != L) {
+      cached_X = x8n_mod(L);
+      cached_L = L;
+    }
+    const uint8_t *p1 = p + L, *p2 = p1 + L, *p3 = p2 + L;
+    uint32_t c1 = 0, c2 = 0, c3 = 0;
+    for (size_t k = 0; k < L; k += 8) {
+      c = crc_step8(c, p + k);
+      c1 = crc_step8(c1, p1 + k);
+      c2 = crc_step8(c2, p2 + k);
+      c3 = crc_step8(c3, p3 + k);
+    }
+    const uint32_t X = cached_X;
+    c = gf2_mulmod(gf2_mulmod(gf2_mulmod(c, X) ^ c1, X) ^ c2, X) ^ c3;
+    p += 4 * L;
+    n -= 4 * L;
   }
+  for (; n >= 8; p += 8, n -= 8) c = crc_step8(c, p);
   for (; n; --n, ++p) c = (c >> 8) ^ g_crc[0][(c ^ *p) & 0xFFu];
   return c ^ 0xFFFFFFFFu;
 }

@@ -61,9 +61,13 @@ def _feed(ring, packets):
 
 
 def test_crc_is_the_ieee_crc32():
+    """Short messages take one table chain, from 256 bytes four segments
+    joined by the GF(2) shift: lengths around the switch and every
+    remainder of the segment split."""
     import zlib
     rng = np.random.default_rng(1)
-    for n in (0, 1, 7, 8, 9, 63, 8200, 8208):
+    for n in (0, 1, 7, 8, 9, 63, 255, 256, 257, 263, 264, 287, 288, 289, 1000, 4101, 8191,
+              8200, 8208, 65536 + 37, (1 << 20) + 3):
         d = rng.integers(0, 256, n, dtype=np.uint8).tobytes()
         assert pk_crc32(d) == zlib.crc32(d) & 0xFFFFFFFF
 
