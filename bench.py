@@ -99,6 +99,11 @@ WORKLOADS["fx192"] = dict(
          "spectra, Gaussian ADC noise plus a common delayed sky signal",
     fengine=dict(N=192, C=1024, taps=4, T=8192), fx=True, N=192, C=1024, T=8192)
 METRIC = "X-engine correlator Tops/s at 192 inputs (8 int ops per complex MAC, lower triangle incl. autos)"
+
+
+def xe_metric(n_inputs):
+    """The X-engine metric, named for the workload's input count."""
+    return METRIC.replace("at 192 inputs", "at %d inputs" % n_inputs)
 INGEST_METRIC = ("packet ingest GB/s: 8208-byte F-engine packets checked and assembled into "
                  "X-engine blocks (192 inputs x 1024 channels)")
 FX_METRIC = ("FX correlator Tops/s at 192 inputs: 8-bit ADC samples in, int64 visibilities out "
@@ -284,7 +289,7 @@ def run_reference(args, w, world, rank):
     tot = sum(el)
     v = ops * args.steps / tot / 1e12
     sample = "%d of %d channels x %d of %d spectra per step" % (nch, w["C"], ts, w["T"])
-    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Tops/s", "n_gpus": args.gpus,
+    line = {"impl": "reference", "metric": xe_metric(w["N"]), "value": v, "unit": "Tops/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
             "data": "synthetic",
@@ -385,13 +390,23 @@ def run_gpu(args, w, world, rank, local):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     w0 = time.perf_counter()
     e0.record(stream)
+    # step k returns once dump k-1 is complete, so the host times between
+    # consecutive returns are the device's per-step pace
+    t_ret = []
     for k in range(args.steps):
         step(k)
+        t_ret.append(time.perf_counter())
     drain()             # the last dump is part of the last step
     e1.record(stream)
     torch.cuda.synchronize()
     wall = time.perf_counter() - w0
     clocks = sampler.stop() if sampler else None
+    step_dist = None
+    if len(t_ret) > 2:
+        iv = sorted(1e3 * (b_ - a_) for a_, b_ in zip(t_ret[1:], t_ret[2:]))
+        q = lambda f: iv[min(len(iv) - 1, int(f * len(iv)))]
+        step_dist = {"p10": q(0.1), "p50": q(0.5), "p90": q(0.9), "n": len(iv),
+                     "clock": "host time between consecutive dump completions (steps 2..K)"}
     barrier(world)
     ms = e0.elapsed_time(e1)
     ms_max = max_over_ranks(ms, world)
@@ -519,7 +534,7 @@ def run_gpu(args, w, world, rank, local):
     ms_step = ms_max / args.steps
     value = world * ops_per_step(w) / (ms_step * 1e-3) / 1e12
     line = {
-        "metric": METRIC, "value": value, "unit": "Tops/s", "n_gpus": world, "steps": args.steps,
+        "metric": xe_metric(N), "value": value, "unit": "Tops/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": value / PAPER_TOPS, "dtype": "u8",
         "data": "synthetic (seeded sky+noise model, device-generated)",
@@ -538,6 +553,7 @@ def run_gpu(args, w, world, rank, local):
                                         "one stream"},
                    "parallelism": "replica per GPU, channels independent" if world > 1 else "1 GPU"},
         "x_real_time": world * C * T * per_dump / REAL_TIME_RATE / (ms_step * 1e-3),
+        "step_ms_distribution": step_dist,
         "wall_ms_per_step": 1e3 * wall / args.steps,
         "gpu_launches": (d["herk_launches"] + d["turn_launches"] + d["norm_launches"]),
         "roofline": roof, "kernels": kernels,
