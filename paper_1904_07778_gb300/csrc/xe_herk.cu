@@ -42,7 +42,6 @@ constexpr int kMaxStages = 12;
 constexpr int kMaxBlocks = 2;                 // 128-row operand blocks per stage
 constexpr int kStageT = 128;                  // spectra per stage = one swizzle row
 constexpr int kOpBlockBytes = 128 * kStageT;  // unpacked: 128 rows x 128 spectra
-constexpr int kPkBlockBytes = 64 * kStageT;   // packed: 64 inputs x 128 spectra
 
 struct TaskGeom {
   int nb;       // column blocks (1 or 2) = B slots 0..nb-1
@@ -465,7 +464,10 @@ static_assert(kRingThreads % 128 == 0, "whole warpgroups");
 static_assert(kUnpackWarps * 32 * kRegsUnpack + (kRingThreads - kUnpackWarps * 32) * kRegsOther <=
                   kRingThreads * kRegsLaunch,
               "the register split must fit in the launch allocation");
-constexpr int kMaxSlots = 16;
+#ifndef XE_MAX_SLOTS
+#define XE_MAX_SLOTS 16
+#endif
+constexpr int kMaxSlots = XE_MAX_SLOTS;  // ring slots at most (shared memory sets the count)
 static_assert(kEpiWarps % 4 == 0, "drain warps cover the four tensor-memory lane quarters");
 
 struct RingCtrl {
