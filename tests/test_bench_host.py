@@ -33,3 +33,8 @@ def test_traffic_applies_only_to_its_source_and_shape(tmp_path, monkeypatch):
     src.write_text("kernel changed")
     assert bench.kernel_traffic("k", 20, n_inputs=192) is None      # the source moved on
     assert bench.kernel_traffic("missing", 20) is None
+
+
+def test_xengine_metric_names_the_input_count():
+    assert bench.xe_metric(192) == bench.METRIC
+    assert "at 32 inputs" in bench.xe_metric(32) and "192" not in bench.xe_metric(32)
