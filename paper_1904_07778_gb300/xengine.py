@@ -221,6 +221,7 @@ class Correlator:
         st = _lib.corr_bind(self._ctx, _P(p))
         if st != CORR_OK:
             raise CorrError(st, "corr_bind")
+        self._bound = vis   # kept alive while the library may still write it
         return vis
 
     def dump_wait(self, check=True):
@@ -274,8 +275,9 @@ class Correlator:
 
     def close(self):
         if self._ctx:
-            corr_destroy(self._ctx)
+            corr_destroy(self._ctx)   # waits for the context's work
             self._ctx = None
+        self._bound = None
 
     def __enter__(self):
         return self
