@@ -116,6 +116,11 @@ struct corr_ctx {
     int slot;  // index into h_dump_status
   };
   std::vector<AsyncDump> dumps;  // outstanding, oldest first
+  // dump events reused across dumps: the stream wait on `dump_ready` takes
+  // its record at the call, so the next dump may record it again; a `done`
+  // event returns to the pool once corr_dump_wait has seen it complete
+  cudaEvent_t dump_ready = nullptr;
+  std::vector<cudaEvent_t> done_pool;
   int* h_dump_status = nullptr;  // pinned, kMaxAsyncDumps status snapshots
   uint8_t* stage[2] = {nullptr, nullptr};
   cudaEvent_t stage_free[2] = {nullptr, nullptr};
@@ -245,6 +250,8 @@ void free_ctx(corr_ctx* x) {
   for (int i = 0; i < 2; ++i)
     if (x->acc_free[i]) cudaEventDestroy(x->acc_free[i]);
   for (auto& d : x->dumps) cudaEventDestroy(d.done);
+  for (cudaEvent_t e : x->done_pool) cudaEventDestroy(e);
+  if (x->dump_ready) cudaEventDestroy(x->dump_ready);
   if (x->h_dump_status) cudaFreeHost(x->h_dump_status);
   if (x->dump_stream) cudaStreamDestroy(x->dump_stream);
   for (int i = 0; i < 2; ++i) {
@@ -616,10 +623,15 @@ int corr_dump_async(corr_ctx* x, int64_t* vis, int reset) {
     ++slot;
   // snapshot and clear the status of the blocks in this integration, in
   // stream order, then hand the accumulator to the dump stream
-  cudaEvent_t ready = nullptr, done = nullptr;
-  if (cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) != cudaSuccess) return CORR_ECUDA;
-  if (cudaEventCreateWithFlags(&done, cudaEventDisableTiming) != cudaSuccess) {
-    cudaEventDestroy(ready);
+  if (!x->dump_ready && cudaEventCreateWithFlags(&x->dump_ready, cudaEventDisableTiming) != cudaSuccess) {
+    x->dump_ready = nullptr;
+    return CORR_ECUDA;
+  }
+  cudaEvent_t ready = x->dump_ready, done = nullptr;
+  if (!x->done_pool.empty()) {
+    done = x->done_pool.back();
+    x->done_pool.pop_back();
+  } else if (cudaEventCreateWithFlags(&done, cudaEventDisableTiming) != cudaSuccess) {
     return CORR_ECUDA;
   }
   int st = CORR_OK;
@@ -640,9 +652,8 @@ int corr_dump_async(corr_ctx* x, int64_t* vis, int reset) {
       phase_end(x, kDump, td, x->dump_stream);
   }
   if (st == CORR_OK && cudaEventRecord(done, x->dump_stream) != cudaSuccess) st = CORR_ECUDA;
-  cudaEventDestroy(ready);  // destruction is deferred until the event completes
   if (st != CORR_OK) {
-    cudaEventDestroy(done);
+    cudaEventDestroy(done);  // its last record may still be pending: not reused
     return st;
   }
   if (copy) x->read_pending[x->cur] = true;
@@ -668,8 +679,11 @@ int corr_dump_wait(corr_ctx* x) {
   const corr_ctx::AsyncDump d = x->dumps.front();
   x->dumps.erase(x->dumps.begin());
   const cudaError_t e = cudaEventSynchronize(d.done);
-  cudaEventDestroy(d.done);
-  if (e != cudaSuccess) return CORR_ECUDA;
+  if (e != cudaSuccess) {
+    cudaEventDestroy(d.done);
+    return CORR_ECUDA;
+  }
+  x->done_pool.push_back(d.done);
   return status_code(x->h_dump_status[d.slot]);
 }
 
