@@ -139,3 +139,40 @@ def test_cylinder_slice_pipelined(xe):
     chans = list(range(0, C, 11))
     want = _want([b.cpu().numpy() for b in blocks], N, C, T, 4, 1, chans=chans)
     assert np.array_equal(got[chans], want)
+
+
+def test_cylinder_full_size_bench_configuration(xe):
+    """192 inputs x 1024 channels x 8192 spectra in the launch configuration
+    the benchmark times: corner turn on 42 SMs beside the cross-multiply, two
+    device blocks cycled, each integration bound to its own device buffer and
+    dumped asynchronously.  Sampled channels of every integration against the
+    oracle; every channel against the total-power invariant."""
+    N, C, T = 192, 1024, 8192
+    nb = N * (N + 1) // 2
+    blocks = [synth.block_device("sky", 60 + k, N, C, T, 1, torch.device("cuda")) for k in range(2)]
+    outs = [torch.empty((C, nb, 2), dtype=torch.int64, device="cuda") for _ in range(2)]
+    order = [0, 1, 0]                        # integration k holds block order[k]
+    kept = []
+    with xe.Correlator(N, C, T, bits=4, layout=1) as cor:
+        cor.set_pipeline(42)
+        for k, b in enumerate(order):
+            out = outs[k % 2]
+            if k >= 2:
+                assert cor.dump_wait() == xe.CORR_OK
+                kept.append(outs[(k - 2) % 2].cpu().numpy())   # read before rebinding
+            cor.bind(out)
+            cor.push(blocks[b])
+            cor.dump_async(out, reset=True)
+        while len(kept) < len(order):
+            assert cor.dump_wait() == xe.CORR_OK
+            kept.append(outs[len(kept) % 2].cpu().numpy())
+    ii = np.array([i * (i + 1) // 2 + i for i in range(N)])
+    chans = np.concatenate([[0, C - 1], np.random.default_rng(9).choice(C, size=6, replace=False)])
+    for k, b in enumerate(order):
+        blk = blocks[b].cpu().numpy()
+        assert np.array_equal(kept[k][chans], oracle.correlate(blk, N, C, T, layout=1, chans=chans))
+        x = blocks[b].view(T, N, C)
+        hi = ((x >> 4).to(torch.int32) ^ 8) - 8
+        lo = ((x & 15).to(torch.int32) ^ 8) - 8
+        p = (hi * hi + lo * lo).sum(dim=(0, 1)).cpu().numpy()
+        assert np.array_equal(kept[k][:, ii, 0].sum(axis=1), p)
