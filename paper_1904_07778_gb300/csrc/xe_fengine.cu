@@ -455,6 +455,7 @@ __global__ void __launch_bounds__(fe_threads(LOGM), fe_min_blocks(LOGM)) fengine
         const float2 zp = z[fe_pad(nu)], zm = z[fe_pad((M - nu) & (M - 1))];
         const float X[2][2] = {{(zp.x + zm.x) * a.scale, (zp.y - zm.y) * a.scale},
                                {(zp.y + zm.y) * a.scale, (zm.x - zp.x) * a.scale}};
+        uint32_t pair = 0;  // the codes of inputs i0 and i0 + 1: one 16-bit store
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
           if (j == 1 && !has1) break;
@@ -468,8 +469,9 @@ __global__ void __launch_bounds__(fe_threads(LOGM), fe_min_blocks(LOGM)) fengine
           if constexpr (POWER) pw[k][j] += (unsigned long long)((long long)vr * vr + (long long)vi * vi);
           const int qr = equalise_nibble(sr - 12582912.0f, gs[k][j], vsat[k][j]);
           const int qi = equalise_nibble(si - 12582912.0f, gs[k][j], vsat[k][j]);
-          codes[(s * C + nu) * 2 + j] = (uint8_t)(a.lo_is_real ? (qi << 4) | qr : (qr << 4) | qi);
+          pair |= (uint32_t)(a.lo_is_real ? (qi << 4) | qr : (qr << 4) | qi) << (8 * j);
         }
+        *reinterpret_cast<uint16_t*>(codes + (s * C + nu) * 2) = (uint16_t)pair;
       }
     }
     __syncthreads();
