@@ -150,3 +150,25 @@ def test_bind_rejections(xe):
         again = cor.bind(_dev(N, C))
         cor.push(synth.random_bytes(2, N * C * T))
         cor.dump_into(again, reset=True)
+
+
+def _blk8(seed, N, C, T):
+    rng = np.random.default_rng(seed)
+    return rng.integers(-127, 128, 2 * N * C * T, dtype=np.int16).astype(np.int8).view(np.uint8)
+
+
+@pytest.mark.parametrize("bits,N,C,T,layout", [(8, 48, 6, 512, 1), (8, 30, 4, 256, 0),
+                                                (4, 12, 3, 70000, 1), (8, 12, 3, 40000, 1)])
+def test_bound_eight_bit_and_multi_launch(xe, bits, N, C, T, layout):
+    """8-bit samples (the byte split) and pushes longer than one exact FP32
+    accumulation (several cross-multiply launches per push, the first storing
+    into the bound buffer and the rest adding)."""
+    gen = _blk8 if bits == 8 else (lambda s, n, c, t: synth.random_bytes(s, n * c * t))
+    blocks = [gen(40 + k, N, C, T) for k in range(2)]
+    buf = _dev(N, C, fill=77)
+    with xe.Correlator(N, C, T, bits=bits, layout=layout) as cor:
+        cor.bind(buf)
+        for b in blocks:
+            cor.push(b)
+        cor.dump_into(buf, reset=True)
+    assert np.array_equal(buf.cpu().numpy(), _want(blocks, N, C, T, layout, bits=bits))

@@ -72,6 +72,19 @@ def test_crc_is_the_ieee_crc32():
         assert pk_crc32(d) == zlib.crc32(d) & 0xFFFFFFFF
 
 
+def test_crc_random_lengths_and_offsets():
+    """Any length and any start address (the four segments and the tail
+    step through unaligned bytes)."""
+    import zlib
+    rng = np.random.default_rng(2)
+    buf = rng.integers(0, 256, 40000, dtype=np.uint8).tobytes()
+    for _ in range(60):
+        off = int(rng.integers(0, 16))
+        n = int(rng.integers(0, 30000))
+        d = buf[off:off + n]
+        assert pk_crc32(d) == zlib.crc32(d) & 0xFFFFFFFF, (off, n)
+
+
 def test_clean_stream_round_trips():
     blocks = _blocks(4)
     with _ring() as ring:
