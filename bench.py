@@ -569,11 +569,13 @@ def run_gpu(args, w, world, rank, local):
 
 
 def run_batch(args, w, world, rank, local):
-    """Batched mixed arrays: the graph-replayed single launch vs one launch per array."""
+    """Batched mixed arrays: the graph-replayed single launch, the graph with
+    the largest array turned in channel ranges beside the cross-multiply, and
+    one launch per array."""
     import torch
     from paper_1904_07778_gb300 import build, synth
     build.build()
-    from paper_1904_07778_gb300.xengine import Batch
+    from paper_1904_07778_gb300.xengine import Batch, CorrError
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -604,11 +606,30 @@ def run_batch(args, w, world, rank, local):
     if sampler:
         sampler.start()
         time.sleep(0.3)
-    ms_graph = timed(b.run, args.steps)
+    ms_single = timed(b.run, args.steps)
+    info_single = b.info()
     ms_plain = timed(b.run_plain, args.steps)
+    # pipelined graph: a short timed sweep of the split, then the best one
+    sweep = {}
+    for sms in (32, 40, 48, 56):
+        for ch in (4, 8):
+            try:
+                b.set_pipeline(sms, ch)
+            except CorrError:
+                continue
+            sweep["%d/%d" % (sms, ch)] = timed(b.run, max(10, args.steps // 20))
+    ms_pipe, pipe_cfg, info_pipe = None, None, None
+    if sweep:
+        pipe_cfg = min(sweep, key=sweep.get)
+        sms, ch = (int(x) for x in pipe_cfg.split("/"))
+        b.set_pipeline(sms, ch)
+        ms_pipe = timed(b.run, args.steps)
+        info_pipe = b.info()
     clocks = sampler.stop() if sampler else None
-    info = b.info()
     b.close()
+    piped = ms_pipe is not None and ms_pipe < ms_single
+    ms_graph = ms_pipe if piped else ms_single
+    info = info_pipe if piped else info_single
     if rank != 0:
         return 0
     value = world * ops / (ms_graph * 1e-3) / 1e12
@@ -620,6 +641,13 @@ def run_batch(args, w, world, rank, local):
         "data": "synthetic (seeded i.i.d. Gaussian, device-generated)",
         "config": {"workload": w["desc"], "arrays": w["batch"], "bits": 4, "layout": "tci",
                    "l2": "inputs larger than L2 (13 GB per run)"},
+        "graph_form": ("pipelined: the largest array turned in channel ranges on %s (turn SMs / "
+                       "ranges) beside the cross-multiply" % pipe_cfg) if piped else "single launch",
+        "single_launch_graph": {"value": world * ops / (ms_single * 1e-3) / 1e12,
+                                "ms_per_step": ms_single, "schedule": info_single},
+        "pipelined_graph": None if ms_pipe is None else {
+            "value": world * ops / (ms_pipe * 1e-3) / 1e12, "ms_per_step": ms_pipe,
+            "turn_sms_ranges": pipe_cfg, "sweep_ms_per_step": sweep},
         "plain_one_launch_per_array": {"value": world * ops / (ms_plain * 1e-3) / 1e12,
                                        "ms_per_step": ms_plain},
         "batched_over_plain": ms_plain / ms_graph,

@@ -368,6 +368,19 @@ int corr_batch_run(corr_batch* b);
  * Asynchronous. */
 int corr_batch_run_plain(corr_batch* b);
 
+/*
+ * corr_batch_set_pipeline -- overlap the corner turn with the cross-multiply
+ * inside each run.  The array with the most bytes to turn (4-bit, [t][c][i]
+ * or [t][i][c], more than 32 inputs) is turned in n_chunks channel ranges on
+ * turn_sms SMs of a second stream, while the other SMs cross-multiply the
+ * other arrays and then each range as soon as it is turned.  The graph that
+ * corr_batch_run replays is re-captured in that form (a few launches per
+ * run instead of one).  turn_sms = 0 restores the single-launch form.
+ * Waits for the batch's stream.  CORR_EINVAL for turn_sms outside
+ * 0 .. SMs - 1, n_chunks < 1, or no array that can be split so.
+ */
+int corr_batch_set_pipeline(corr_batch* b, int turn_sms, int n_chunks);
+
 /* Wait for the batch's stream; returns a pending device status (CORR_ERANGE,
  * CORR_ETIMEDOUT) once, else CORR_OK. */
 int corr_batch_sync(corr_batch* b);

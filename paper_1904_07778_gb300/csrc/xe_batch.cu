@@ -47,6 +47,15 @@ struct corr_batch {
   cudaGraphExec_t exec = nullptr;
   int* d_status = nullptr;
   int* h_status = nullptr;
+  // pipelined runs (corr_batch_set_pipeline): array pipe_inst is turned in
+  // channel ranges pipe_c[j] .. pipe_c[j+1] on pipe_sms SMs of turn_stream;
+  // task list 0 holds the other arrays' tasks, list 1 + j range j's
+  int pipe_sms = 0, pipe_inst = -1;
+  std::vector<int> pipe_c;
+  std::vector<HerkTask*> d_pipe_tasks;
+  std::vector<int> n_pipe_tasks, max_nblk_pipe;
+  cudaStream_t turn_stream = nullptr;
+  std::vector<cudaEvent_t> pipe_ev;  // [0] fork, [1 + j] range j turned
 };
 
 namespace {
@@ -67,6 +76,9 @@ void free_batch(corr_batch* b) {
   for (auto p : b->turned) cudaFree(p);
   for (auto p : b->acc) cudaFree(p);
   for (auto p : b->d_tasks_one) cudaFree(p);
+  for (auto p : b->d_pipe_tasks) cudaFree(p);
+  for (auto e : b->pipe_ev) cudaEventDestroy(e);
+  if (b->turn_stream) cudaStreamDestroy(b->turn_stream);
   cudaFree(b->d_insts);
   cudaFree(b->d_tmaps);
   cudaFree(b->d_tasks);
@@ -165,6 +177,47 @@ cudaError_t enqueue_batched(corr_batch* b) {
   return herk4_launch(batched_args(b), nullptr, b->n_tasks, b->stream);
 }
 
+// Enqueue one pipelined run: the split array's ranges are turned one after
+// another on pipe_sms persistent CTAs of the turn stream; the batch's stream
+// turns the other arrays, cross-multiplies them, and then each range once its
+// turn is done, every launch capped at the SMs the turn leaves free (so that
+// no kernel ever waits for another to start).
+cudaError_t enqueue_pipelined(corr_batch* b) {
+  const int k = b->pipe_inst, nch = (int)b->pipe_c.size() - 1;
+  const corr_shape& sh = b->shapes[k];
+  cudaError_t e;
+  if ((e = cudaEventRecord(b->pipe_ev[0], b->stream)) != cudaSuccess ||
+      (e = cudaStreamWaitEvent(b->turn_stream, b->pipe_ev[0], 0)) != cudaSuccess)
+    return e;
+  for (int j = 0; j < nch; ++j) {
+    if ((e = turn_rows_chans(b->input[k], b->turned[k], sh.layout, sh.bits, sh.n_inputs,
+                             sh.n_chans, sh.n_time, b->pipe_c[j], b->pipe_c[j + 1],
+                             b->insts[k].row_stride, b->turn_stream, b->pipe_sms)) != cudaSuccess ||
+        (e = cudaEventRecord(b->pipe_ev[1 + j], b->turn_stream)) != cudaSuccess)
+      return e;
+  }
+  for (int q = 0; q < b->n; ++q) {
+    const corr_shape& s = b->shapes[q];
+    if (q == k || !needs_turn(s.layout, s.bits)) continue;
+    if ((e = turn_rows(b->input[q], b->turned[q], s.layout, s.bits, s.n_inputs, s.n_chans,
+                       s.n_time, b->insts[q].row_stride, b->stream)) != cudaSuccess)
+      return e;
+  }
+  HerkArgs a = batched_args(b);
+  a.cta_first = nullptr;
+  a.grid = sm_count() - b->pipe_sms;
+  for (int j = 0; j <= nch; ++j) {
+    // the last wait also joins the turn stream back into the batch's stream
+    if (j > 0 && (e = cudaStreamWaitEvent(b->stream, b->pipe_ev[j], 0)) != cudaSuccess) return e;
+    if (b->n_pipe_tasks[j] == 0) continue;
+    a.tasks = b->d_pipe_tasks[j];
+    a.n_tasks = b->n_pipe_tasks[j];
+    a.max_nblk = b->max_nblk_pipe[j];
+    if ((e = herk4_launch(a, nullptr, a.n_tasks, b->stream)) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 int capture_graph(corr_batch* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
@@ -172,7 +225,7 @@ int capture_graph(corr_batch* b) {
   b->graph = nullptr;
   if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
     return CORR_ECUDA;
-  cudaError_t e = enqueue_batched(b);
+  cudaError_t e = b->pipe_sms > 0 ? enqueue_pipelined(b) : enqueue_batched(b);
   cudaGraph_t g = nullptr;
   cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
   if (e != cudaSuccess || e2 != cudaSuccess || !g) {
@@ -483,6 +536,95 @@ int corr_batch_run_plain(corr_batch* b) {
   return CORR_OK;
 }
 
+int corr_batch_set_pipeline(corr_batch* b, int turn_sms, int n_chunks) {
+  TraceRange trace_("corr_batch_set_pipeline");
+  if (!b || turn_sms < 0 || turn_sms >= sm_count() || n_chunks < 1) return CORR_EINVAL;
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return CORR_ECUDA;
+  if (turn_sms == 0) {
+    b->pipe_sms = 0;
+    return capture_graph(b);
+  }
+  // the array with the most bytes to turn that can be cut by channels
+  int k = -1;
+  double most = 0.0;
+  for (int q = 0; q < b->n; ++q) {
+    const corr_shape& s = b->shapes[q];
+    const double bytes = (double)s.n_inputs * s.n_chans * s.n_time;
+    if (s.bits == 4 && (s.layout == CORR_L_TCI || s.layout == CORR_L_TIC) && 2 * s.n_inputs > 64 &&
+        bytes > most) {
+      most = bytes;
+      k = q;
+    }
+  }
+  if (k < 0) return CORR_EINVAL;
+  const corr_shape& sh = b->shapes[k];
+  // range starts on whole 128-byte tiles of the turned rows where possible
+  int g = 128, n = sh.n_inputs;
+  while (n % 2 == 0 && g > 1 && (sh.layout == CORR_L_TCI)) {
+    n /= 2;
+    g /= 2;
+  }
+  const int unit = sh.layout == CORR_L_TIC ? 128 : g;  // channels per step of a range start
+  const int nch = std::max(1, std::min(n_chunks, sh.n_chans / unit));
+  std::vector<int> c(1, 0);
+  for (int j = 1; j < nch; ++j) {
+    const int cj = (int)((long long)j * sh.n_chans / nch) / unit * unit;
+    if (cj > c.back()) c.push_back(cj);
+  }
+  c.push_back(sh.n_chans);
+  // task lists: the other arrays, then each range of the split array
+  std::vector<std::vector<HerkTask>> lists(c.size());
+  for (int q = 0; q < b->n; ++q) {
+    const corr_shape& s = b->shapes[q];
+    int rpc = 0;
+    for (HerkTask x : plan_tasks(s.n_inputs * (s.bits / 4), s.n_chans, &rpc)) {
+      x.inst = q;
+      int li = 0;
+      if (q == k) {
+        li = 1;
+        while (li + 1 < (int)c.size() && x.chan0 >= c[li]) ++li;
+      }
+      lists[li].push_back(x);
+    }
+  }
+  for (auto p : b->d_pipe_tasks) cudaFree(p);
+  b->d_pipe_tasks.assign(lists.size(), nullptr);
+  b->n_pipe_tasks.assign(lists.size(), 0);
+  b->max_nblk_pipe.assign(lists.size(), 1);
+  b->pipe_sms = 0;  // until everything below is in place
+  for (size_t j = 0; j < lists.size(); ++j) {
+    b->n_pipe_tasks[j] = (int)lists[j].size();
+    if (lists[j].empty()) continue;
+    b->max_nblk_pipe[j] = tasks_max_nblk(lists[j]);
+    if (cudaMalloc(&b->d_pipe_tasks[j], sizeof(HerkTask) * lists[j].size()) != cudaSuccess)
+      return CORR_ENOMEM;
+    if (cudaMemcpy(b->d_pipe_tasks[j], lists[j].data(), sizeof(HerkTask) * lists[j].size(),
+                   cudaMemcpyHostToDevice) != cudaSuccess)
+      return CORR_ECUDA;
+  }
+  if (!b->turn_stream && cudaStreamCreateWithFlags(&b->turn_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    b->turn_stream = nullptr;
+    return CORR_ECUDA;
+  }
+  while (b->pipe_ev.size() < c.size()) {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return CORR_ECUDA;
+    b->pipe_ev.push_back(e);
+  }
+  b->pipe_inst = k;
+  b->pipe_c = c;
+  b->pipe_sms = turn_sms;
+  // set every launch attribute outside the capture, then capture one run
+  if (enqueue_pipelined(b) != cudaSuccess || cudaStreamSynchronize(b->stream) != cudaSuccess ||
+      cudaMemset(b->d_status, 0, sizeof(int)) != cudaSuccess) {
+    b->pipe_sms = 0;
+    cudaGetLastError();
+    capture_graph(b);
+    return CORR_ECUDA;
+  }
+  return capture_graph(b);
+}
+
 int corr_batch_sync(corr_batch* b) {
   if (!b) return CORR_EINVAL;
   return take_status(b);
@@ -495,6 +637,13 @@ int corr_batch_info_get(corr_batch* b, corr_batch_info* out) {
   out->n_ctas = b->n_ctas;
   int launches = 1;
   for (const corr_shape& s : b->shapes) launches += needs_turn(s.layout, s.bits) ? 1 : 0;
+  if (b->pipe_sms > 0) {  // the split array: one turn and one cross-multiply per range
+    const int nch = (int)b->pipe_c.size() - 1;
+    launches = 2 * nch;
+    for (int q = 0; q < b->n; ++q)
+      if (q != b->pipe_inst && needs_turn(b->shapes[q].layout, b->shapes[q].bits)) ++launches;
+    if (b->n_pipe_tasks[0] > 0) ++launches;
+  }
   out->launches_per_run = launches;
   for (int i = 0; i < 3; ++i) out->tuned_ms[i] = b->tuned_ms[i];
   out->tune_source = b->tune_source;

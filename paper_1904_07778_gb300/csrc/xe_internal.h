@@ -115,6 +115,11 @@ bool make_sample_tmap(CUtensorMap* m, const uint8_t* x, int n_time, long long ro
 // SM (for overlapping it with a cross-multiply on the remaining SMs).
 cudaError_t turn_launch(const uint8_t* in, uint8_t* out, int T, int G, int K, long long out_stride,
                         cudaStream_t s, bool pair_rows = false, int persist_ctas = 0);
+// The same with input rows in_stride >= K bytes apart: a range of K bytes cut
+// out of each row of a wider block.
+cudaError_t turn_launch_strided(const uint8_t* in, uint8_t* out, int T, int G, int K,
+                                long long in_stride, long long out_stride, cudaStream_t s,
+                                bool pair_rows = false, int persist_ctas = 0);
 
 // A block in packet order, [slot][fid][xid][8][chans_pkt][inputs_pkt] bytes,
 // becomes [c][i][t] rows of out_stride bytes (c = xid chans_pkt + cc,
@@ -137,6 +142,11 @@ bool turn_can_persist(int layout, int bits);
 cudaError_t turn_rows(const uint8_t* in, uint8_t* out, int layout, int bits, int n_inputs,
                       int n_chans, int n_time, long long out_stride, cudaStream_t s,
                       int persist_ctas = 0);
+// turn_rows for channels c0 .. c1-1 only (4-bit [t][c][i] or [t][i][c]):
+// their rows of the whole block's output.  cudaErrorInvalidValue otherwise.
+cudaError_t turn_rows_chans(const uint8_t* in, uint8_t* out, int layout, int bits, int n_inputs,
+                            int n_chans, int n_time, int c0, int c1, long long out_stride,
+                            cudaStream_t s, int persist_ctas = 0);
 
 // Tasks of one array (see HerkTask): rows_per_chan is set for stacked
 // arrays.  With singles, every task has one column block (128 x 128).

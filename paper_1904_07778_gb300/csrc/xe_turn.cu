@@ -77,9 +77,11 @@ __device__ __forceinline__ void turn_tile_store(uint8_t* __restrict__ out, int T
 
 
 // One tile: 256 threads (tid 0..255) move spectra t0 .. t0+255 of byte rows
-// k0 .. k0+127 of group g through `tile`, meeting at barrier `bar`.
+// k0 .. k0+127 of group g through `tile`, meeting at barrier `bar`.  Input
+// row (t, g) starts at in + (t G + g) ks: ks = K, or more for a range of
+// rows cut from a wider block.
 __device__ __forceinline__ void turn_tile(const uint8_t* __restrict__ in, uint8_t* __restrict__ out,
-                                          int T, int G, int K, long long os, int vec_ok,
+                                          int T, int G, int K, long long ks, long long os, int vec_ok,
                                           int pair_rows, int t0, int k0, int g, uint32_t* tile,
                                           int tid, int bar) {
   const bool full = vec_ok && t0 + kTT <= T && k0 + kTK <= K;
@@ -90,7 +92,7 @@ __device__ __forceinline__ void turn_tile(const uint8_t* __restrict__ in, uint8_
 #pragma unroll
     for (int it = 0; it < 4; ++it) {
       const int e = it * 256 + tid, r = e >> 2, p = e & 3;
-      ld32B(in + ((long long)(t0 + r) * G + g) * K + k0 + 32 * p, v[it]);
+      ld32B(in + ((long long)(t0 + r) * G + g) * ks + k0 + 32 * p, v[it]);
     }
 #pragma unroll
     for (int it = 0; it < 4; ++it) {
@@ -108,7 +110,7 @@ __device__ __forceinline__ void turn_tile(const uint8_t* __restrict__ in, uint8_
       const int r = e >> 5, w = e & 31;
       uint32_t x = 0;
       if (t0 + r < T) {
-        const long long off = ((long long)(t0 + r) * G + g) * K + k0 + 4 * w;
+        const long long off = ((long long)(t0 + r) * G + g) * ks + k0 + 4 * w;
         for (int b = 0; b < 4; ++b)
           if (k0 + 4 * w + b < K) x |= (uint32_t)in[off + b] << (8 * b);
       }
@@ -121,10 +123,10 @@ __device__ __forceinline__ void turn_tile(const uint8_t* __restrict__ in, uint8_
 
 __global__ void __launch_bounds__(256, 4) turn_kernel(const uint8_t* __restrict__ in,
                                                       uint8_t* __restrict__ out, int T, int G,
-                                                      int K, long long os, int vec_ok,
-                                                      int pair_rows) {
+                                                      int K, long long ks, long long os,
+                                                      int vec_ok, int pair_rows) {
   __shared__ __align__(16) uint32_t tile[kTT * 32];
-  turn_tile(in, out, T, G, K, os, vec_ok, pair_rows, blockIdx.x * kTT, blockIdx.y * kTK,
+  turn_tile(in, out, T, G, K, ks, os, vec_ok, pair_rows, blockIdx.x * kTT, blockIdx.y * kTK,
             blockIdx.z, tile, threadIdx.x, 0);
 }
 
@@ -164,18 +166,18 @@ __device__ __forceinline__ void cp_async16(uint32_t* dst, const uint8_t* src) {
 // 4c .. 4c+3.  Consecutive threads take consecutive 16-byte chunks, so each
 // warp instruction covers four whole 128-byte rows (every sector requested
 // once, not half of it by each of two instructions).
-__device__ __forceinline__ void tile_prefetch(const uint8_t* __restrict__ in, int G, int K, int t0,
+__device__ __forceinline__ void tile_prefetch(const uint8_t* __restrict__ in, int G, long long ks, int t0,
                                               int k0, int g, uint32_t* tile, int tid) {
 #pragma unroll
   for (int it = 0; it < 8; ++it) {
     const int e = it * 256 + tid, r = e >> 3, c = e & 7;
-    cp_async16(&tile[tile_word(r, 4 * c)], in + ((long long)(t0 + r) * G + g) * K + k0 + 16 * c);
+    cp_async16(&tile[tile_word(r, 4 * c)], in + ((long long)(t0 + r) * G + g) * ks + k0 + 16 * c);
   }
 }
 
 __global__ void __launch_bounds__(256 * kTurnGroups, 1)
     turn_persist_kernel(const uint8_t* __restrict__ in, uint8_t* __restrict__ out, int T, int G,
-                        int K, long long os, int vec_ok, int pair_rows) {
+                        int K, long long ks, long long os, int vec_ok, int pair_rows) {
   extern __shared__ __align__(16) uint32_t tiles[];
   const int grp = threadIdx.x >> 8, tid = threadIdx.x & 255, bar = 1 + grp;
   uint32_t* const mine = tiles + kTurnBufs * grp * kTileWords;  // this group's buffers
@@ -197,7 +199,7 @@ __global__ void __launch_bounds__(256 * kTurnGroups, 1)
     if (w < n) {
       int t0, k0, g;
       coords(w, t0, k0, g);
-      if (is_full(t0, k0)) tile_prefetch(in, G, K, t0, k0, g, mine + b * kTileWords, tid);
+      if (is_full(t0, k0)) tile_prefetch(in, G, ks, t0, k0, g, mine + b * kTileWords, tid);
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
   };
@@ -217,7 +219,7 @@ __global__ void __launch_bounds__(256 * kTurnGroups, 1)
       group_bar(bar);
       turn_tile_store(out, T, K, G, os, pair_rows, t0, k0, g, tile, tid, true);
     } else {
-      turn_tile(in, out, T, G, K, os, vec_ok, pair_rows, t0, k0, g, tile, tid, bar);
+      turn_tile(in, out, T, G, K, ks, os, vec_ok, pair_rows, t0, k0, g, tile, tid, bar);
     }
     group_bar(bar);
     if (++b == kTurnBufs) b = 0;
@@ -367,7 +369,14 @@ __global__ void normalise_kernel(const int64_t* __restrict__ acc, double* __rest
 
 cudaError_t turn_launch(const uint8_t* in, uint8_t* out, int T, int G, int K, long long out_stride,
                         cudaStream_t s, bool pair_rows, int persist_ctas) {
-  const int vec_ok = (K % 32 == 0) && (T % 32 == 0) && (out_stride % 32 == 0) &&
+  return turn_launch_strided(in, out, T, G, K, K, out_stride, s, pair_rows, persist_ctas);
+}
+
+cudaError_t turn_launch_strided(const uint8_t* in, uint8_t* out, int T, int G, int K,
+                                long long in_stride, long long out_stride, cudaStream_t s,
+                                bool pair_rows, int persist_ctas) {
+  if (in_stride < K) return cudaErrorInvalidValue;
+  const int vec_ok = (K % 32 == 0) && (in_stride % 32 == 0) && (T % 32 == 0) && (out_stride % 32 == 0) &&
                      (reinterpret_cast<uintptr_t>(in) % 32 == 0) &&
                      (reinterpret_cast<uintptr_t>(out) % 32 == 0);
   const long long n_tiles = (long long)((T + kTT - 1) / kTT) * ((K + kTK - 1) / kTK) * G;
@@ -381,11 +390,11 @@ cudaError_t turn_launch(const uint8_t* in, uint8_t* out, int T, int G, int K, lo
       attr = true;
     }
     turn_persist_kernel<<<persist_ctas, 256 * kTurnGroups, smem, s>>>(
-        in, out, T, G, K, out_stride, vec_ok, pair_rows ? 1 : 0);
+        in, out, T, G, K, in_stride, out_stride, vec_ok, pair_rows ? 1 : 0);
     return cudaGetLastError();
   }
   dim3 grid((T + kTT - 1) / kTT, (K + kTK - 1) / kTK, G);
-  turn_kernel<<<grid, 256, 0, s>>>(in, out, T, G, K, out_stride, vec_ok, pair_rows ? 1 : 0);
+  turn_kernel<<<grid, 256, 0, s>>>(in, out, T, G, K, in_stride, out_stride, vec_ok, pair_rows ? 1 : 0);
   return cudaGetLastError();
 }
 
@@ -433,6 +442,21 @@ cudaError_t turn_rows(const uint8_t* in, uint8_t* out, int layout, int bits, int
                  : turn_launch(in, out, T, N, C, out_stride, s, false, persist_ctas);
   if (eight) return split_planes_launch(in, out, (long long)C * N, T, out_stride, s);
   return cudaSuccess;
+}
+
+cudaError_t turn_rows_chans(const uint8_t* in, uint8_t* out, int layout, int bits, int n_inputs,
+                            int n_chans, int n_time, int c0, int c1, long long out_stride,
+                            cudaStream_t s, int persist_ctas) {
+  const int N = n_inputs, C = n_chans, T = n_time;
+  if (bits != 4 || c0 < 0 || c1 > C || c0 >= c1) return cudaErrorInvalidValue;
+  // channels c0 .. c1-1 are output rows c N + i for c0 <= c < c1
+  uint8_t* o = out + (long long)c0 * N * out_stride;
+  if (layout == 0)  // [t][c][i]: bytes c0 N .. c1 N of each spectrum
+    return turn_launch_strided(in + (long long)c0 * N, o, T, 1, (c1 - c0) * N, (long long)C * N,
+                               out_stride, s, false, persist_ctas);
+  if (layout == 1)  // [t][i][c]: bytes c0 .. c1 of each (spectrum, input) row
+    return turn_launch_strided(in + c0, o, T, N, c1 - c0, C, out_stride, s, false, persist_ctas);
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t normalise_launch(const int64_t* acc, double* rho, int n_inputs, int n_chans,

@@ -73,7 +73,7 @@ _lib.corr_dump_wait.argtypes = [_P]
 _lib.corr_dump_wait.restype = _I
 _lib.corr_bind.argtypes = [_P, _P]
 _lib.corr_bind.restype = _I
-EXPORTS += ["corr_dump_async", "corr_dump_wait"]
+EXPORTS += ["corr_dump_async", "corr_dump_wait", "corr_bind"]
 CORR_MAX_ASYNC_DUMPS = 4
 _lib.corr_correlate_noalloc.argtypes = [_P, _I, _I, _I, _I, _U, _P, _P, _P]
 _lib.corr_correlate_noalloc.restype = _I
@@ -295,7 +295,7 @@ class Correlator:
 # ------------------------------------------------------------------- batches
 EXPORTS += ["corr_batch_create", "corr_batch_input", "corr_batch_output", "corr_batch_set_input",
             "corr_batch_get_output", "corr_batch_run", "corr_batch_run_plain", "corr_batch_sync",
-            "corr_batch_info_get", "corr_batch_destroy", "corr_plan_schedule"]
+            "corr_batch_info_get", "corr_batch_destroy", "corr_plan_schedule", "corr_batch_set_pipeline"]
 CORR_SCHED_PAIRS_LPT, CORR_SCHED_SINGLES_LPT, CORR_SCHED_PAIRS_RR = 0, 1, 2
 
 
@@ -320,6 +320,7 @@ _lib.corr_batch_set_input.argtypes = [_P, _I, _P, _SZ]
 _lib.corr_batch_get_output.argtypes = [_P, _I, _P]
 _lib.corr_batch_run.argtypes = [_P]
 _lib.corr_batch_run_plain.argtypes = [_P]
+_lib.corr_batch_set_pipeline.argtypes = [_P, _I, _I]
 _lib.corr_batch_sync.argtypes = [_P]
 _lib.corr_batch_info_get.argtypes = [_P, ctypes.POINTER(CorrBatchInfo)]
 _lib.corr_batch_destroy.argtypes = [_P]
@@ -387,6 +388,14 @@ class Batch:
         st = _lib.corr_batch_run_plain(self._b)
         if st != CORR_OK:
             raise CorrError(st, "corr_batch_run_plain")
+
+    def set_pipeline(self, turn_sms, n_chunks=8):
+        """Turn the largest array in channel ranges on turn_sms SMs beside the
+        cross-multiply of the ranges already turned (corr_batch_set_pipeline);
+        0 restores the single-launch graph."""
+        st = _lib.corr_batch_set_pipeline(self._b, turn_sms, n_chunks)
+        if st != CORR_OK:
+            raise CorrError(st, "corr_batch_set_pipeline")
 
     def sync(self):
         return _lib.corr_batch_sync(self._b)

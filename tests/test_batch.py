@@ -154,3 +154,48 @@ def test_batch_of_many_small_arrays(xe):
         b.run()
         assert b.sync() == xe.CORR_OK
         _check(b, shapes, blocks)
+
+
+PIPE_CASES = [
+    # split array [t][i][c] at whole 128-channel ranges, beside stacked and pre-turned arrays
+    ([(192, 256, 256, 4, 1), (32, 64, 1024, 4, 0), (20, 40, 320, 4, 2)], 16, 4),
+    # [t][i][c] with a ragged last range (300 channels: the byte path), alone
+    ([(160, 300, 256, 4, 1)], 24, 3),
+    # [t][c][i]: ranges on even channels at 64 inputs, beside a [t][i][c] array
+    ([(64, 300, 256, 4, 0), (48, 8, 512, 4, 1), (100, 3, 384, 4, 0)], 32, 3),
+]
+
+
+@pytest.mark.parametrize("shapes,turn_sms,chunks", PIPE_CASES)
+def test_batch_pipelined_exact(xe, shapes, turn_sms, chunks):
+    """corr_batch_set_pipeline: the largest splittable array turned in channel
+    ranges on a second stream beside the cross-multiply; every replay exact,
+    and the single-launch graph restored afterwards."""
+    with xe.Batch(shapes) as b:
+        b.set_pipeline(turn_sms, chunks)
+        assert b.info()["launches_per_run"] > 2
+        for rep in range(2):
+            blocks = _blocks(shapes, 300 + rep)
+            for k, blk in enumerate(blocks):
+                b.set_input(k, blk)
+            b.run()
+            assert b.sync() == xe.CORR_OK
+            _check(b, shapes, blocks)
+        b.set_pipeline(0)
+        blocks = _blocks(shapes, 310)
+        for k, blk in enumerate(blocks):
+            b.set_input(k, blk)
+        b.run()
+        assert b.sync() == xe.CORR_OK
+        _check(b, shapes, blocks)
+
+
+def test_batch_pipeline_rejections(xe):
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    with xe.Batch([(32, 64, 1024, 4, 0), (20, 40, 320, 4, 2)]) as b:   # nothing to split
+        with pytest.raises(xe.CorrError):
+            b.set_pipeline(16, 4)
+    with xe.Batch([(64, 16, 256, 4, 1)]) as b:
+        for sms, ch in ((nsm, 4), (-1, 4), (8, 0)):
+            with pytest.raises(xe.CorrError):
+                b.set_pipeline(sms, ch)
