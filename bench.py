@@ -611,8 +611,8 @@ def run_batch(args, w, world, rank, local):
     ms_plain = timed(b.run_plain, args.steps)
     # pipelined graph: a short timed sweep of the split, then the best one
     sweep = {}
-    for sms in (32, 40, 48, 56):
-        for ch in (4, 8):
+    for sms in (32, 36, 38, 40, 42, 44, 48, 52, 56):
+        for ch in (4, 8, 16, 32):
             try:
                 b.set_pipeline(sms, ch)
             except CorrError:
