@@ -317,6 +317,9 @@ typedef struct corr_batch corr_batch; /* opaque, owned by the library */
 #define CORR_SCHED_SINGLES_LPT 1 /* 128x128 tasks, longest-first                      */
 #define CORR_SCHED_PAIRS_RR 2    /* 128x256 tasks, round robin in list order           */
 
+/* schedule, n_tasks and n_ctas describe the single-launch form;
+ * launches_per_run counts the graph corr_batch_run replays now (more once
+ * corr_batch_set_pipeline has split the run). */
 typedef struct corr_batch_info {
   int schedule;          /* CORR_SCHED_* in use                                  */
   int n_tasks;           /* tasks of one cross-multiply launch                   */
