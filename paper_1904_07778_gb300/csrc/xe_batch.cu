@@ -558,13 +558,9 @@ int corr_batch_set_pipeline(corr_batch* b, int turn_sms, int n_chunks) {
   }
   if (k < 0) return CORR_EINVAL;
   const corr_shape& sh = b->shapes[k];
-  // range starts on whole 128-byte tiles of the turned rows where possible
-  int g = 128, n = sh.n_inputs;
-  while (n % 2 == 0 && g > 1 && (sh.layout == CORR_L_TCI)) {
-    n /= 2;
-    g /= 2;
-  }
-  const int unit = sh.layout == CORR_L_TIC ? 128 : g;  // channels per step of a range start
+  // ranges start on whole 128-byte tiles of the input rows: channel c0 starts
+  // at byte c0 of a [t][i][c] row and at byte c0 N of a [t][c][i] row
+  const int unit = sh.layout == CORR_L_TIC ? 128 : 128 / std::gcd(sh.n_inputs, 128);
   const int nch = std::max(1, std::min(n_chunks, sh.n_chans / unit));
   std::vector<int> c(1, 0);
   for (int j = 1; j < nch; ++j) {
