@@ -202,6 +202,20 @@ int corr_bind(corr_ctx* ctx, int64_t* vis);
  */
 int corr_normalise(corr_ctx* ctx, double* rho);
 
+/*
+ * corr_normalise_flags -- corr_normalise that also reports where the
+ * coefficient is undefined.  The paper defines no normalisation; the rule is
+ * the one above: rho = 0 where V_ii * V_jj == 0 (an input that was silent
+ * over the whole integration), and then zero_flag = 1 for that baseline.
+ *   rho       : double [C][N(N+1)/2][2], host or device memory.
+ *   zero_flag : uint8 [C][N(N+1)/2], host or device memory, or NULL (then
+ *               this is corr_normalise): 1 where V_ii * V_jj == 0, else 0.
+ * Synchronous for host buffers, stream-ordered for device buffers.  Errors
+ * as corr_normalise; CORR_ENOMEM if a host buffer's staging copy cannot be
+ * allocated.
+ */
+int corr_normalise_flags(corr_ctx* ctx, double* rho, uint8_t* zero_flag);
+
 /* corr_sync -- wait for all pushed work and queued dumps; returns any deferred
  * device error not already returned by corr_dump_wait. */
 int corr_sync(corr_ctx* ctx);
@@ -266,17 +280,23 @@ int corr_get_stats(corr_ctx* ctx, corr_stats* out);
  * CORR_NOALLOC_SCRATCH_BYTES that exists on every device that loads the
  * library, for the life of the process.  The call itself allocates nothing
  * and frees nothing, on host or device.
- *   block   : device pointer, N * C * T * bits / 4 bytes in `layout` (4-bit).
- *   vis     : device pointer, int64 [C][N(N+1)/2][2]; overwritten with this
- *             block's visibilities (not added to).
- *   status  : optional device int; receives the device status bits of this
- *             call (0 ok, 1 a bounded device-side wait ran out).
+ *   block   : device pointer on the current device, N * C * T * bits / 4
+ *             bytes in `layout` (4-bit).
+ *   vis     : device pointer on the current device, int64 [C][N(N+1)/2][2];
+ *             overwritten with this block's visibilities (not added to).
+ *   status  : optional device int on the current device; receives the device
+ *             status bits of this call (0 ok, 1 a bounded device-side wait ran
+ *             out).  The call returns before the GPU has run the work, so a
+ *             device-side failure is reported only here: a caller that passes
+ *             NULL does not learn of it.
  *   stream  : cudaStream_t to run on (NULL: the legacy default stream).
  * Limits: 256 + 20 * tasks (rounded up to 256) + (layout != CORR_L_CIT ?
- * N * C * ceil16(T) : 0) bytes must fit the scratch, where tasks is C / (128 /
+ * N * C * ceil32(T) : 0) bytes must fit the scratch, where tasks is C / (128 /
  * 2^ceil(log2 2N)) rounded up for 2N <= 64, else C times the tasks of one
- * channel; larger requests return CORR_EINVAL.  Host pointers return
- * CORR_EINVAL.  Asynchronous: returns once the work is queued.
+ * channel; larger requests return CORR_EINVAL.  Host pointers, and device
+ * pointers of another GPU, return CORR_EINVAL.  CORR_ECUDA if the device
+ * lacks the shared memory the cross-multiply needs.  Asynchronous: returns
+ * once the work is queued.
  * Set-up: the first call on a device looks up the scratch array's device
  * address (cudaGetSymbolAddress) with that device current; make that first
  * call before any stream capture.

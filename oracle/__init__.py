@@ -52,7 +52,7 @@ def _load():
             lib.oracle_decode.argtypes = [P, I, I, I, I, I, I, P, P]
             lib.oracle_correlate_cd.argtypes = [P, I, I, I, P]
             lib.oracle_normalise.argtypes = [P, I, I, P, P]
-            lib.oracle_projected_power.argtypes = [P, I, I, I, I, I, I, P, I, P, I, P]
+            lib.oracle_projected_power.argtypes = [P, I, I, I, I, I, I, P, I, P, I, P, I]
             for f in (lib.oracle_correlate, lib.oracle_decode, lib.oracle_correlate_cd,
                       lib.oracle_normalise, lib.oracle_projected_power):
                 f.restype = I
@@ -145,8 +145,10 @@ def normalise(vis: np.ndarray, n_inputs: int):
 
 
 def projected_power(block, n_inputs, n_chans, n_time, w, bits=4, layout=L_TCI, hi_is_real=True,
-                    chans=None):
-    """sum_t |sum_i conj(w_v,i) x_i(c,t)|^2 for integer complex weights w[nvec][N]."""
+                    chans=None, threads=None):
+    """sum_t |sum_i conj(w_v,i) x_i(c,t)|^2 for integer complex weights w[nvec][N],
+    int64 [n_chans or len(chans)][nvec]; channels spread over ``threads``
+    threads (default: every core)."""
     lib = _load()
     blk = np.ascontiguousarray(np.asarray(block, dtype=np.uint8).reshape(-1))
     w = np.asarray(w)
@@ -158,9 +160,16 @@ def projected_power(block, n_inputs, n_chans, n_time, w, bits=4, layout=L_TCI, h
         ch = np.ascontiguousarray(np.asarray(chans, dtype=np.int32))
         nch = ch.size
     out = np.zeros((nch, nvec), dtype=np.int64)
+    need = n_inputs * n_chans * n_time * (bits // 4)
+    if blk.size != need:
+        raise ValueError("block has %d bytes, expected %d" % (blk.size, need))
+    if wi.shape != (nvec, n_inputs, 2):
+        raise ValueError("w must be [nvec][n_inputs] complex integers")
+    if threads is None:
+        threads = os.cpu_count() or 1
     st = lib.oracle_projected_power(_ptr(blk), layout, bits, 1 if hi_is_real else 0, n_inputs,
                                     n_chans, n_time, _ptr(ch) if ch is not None else None, nch,
-                                    _ptr(wi), nvec, _ptr(out))
+                                    _ptr(wi), nvec, _ptr(out), int(threads))
     if st not in (0, ERANGE):
         raise RuntimeError("oracle_projected_power failed: %d" % st)
     return out

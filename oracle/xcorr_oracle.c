@@ -256,34 +256,102 @@ int oracle_normalise(const int64_t* vis, int N, int C, double* rho, uint8_t* zer
  * Projected power P[k][v] = sum_t | sum_i conj(w_v,i) x_i(c_k, t) |^2 for
  * complex integer weight vectors w[v][i][2].  For the Hermitian matrix V of
  * a channel, P equals w^H V w, which gives a full-coverage check of a
- * visibility matrix at sizes where the full oracle is too slow.
+ * visibility matrix at sizes where the full oracle is too slow.  Each
+ * channel's samples are decoded once (as in correlate_channel); channels are
+ * spread over nthreads threads (<= 1: serial).
  */
+typedef struct {
+  const uint8_t* in;
+  int layout, bits, hi_is_real, N, C, T;
+  const int* chans;
+  int nchan;
+  const int32_t* w;
+  int nvec;
+  int64_t* out;
+  int stride, offset;
+  int status;
+} power_job;
+
+static int power_channel(const power_job* jb, int c, int64_t* out) {
+  int N = jb->N, T = jb->T;
+  int* re = (int*)malloc(sizeof(int) * (size_t)N * (T > 0 ? T : 1));
+  int* im = (int*)malloc(sizeof(int) * (size_t)N * (T > 0 ? T : 1));
+  if (!re || !im) {
+    free(re);
+    free(im);
+    return OR_ENOMEM;
+  }
+  int status = OR_OK;
+  for (int i = 0; i < N; ++i)
+    for (int t = 0; t < T; ++t) {
+      int st = decode(jb->in, jb->layout, jb->bits, jb->hi_is_real, N, jb->C, T, c, i, t,
+                      &re[(size_t)i * T + t], &im[(size_t)i * T + t]);
+      if (st != OR_OK) status = st;
+    }
+  for (int v = 0; v < jb->nvec; ++v) {
+    const int32_t* wv = jb->w + (size_t)v * N * 2;
+    int64_t acc = 0;
+    for (int t = 0; t < T; ++t) {
+      int64_t pre = 0, pim = 0;
+      for (int i = 0; i < N; ++i) {
+        int64_t a = re[(size_t)i * T + t], b = im[(size_t)i * T + t];
+        int64_t wr = wv[2 * i], wi = wv[2 * i + 1];
+        /* conj(w) * x = (wr - i wi)(a + i b) = (wr a + wi b) + i (wr b - wi a) */
+        pre += wr * a + wi * b;
+        pim += wr * b - wi * a;
+      }
+      acc += pre * pre + pim * pim;
+    }
+    out[v] = acc;
+  }
+  free(re);
+  free(im);
+  return status;
+}
+
+static void* power_worker(void* arg) {
+  power_job* jb = (power_job*)arg;
+  for (int k = jb->offset; k < jb->nchan; k += jb->stride) {
+    int c = jb->chans ? jb->chans[k] : k;
+    int st = power_channel(jb, c, jb->out + (size_t)k * jb->nvec);
+    if (st != OR_OK) jb->status = st;
+  }
+  return NULL;
+}
+
 int oracle_projected_power(const uint8_t* in, int layout, int bits, int hi_is_real, int N, int C,
                            int T, const int* chans, int nchan, const int32_t* w, int nvec,
-                           int64_t* out) {
-  if (!in || !w || !out) return OR_EINVAL;
+                           int64_t* out, int nthreads) {
+  if (!in || !w || !out || N < 1 || C < 1 || T < 0 || nvec < 0 || (bits != 4 && bits != 8) ||
+      layout < 0 || layout > 2)
+    return OR_EINVAL;
   if (!chans) nchan = C;
-  int status = OR_OK;
-  for (int k = 0; k < nchan; ++k) {
-    int c = chans ? chans[k] : k;
-    if (c < 0 || c >= C) return OR_EINVAL;
-    for (int v = 0; v < nvec; ++v) {
-      int64_t acc = 0;
-      for (int t = 0; t < T; ++t) {
-        int64_t pre = 0, pim = 0;
-        for (int i = 0; i < N; ++i) {
-          int a, b;
-          int st = decode(in, layout, bits, hi_is_real, N, C, T, c, i, t, &a, &b);
-          if (st != OR_OK) status = st;
-          int64_t wr = w[((size_t)v * N + i) * 2], wi = w[((size_t)v * N + i) * 2 + 1];
-          /* conj(w) * x = (wr - i wi)(a + i b) = (wr a + wi b) + i (wr b - wi a) */
-          pre += wr * a + wi * b;
-          pim += wr * b - wi * a;
-        }
-        acc += pre * pre + pim * pim;
-      }
-      out[(size_t)k * nvec + v] = acc;
-    }
+  for (int k = 0; chans && k < nchan; ++k)
+    if (chans[k] < 0 || chans[k] >= C) return OR_EINVAL;
+  if (nthreads < 1) nthreads = 1;
+  if (nthreads > nchan) nthreads = nchan > 0 ? nchan : 1;
+  power_job* jobs = (power_job*)calloc((size_t)nthreads, sizeof(power_job));
+  pthread_t* th = (pthread_t*)calloc((size_t)nthreads, sizeof(pthread_t));
+  if (!jobs || !th) {
+    free(jobs);
+    free(th);
+    return OR_ENOMEM;
   }
+  for (int k = 0; k < nthreads; ++k) {
+    power_job jb = {in, layout, bits, hi_is_real, N, C, T, chans, nchan, w, nvec, out, nthreads, k,
+                    OR_OK};
+    jobs[k] = jb;
+  }
+  if (nthreads == 1) {
+    power_worker(&jobs[0]);
+  } else {
+    for (int k = 0; k < nthreads; ++k) pthread_create(&th[k], NULL, power_worker, &jobs[k]);
+    for (int k = 0; k < nthreads; ++k) pthread_join(th[k], NULL);
+  }
+  int status = OR_OK;
+  for (int k = 0; k < nthreads; ++k)
+    if (jobs[k].status != OR_OK) status = jobs[k].status;
+  free(jobs);
+  free(th);
   return status;
 }

@@ -583,42 +583,63 @@ int corr_batch_set_pipeline(corr_batch* b, int turn_sms, int n_chunks) {
       lists[li].push_back(x);
     }
   }
-  for (auto p : b->d_pipe_tasks) cudaFree(p);
-  b->d_pipe_tasks.assign(lists.size(), nullptr);
-  b->n_pipe_tasks.assign(lists.size(), 0);
-  b->max_nblk_pipe.assign(lists.size(), 1);
-  b->pipe_sms = 0;  // until everything below is in place
+  // Build the new device task lists first.  The graph captured now may still
+  // reference the old lists, so they are freed only after a new graph has
+  // replaced it; on an early error the old graph and its lists stay as they
+  // were.
+  std::vector<HerkTask*> d_new(lists.size(), nullptr);
+  std::vector<int> n_new(lists.size(), 0), nblk_new(lists.size(), 1);
+  auto drop_new = [&](int st) {
+    for (auto p : d_new) cudaFree(p);
+    cudaGetLastError();
+    return st;
+  };
   for (size_t j = 0; j < lists.size(); ++j) {
-    b->n_pipe_tasks[j] = (int)lists[j].size();
+    n_new[j] = (int)lists[j].size();
     if (lists[j].empty()) continue;
-    b->max_nblk_pipe[j] = tasks_max_nblk(lists[j]);
-    if (cudaMalloc(&b->d_pipe_tasks[j], sizeof(HerkTask) * lists[j].size()) != cudaSuccess)
-      return CORR_ENOMEM;
-    if (cudaMemcpy(b->d_pipe_tasks[j], lists[j].data(), sizeof(HerkTask) * lists[j].size(),
+    nblk_new[j] = tasks_max_nblk(lists[j]);
+    if (cudaMalloc(&d_new[j], sizeof(HerkTask) * lists[j].size()) != cudaSuccess) {
+      d_new[j] = nullptr;
+      return drop_new(CORR_ENOMEM);
+    }
+    if (cudaMemcpy(d_new[j], lists[j].data(), sizeof(HerkTask) * lists[j].size(),
                    cudaMemcpyHostToDevice) != cudaSuccess)
-      return CORR_ECUDA;
+      return drop_new(CORR_ECUDA);
   }
   if (!b->turn_stream && cudaStreamCreateWithFlags(&b->turn_stream, cudaStreamNonBlocking) != cudaSuccess) {
     b->turn_stream = nullptr;
-    return CORR_ECUDA;
+    return drop_new(CORR_ECUDA);
   }
   while (b->pipe_ev.size() < c.size()) {
     cudaEvent_t e = nullptr;
-    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return CORR_ECUDA;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return drop_new(CORR_ECUDA);
     b->pipe_ev.push_back(e);
   }
+  std::vector<HerkTask*> d_old;
+  d_old.swap(b->d_pipe_tasks);
+  b->d_pipe_tasks = d_new;
+  b->n_pipe_tasks = n_new;
+  b->max_nblk_pipe = nblk_new;
   b->pipe_inst = k;
   b->pipe_c = c;
   b->pipe_sms = turn_sms;
   // set every launch attribute outside the capture, then capture one run
+  int st = CORR_OK;
   if (enqueue_pipelined(b) != cudaSuccess || cudaStreamSynchronize(b->stream) != cudaSuccess ||
       cudaMemset(b->d_status, 0, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    st = CORR_ECUDA;
+  } else {
+    st = capture_graph(b);
+  }
+  if (st != CORR_OK) {  // back to the single-launch graph, which uses no range lists
     b->pipe_sms = 0;
     cudaGetLastError();
     capture_graph(b);
-    return CORR_ECUDA;
   }
-  return capture_graph(b);
+  // no graph references the old lists any more (capture_graph destroyed it)
+  for (auto p : d_old) cudaFree(p);
+  return st;
 }
 
 int corr_batch_sync(corr_batch* b) {

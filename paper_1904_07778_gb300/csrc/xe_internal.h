@@ -154,8 +154,9 @@ std::vector<HerkTask> plan_tasks(int byte_rows, int n_chans, int* rows_per_chan,
 // Largest number of resident 128-row blocks of any task in the list.
 int tasks_max_nblk(const std::vector<HerkTask>& tasks);
 
-// FP64 correlation coefficients from int64 visibilities.
-cudaError_t normalise_launch(const int64_t* acc, double* rho, int n_inputs, int n_chans,
-                             cudaStream_t s);
+// FP64 correlation coefficients from int64 visibilities; zero_flag (may be
+// null) gets 1 per baseline whose denominator V_ii V_jj is zero, else 0.
+cudaError_t normalise_launch(const int64_t* acc, double* rho, uint8_t* zero_flag, int n_inputs,
+                             int n_chans, cudaStream_t s);
 
 }  // namespace xe

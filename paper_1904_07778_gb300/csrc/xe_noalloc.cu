@@ -50,7 +50,7 @@ int scratch_address(void** out) {
 // Tasks per channel of the lower-triangle tiling (same tiling as the
 // context path): row block r takes column blocks r .. r + ceil(nrb/2) - 1
 // (mod nrb), plus r + nrb/2 for r < nrb/2 when nrb is even; the first two
-// share a task, the others have one task each.
+// share a task, every further column is a task of its own.
 __host__ __device__ inline int row_cols(int nrb, int r) {
   int n = (nrb + 1) / 2;
   if (nrb % 2 == 0 && r < nrb / 2) ++n;
@@ -60,14 +60,12 @@ __host__ __device__ inline int row_col(int nrb, int r, int k) {
   const int base = (nrb + 1) / 2;
   return k < base ? (r + k) % nrb : r + nrb / 2;
 }
-// columns 0 and 1 share one task, every further column is a task of its own
-__host__ __device__ inline int row_tasks(int nrb, int r) {
-  const int ncol = row_cols(nrb, r);
-  return ncol > 1 ? ncol - 1 : 1;
-}
 
-__global__ void plan_kernel(HerkTask* tasks, long long n_tasks, int n, int c, int rpc, int per_chan,
-                            int nrb) {
+// Task e of the list: the 128 x 256 tasks (first two columns of a row) of
+// every channel come first, then the single-column tasks, the order the
+// context path's planner uses.  pairs / singles: tasks of each kind per channel.
+__global__ void plan_kernel(HerkTask* tasks, long long n_tasks, int rpc, int pairs, int singles,
+                            int n_chans, int nrb) {
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n_tasks;
        e += (long long)gridDim.x * blockDim.x) {
     HerkTask t;
@@ -77,39 +75,52 @@ __global__ void plan_kernel(HerkTask* tasks, long long n_tasks, int n, int c, in
       t.rb = 0;
       t.cb[0] = 0;
       t.cb[1] = -1;
-    } else {
-      t.chan0 = (int)(e / per_chan);
-      int local = (int)(e % per_chan), r = 0;
+    } else if (e < (long long)n_chans * pairs) {
+      t.chan0 = (int)(e / pairs);
+      int local = (int)(e % pairs), r = 0;
       for (; r < nrb; ++r) {
-        const int nt = row_tasks(nrb, r);
-        if (local < nt) break;
-        local -= nt;
+        if (row_cols(nrb, r) < 2) continue;
+        if (local == 0) break;
+        --local;
       }
-      const int ncol = row_cols(nrb, r);
       t.rb = r;
-      if (local == 0) {
-        t.cb[0] = row_col(nrb, r, 0);
-        t.cb[1] = ncol > 1 ? row_col(nrb, r, 1) : -1;
-      } else {
-        t.cb[0] = row_col(nrb, r, local + 1);
-        t.cb[1] = -1;
+      t.cb[0] = row_col(nrb, r, 0);
+      t.cb[1] = row_col(nrb, r, 1);
+    } else {
+      const long long e2 = e - (long long)n_chans * pairs;
+      t.chan0 = (int)(e2 / singles);
+      int local = (int)(e2 % singles), r = 0, k = 0;
+      for (; r < nrb; ++r) {
+        const int ncol = row_cols(nrb, r);
+        const int first = ncol > 1 ? 2 : 0;  // columns of this row in single-column tasks
+        if (local < ncol - first) {
+          k = first + local;
+          break;
+        }
+        local -= ncol - first;
       }
+      t.rb = r;
+      t.cb[0] = row_col(nrb, r, k);
+      t.cb[1] = -1;
     }
     tasks[e] = t;
   }
-  (void)n;
-  (void)c;
 }
 
 __global__ void copy_status_kernel(const int* from, int* to) { *to = *from; }
 
+// Device (or managed) memory of the current device.  Memory of another GPU
+// would be read and written by this device's kernels: rejected.
 bool is_device(const void* p) {
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  if (at.type == cudaMemoryTypeDevice) return at.device == dev;
+  return at.type == cudaMemoryTypeManaged;
 }
 
 }  // namespace
@@ -127,7 +138,7 @@ extern "C" int corr_correlate_noalloc(const void* block, int n_inputs, int n_cha
   if (!is_device(block) || !is_device(vis) || (status && !is_device(status))) return CORR_EINVAL;
   const int N = n_inputs, C = n_chans, T = n_time;
   // scratch layout: [status (256 B)] [tasks] [corner-turned block]
-  int rpc = 0, per_chan = 0, nrb = 0;
+  int rpc = 0, pairs = 0, singles = 0, nrb = 0;
   long long n_tasks;
   if (2 * N <= 64) {
     rpc = 2;
@@ -135,13 +146,21 @@ extern "C" int corr_correlate_noalloc(const void* block, int n_inputs, int n_cha
     n_tasks = ((long long)C + 128 / rpc - 1) / (128 / rpc);
   } else {
     nrb = (2 * N + 127) / 128;
-    for (int r = 0; r < nrb; ++r) per_chan += row_tasks(nrb, r);
-    n_tasks = (long long)per_chan * C;
+    for (int r = 0; r < nrb; ++r) {
+      const int ncol = row_cols(nrb, r);
+      pairs += ncol > 1 ? 1 : 0;
+      singles += ncol > 1 ? ncol - 2 : 1;
+    }
+    n_tasks = (long long)(pairs + singles) * C;
   }
   const long long task_bytes = (n_tasks * (long long)sizeof(HerkTask) + 255) / 256 * 256;
-  const long long row_stride = ((long long)T + 15) / 16 * 16;
+  // turned rows padded to 32 bytes: the corner turn's fast path, as in corr_create
+  const long long row_stride = ((long long)T + 31) / 32 * 32;
   const long long turned_bytes = layout == CORR_L_CIT ? 0 : row_stride * N * C;
   if (256 + task_bytes + turned_bytes > (long long)kNoAllocScratchBytes) return CORR_EINVAL;
+  // the cross-multiply needs four ring slots of its largest stage (as corr_create checks)
+  const int smem = herk4_max_smem();
+  if (smem < 4 * 2 * (16384 + 8192) + 1024) return CORR_ECUDA;
   void* base = nullptr;
   int st = scratch_address(&base);
   if (st != CORR_OK) return st;
@@ -153,7 +172,7 @@ extern "C" int corr_correlate_noalloc(const void* block, int n_inputs, int n_cha
   // the scratch keeps the previous call's contents: clear the status word
   if (cudaMemsetAsync(d_status, 0, sizeof(int), s) != cudaSuccess) return CORR_ECUDA;
   const int pblocks = (int)std::min<long long>((n_tasks + 255) / 256, 1024);
-  plan_kernel<<<pblocks, 256, 0, s>>>(tasks, n_tasks, N, C, rpc, per_chan, nrb);
+  plan_kernel<<<pblocks, 256, 0, s>>>(tasks, n_tasks, rpc, pairs, singles, C, nrb);
   if (cudaGetLastError() != cudaSuccess) return CORR_ECUDA;
 
   const uint8_t* src = static_cast<const uint8_t*>(block);
@@ -176,7 +195,7 @@ extern "C" int corr_correlate_noalloc(const void* block, int n_inputs, int n_cha
   a.in.n_chans = C;
   a.in.rows_per_chan = rpc;
   a.lo_is_real = (flags & CORR_F_LO_IS_REAL) ? 1 : 0;
-  a.smem_bytes = herk4_max_smem();
+  a.smem_bytes = smem;
   a.n_tasks = (int)n_tasks;
   a.max_nblk = (rpc == 0 && nrb >= 2) ? 2 : 1;  // row blocks resident per task (see planner)
   a.bits = 4;

@@ -146,6 +146,7 @@ struct corr_ctx {
   int* d_status = nullptr;
   int* h_status = nullptr;  // pinned
   double* rho_tmp = nullptr;
+  uint8_t* flag_tmp = nullptr;
   bool seq_started = false;
   uint64_t next_seq = 0;
   // run-time counters and optional per-phase event timing
@@ -263,6 +264,7 @@ void free_ctx(corr_ctx* x) {
   cudaFree(x->tasks);
   cudaFree(x->d_status);
   cudaFree(x->rho_tmp);
+  cudaFree(x->flag_tmp);
   for (auto& t : x->pending) {
     cudaEventDestroy(t.begin);
     cudaEventDestroy(t.end);
@@ -739,11 +741,14 @@ int corr_restore(corr_ctx* x, const int64_t* vis) {
   return CORR_OK;
 }
 
-int corr_normalise(corr_ctx* x, double* rho) {
+int corr_normalise(corr_ctx* x, double* rho) { return corr_normalise_flags(x, rho, nullptr); }
+
+int corr_normalise_flags(corr_ctx* x, double* rho, uint8_t* zero_flag) {
   TraceRange trace_("corr_normalise");
   if (!x || !rho) return CORR_EINVAL;
   if (pipe_join(x) != CORR_OK) return CORR_ECUDA;
   const size_t bytes = x->acc_bytes;  // same element count, 8-byte elements
+  const size_t flag_bytes = bytes / 16;  // one byte per baseline and channel
   if (!x->acc_live) {
     if (int g = guard_acc_write(x, x->stream)) return g;
     if (cudaMemsetAsync(x->acc, 0, x->acc_bytes, x->stream) != cudaSuccess) return CORR_ECUDA;
@@ -755,12 +760,21 @@ int corr_normalise(corr_ctx* x, double* rho) {
     if (!x->rho_tmp && cudaMalloc(&x->rho_tmp, bytes) != cudaSuccess) return CORR_ENOMEM;
     d = x->rho_tmp;
   }
+  const bool fdev = zero_flag && is_device_ptr(zero_flag);
+  uint8_t* f = zero_flag;
+  if (zero_flag && !fdev) {
+    if (!x->flag_tmp && cudaMalloc(&x->flag_tmp, flag_bytes) != cudaSuccess) return CORR_ENOMEM;
+    f = x->flag_tmp;
+  }
   cudaEvent_t tn = phase_begin(x, x->stream);
-  cudaError_t e = normalise_launch(x->acc, d, x->n_inputs, x->n_chans, x->stream);
+  cudaError_t e = normalise_launch(x->acc, d, f, x->n_inputs, x->n_chans, x->stream);
   if (e != cudaSuccess) return cuda_fail(e);
   phase_end(x, kNorm, tn, x->stream);
   ++x->stats.norm_launches;
   if (!dev && cudaMemcpyAsync(rho, d, bytes, cudaMemcpyDeviceToHost, x->stream) != cudaSuccess)
+    return CORR_ECUDA;
+  if (zero_flag && !fdev &&
+      cudaMemcpyAsync(zero_flag, f, flag_bytes, cudaMemcpyDeviceToHost, x->stream) != cudaSuccess)
     return CORR_ECUDA;
   return take_status(x);
 }

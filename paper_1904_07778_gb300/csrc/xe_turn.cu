@@ -341,7 +341,8 @@ __global__ void split_planes_kernel(const uint8_t* __restrict__ in, uint8_t* __r
 
 // ---------------------------------------------------------------- normalise
 __global__ void normalise_kernel(const int64_t* __restrict__ acc, double* __restrict__ rho,
-                                 int n, long long nbl, long long total) {
+                                 uint8_t* __restrict__ zero_flag, int n, long long nbl,
+                                 long long total) {
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
     const long long c = e / nbl, b = e % nbl;
@@ -361,6 +362,7 @@ __global__ void normalise_kernel(const int64_t* __restrict__ acc, double* __rest
     }
     rho[2 * e] = re;
     rho[2 * e + 1] = im;
+    if (zero_flag) zero_flag[e] = den2 == 0.0 ? 1 : 0;
   }
   (void)n;
 }
@@ -459,13 +461,13 @@ cudaError_t turn_rows_chans(const uint8_t* in, uint8_t* out, int layout, int bit
   return cudaErrorInvalidValue;
 }
 
-cudaError_t normalise_launch(const int64_t* acc, double* rho, int n_inputs, int n_chans,
-                             cudaStream_t s) {
+cudaError_t normalise_launch(const int64_t* acc, double* rho, uint8_t* zero_flag, int n_inputs,
+                             int n_chans, cudaStream_t s) {
   const long long nbl = (long long)n_inputs * (n_inputs + 1) / 2;
   const long long total = nbl * n_chans;
   long long blocks = (total + 255) / 256;
   if (blocks > 152 * 32) blocks = 152 * 32;
-  normalise_kernel<<<(unsigned)blocks, 256, 0, s>>>(acc, rho, n_inputs, nbl, total);
+  normalise_kernel<<<(unsigned)blocks, 256, 0, s>>>(acc, rho, zero_flag, n_inputs, nbl, total);
   return cudaGetLastError();
 }
 

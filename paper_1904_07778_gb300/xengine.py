@@ -61,6 +61,9 @@ class CorrStats(ctypes.Structure):
 
 
 _lib.corr_set_timing.argtypes = [_P, _I]
+_lib.corr_normalise_flags.argtypes = [_P, _P, _P]
+_lib.corr_normalise_flags.restype = _I
+EXPORTS.append("corr_normalise_flags")
 _lib.corr_restore.argtypes = [_P, _P]
 _lib.corr_restore.restype = _I
 EXPORTS.append("corr_restore")
@@ -117,6 +120,10 @@ def corr_dump(ctx, vis_ptr: int, reset: int = 1) -> int:
 
 def corr_normalise(ctx, rho_ptr: int) -> int:
     return _lib.corr_normalise(ctx, _P(rho_ptr))
+
+
+def corr_normalise_flags(ctx, rho_ptr: int, flag_ptr: int) -> int:
+    return _lib.corr_normalise_flags(ctx, _P(rho_ptr), _P(flag_ptr) if flag_ptr else None)
 
 
 def corr_sync(ctx) -> int:
@@ -255,8 +262,17 @@ class Correlator:
             raise CorrError(st, "corr_normalise")
         return rho
 
-    def normalise(self):
-        return self.normalise_into(np.empty((self.n_chans, self.n_baselines, 2), dtype=np.float64))
+    def normalise(self, flags=False):
+        """FP64 correlation coefficients [C][B][2]; with flags=True also the
+        zero-denominator flags [C][B] (1 where V_ii V_jj = 0)."""
+        rho = np.empty((self.n_chans, self.n_baselines, 2), dtype=np.float64)
+        if not flags:
+            return self.normalise_into(rho)
+        zf = np.empty((self.n_chans, self.n_baselines), dtype=np.uint8)
+        st = corr_normalise_flags(self._ctx, rho.ctypes.data, zf.ctypes.data)
+        if st != CORR_OK:
+            raise CorrError(st, "corr_normalise_flags")
+        return rho, zf
 
     def set_timing(self, on=True):
         corr_set_timing(self._ctx, 1 if on else 0)

@@ -130,6 +130,39 @@ def test_normalise(xe):
     assert np.allclose(rho, want, rtol=1e-12, atol=0)
 
 
+@pytest.mark.parametrize("device_out", [False, True])
+def test_normalise_zero_denominator_flags(xe, device_out):
+    """An input silent over the whole integration makes V_ii = 0: rho is 0
+    and the flag is set on its row and column (auto included), nowhere
+    else; every value and flag equals the oracle's."""
+    N, C, T = 24, 5, 300
+    silent = 7
+    blks = [synth.block("sky", 40 + k, N, C, T, layout=1) for k in range(2)]
+    for b in blks:
+        b.reshape(T, N, C)[:, silent, :] = 0          # [t][i][c]: input 7 silent everywhere
+    with xe.Correlator(N, C, T, layout=1) as cor:
+        for b in blks:
+            cor.push(b)
+        if device_out:
+            nb = N * (N + 1) // 2
+            rho_d = torch.empty((C, nb, 2), dtype=torch.float64, device="cuda")
+            flag_d = torch.full((C, nb), 9, dtype=torch.uint8, device="cuda")
+            assert xe.corr_normalise_flags(cor._ctx, rho_d.data_ptr(), flag_d.data_ptr()) == xe.CORR_OK
+            cor.sync()
+            rho, zf = rho_d.cpu().numpy(), flag_d.cpu().numpy()
+        else:
+            rho, zf = cor.normalise(flags=True)
+        vis = cor.dump()
+    assert np.array_equal(vis, _oracle(blks, N, C, T, 1))
+    want_rho, want_flag = oracle.normalise(vis, N)
+    assert np.array_equal(zf, want_flag)
+    assert np.allclose(rho, want_rho, rtol=1e-12, atol=0)
+    ii, jj = np.tril_indices(N)
+    touched = (ii == silent) | (jj == silent)
+    assert (zf[:, touched] == 1).all() and (zf[:, ~touched] == 0).all()
+    assert (rho[:, touched] == 0).all()
+
+
 def test_dish_array_full_size(xe):
     """32 inputs, 256 channels, 1024 spectra, payload order: full parity."""
     N, C, T = 32, 256, 1024

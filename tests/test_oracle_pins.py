@@ -229,6 +229,30 @@ def test_projected_power_is_quadratic_form():
                 assert q.imag == 0 and int(q.real) == pp[c, k]
 
 
+def test_projected_power_brute_force_every_layout_and_thread_count():
+    """The projected power against a direct numpy evaluation of its
+    definition (decode by hand, then sum over time of |w^H x(t)|^2), for every
+    layout, a channel subset and one or several threads."""
+    N, C, T = 5, 7, 33
+    rng = np.random.default_rng(31)
+    w = rng.integers(-2, 3, size=(3, N)) + 1j * rng.integers(-2, 3, size=(3, N))
+    nib = lambda n: np.where(n >= 8, n - 16, n)
+    for layout in (0, 1, 2):
+        blk = synth.random_bytes(40 + layout, N * C * T)
+        shape = {0: (T, C, N), 1: (T, N, C), 2: (C, N, T)}[layout]
+        perm = {0: (1, 2, 0), 1: (2, 1, 0), 2: (0, 1, 2)}[layout]
+        b = blk.reshape(shape).transpose(perm).astype(np.int64)   # [C][N][T]
+        x = nib(b >> 4) + 1j * nib(b & 15)
+        want = np.array([[int(np.rint((np.abs(np.conj(wv) @ x[c]) ** 2).sum())) for wv in w]
+                         for c in range(C)])
+        for threads in (1, 3):
+            got = oracle.projected_power(blk, N, C, T, w, layout=layout, threads=threads)
+            assert np.array_equal(got, want), (layout, threads)
+        sub = [6, 0, 3]
+        got = oracle.projected_power(blk, N, C, T, w, layout=layout, chans=sub, threads=2)
+        assert np.array_equal(got, want[sub])
+
+
 def test_minus_128_rejected():
     """8-bit -128 lies outside the symmetric quantiser and is an error."""
     blk = np.array([0x80, 0x00, 0x01, 0x02], dtype=np.uint8)

@@ -5,15 +5,18 @@ by another framework, allocation frozen after start-up, real-time loops).  It
 keeps its intermediates in a fixed scratch array inside the library, shared by
 every call.  This test calls it through the C ABI several times in a row, with
 different shapes, and checks each result against the context path
-(corr_create / corr_push / corr_dump) on the same bytes: the visibilities are
-integers, so they must agree exactly.  The file name sorts last so that a run
-stopping at the first failure has already run every other test.
+(corr_create / corr_push / corr_dump) and against the oracle on the same
+bytes: the visibilities are integers, so they must agree exactly.  The file
+name sorts last so that a run stopping at the first failure has already run
+every other test.
 """
 import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -51,13 +54,16 @@ def test_noalloc_matches_context_path_on_consecutive_calls(xe):
         (64, 16, 1024, xe.CORR_L_TIC),   # corner turn through the scratch
         (32, 64, 512, xe.CORR_L_TCI),    # stacked small array
         (100, 5, 300, xe.CORR_L_CIT),    # ragged tail, no corner turn
+        (130, 4, 1024, xe.CORR_L_TIC),   # three row blocks: paired tasks on the TMA ring kernel
+        (4, 1, 70000, xe.CORR_L_CIT),    # longer than one accumulation, unaligned rows
         (64, 16, 1024, xe.CORR_L_TIC),   # first shape again, new data
     ]
     for N, C, T, layout in cases:
-        blk = torch.from_numpy(rng.integers(0, 256, N * C * T, dtype=np.uint8)).cuda()
+        host = rng.integers(0, 256, N * C * T, dtype=np.uint8)
+        blk = torch.from_numpy(host).cuda()
         got = _noalloc(xe, blk, N, C, T, layout)
-        want = _reference(xe, blk, N, C, T, layout)
-        assert np.array_equal(got, want), (N, C, T, layout)
+        assert np.array_equal(got, _reference(xe, blk, N, C, T, layout)), (N, C, T, layout)
+        assert np.array_equal(got, oracle.correlate(host, N, C, T, layout=layout)), (N, C, T, layout)
 
 
 def test_noalloc_rejects_requests_beyond_the_scratch(xe):
