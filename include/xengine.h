@@ -262,6 +262,28 @@ typedef struct corr_stats {
   uint64_t timed_herk;      /* launches included in herk_ms                   */
 } corr_stats;
 
+/*
+ * corr_set_fault_injection -- test hook for the failure detection of the
+ * device-side waits (the paper has no counterpart; its pipeline monitor of
+ * Sec. 2.2 only reports status).  Every wait inside the cross-multiply is
+ * bounded; when one runs out the kernel records CORR_ETIMEDOUT in the
+ * context's status word, lets every role of the CTA leave (no copy or MMA
+ * left in flight, tensor memory freed) and returns, so the context stays
+ * usable.  This call makes that happen on purpose:
+ *   stage       : >= 0: the first CTA of every later cross-multiply never
+ *                 loads its stage `stage` (128-spectrum steps of its task
+ *                 list), so the waits for it run out; -1 turns it off.
+ *   wait_log2   : 1 .. 40 limits every wait to 2^wait_log2 SM cycles
+ *                 instead of the default budget of 2^31 (about a second);
+ *                 0 restores the default.
+ * The visibilities of a push made with a fault are undefined and its dump
+ * returns CORR_ETIMEDOUT.  Only the 4-bit TMA path of corr_push (row
+ * strides that are multiples of 16 bytes) reads the hook.  Waits for the
+ * context's work first.  CORR_EINVAL for stage outside -1 .. 2^24 - 2 or
+ * wait_log2 outside 0 .. 40.
+ */
+int corr_set_fault_injection(corr_ctx* ctx, int stage, int wait_log2);
+
 /* corr_set_timing -- turn per-phase device timing on (1) or off (0). */
 int corr_set_timing(corr_ctx* ctx, int on);
 
@@ -489,9 +511,12 @@ int corr_svc_submit(corr_svc* s, const corr_req* r, int64_t* id);
 int corr_svc_state(corr_svc* s, int64_t id, int* state);
 
 /* corr_svc_push -- the request's next block (host or device memory, N C T
- * bits/4 bytes in its layout), copied in on the ingest stream.  CORR_ESTATE
- * unless the request is active and still expects blocks; CORR_EBUSY while two
- * pushed blocks are waiting for ticks. */
+ * bits/4 bytes in its layout), copied in on the ingest stream.  The copy is
+ * ordered after nothing the caller queued: a device block must be complete
+ * when the call is made (synchronize its producer first).  The block may be
+ * reused once the tick that integrates it has completed (corr_svc_wait).
+ * CORR_ESTATE unless the request is active and still expects blocks;
+ * CORR_EBUSY while two pushed blocks are waiting for ticks. */
 int corr_svc_push(corr_svc* s, int64_t id, const void* block, size_t nbytes);
 
 /* corr_svc_tick -- correlate the oldest waiting block of every active

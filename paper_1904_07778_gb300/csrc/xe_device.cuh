@@ -11,6 +11,7 @@ namespace xe {
 
 // Cycle budget of one bounded wait (about a second at GB300 clocks).
 constexpr long long kWaitCycles = 1ll << 31;
+static_assert(kWaitCycles == (1ll << 31), "mbar_wait's default budget_log2 is 31");
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -34,13 +35,15 @@ __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Wait until the phase with the given parity has completed, or give up.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
+// Wait until the phase with the given parity has completed, or give up when
+// *abort is set or after 2^budget_log2 cycles (default kWaitCycles).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort,
+                                          int budget_log2 = 31) {
   if (mbar_test(bar, parity)) return true;
   const long long t0 = clock64();
   while (!mbar_test(bar, parity)) {
     if (*abort) return false;
-    if (clock64() - t0 > kWaitCycles) return false;
+    if ((clock64() - t0) >> budget_log2) return false;
   }
   return true;
 }
@@ -171,6 +174,13 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const void* tmap, int 
       " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
       "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(smem_addr(bar))
       : "memory");
+}
+// Ask for a box of a tensor to be brought into L2 (no completion, no shared
+// memory): the later load of the same box then hits L2.
+__device__ __forceinline__ void tma_prefetch_3d(const void* tmap, int c0, int c1, int c2) {
+  asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];" ::"l"(tmap),
+               "r"(c0), "r"(c1), "r"(c2)
+               : "memory");
 }
 // Order a tensor map that was written to global memory by ordinary stores
 // (a host copy) before its first use by TMA in this kernel.

@@ -59,7 +59,11 @@ struct HerkInst {
   int rows_per_chan;         // stacked mode: rows per channel in a tile; 0 = not stacked
   int accumulate;            // 0: store into acc, 1: add into acc
   int vec_ok;                // 16-byte loads are aligned everywhere
-  int pad;
+  // Fault injection for the tests of the bounded waits, read from the
+  // single-array launch's instance only (0 = off): bits 0..23 = s > 0 makes
+  // the TMA loader of CTA 0 skip its stage s - 1, so the waits for it run
+  // out; bits 24..30 = w > 0 limits every wait to 2^w cycles.
+  int fault;
 };
 
 struct HerkArgs {

@@ -152,6 +152,8 @@ struct corr_ctx {
   // run-time counters and optional per-phase event timing
   corr_stats stats{};
   bool timing = false;
+  // fault injection for the tests of the bounded device waits (HerkInst::fault; 0 = off)
+  int fault = 0;
   struct Timed {
     int phase;
     cudaEvent_t begin, end;
@@ -490,6 +492,7 @@ int corr_push(corr_ctx* x, const void* block, size_t nbytes, uint64_t seq) {
   HerkArgs a;
   memset(&a, 0, sizeof(a));
   a.in.x = src;
+  a.in.fault = x->fault;
   a.in.acc = x->acc;
   a.tasks = x->tasks;
   a.status = x->d_status;
@@ -777,6 +780,14 @@ int corr_normalise_flags(corr_ctx* x, double* rho, uint8_t* zero_flag) {
       cudaMemcpyAsync(zero_flag, f, flag_bytes, cudaMemcpyDeviceToHost, x->stream) != cudaSuccess)
     return CORR_ECUDA;
   return take_status(x);
+}
+
+int corr_set_fault_injection(corr_ctx* x, int stage, int wait_log2) {
+  if (!x || stage < -1 || stage >= (1 << 24) - 1 || wait_log2 < 0 || wait_log2 > 40)
+    return CORR_EINVAL;
+  if (pipe_join(x) != CORR_OK) return CORR_ECUDA;
+  x->fault = (stage + 1) | (wait_log2 << 24);
+  return CORR_OK;
 }
 
 int corr_set_timing(corr_ctx* x, int on) {

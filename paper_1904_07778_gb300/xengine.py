@@ -61,6 +61,9 @@ class CorrStats(ctypes.Structure):
 
 
 _lib.corr_set_timing.argtypes = [_P, _I]
+_lib.corr_set_fault_injection.argtypes = [_P, _I, _I]
+_lib.corr_set_fault_injection.restype = _I
+EXPORTS.append("corr_set_fault_injection")
 _lib.corr_normalise_flags.argtypes = [_P, _P, _P]
 _lib.corr_normalise_flags.restype = _I
 EXPORTS.append("corr_normalise_flags")
@@ -273,6 +276,14 @@ class Correlator:
         if st != CORR_OK:
             raise CorrError(st, "corr_normalise_flags")
         return rho, zf
+
+    def set_fault_injection(self, stage, wait_log2=0):
+        """Test hook (corr_set_fault_injection): the first CTA of later
+        cross-multiplies never loads its stage ``stage`` (-1: off), and every
+        device wait gives up after 2^wait_log2 cycles (0: default budget)."""
+        st = _lib.corr_set_fault_injection(self._ctx, stage, wait_log2)
+        if st != CORR_OK:
+            raise CorrError(st, "corr_set_fault_injection")
 
     def set_timing(self, on=True):
         corr_set_timing(self._ctx, 1 if on else 0)

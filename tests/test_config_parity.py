@@ -124,6 +124,7 @@ def test_service_scale_up_arrays(xe):
     dev = torch.device("cuda")
     data = {k: [synth.block_device("gauss", 400 + 10 * k + s, n, C, t, lay, dev, bits=bits)
                 for s in range(nblk)] for k, (n, t, nblk) in enumerate(reqs)}
+    torch.cuda.synchronize()   # a pushed block must be complete: the service copies it on its own stream
     results = {}
     with xe.Service(48 << 30) as svc:
         ids = [svc.submit(n, C, bits, lay, t, nblk) for n, t, nblk in reqs]
