@@ -175,13 +175,6 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const void* tmap, int 
       "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(smem_addr(bar))
       : "memory");
 }
-// Ask for a box of a tensor to be brought into L2 (no completion, no shared
-// memory): the later load of the same box then hits L2.
-__device__ __forceinline__ void tma_prefetch_3d(const void* tmap, int c0, int c1, int c2) {
-  asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];" ::"l"(tmap),
-               "r"(c0), "r"(c1), "r"(c2)
-               : "memory");
-}
 // Order a tensor map that was written to global memory by ordinary stores
 // (a host copy) before its first use by TMA in this kernel.
 __device__ __forceinline__ void tensormap_acquire(const void* tmap) {

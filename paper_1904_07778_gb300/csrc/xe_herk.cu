@@ -468,11 +468,6 @@ static_assert(kUnpackWarps * 32 * kRegsUnpack + (kRingThreads - kUnpackWarps * 3
 #define XE_MAX_SLOTS 16
 #endif
 constexpr int kMaxSlots = XE_MAX_SLOTS;  // ring slots at most (shared memory sets the count)
-// Stages the TMA warp prefetches into L2 ahead of its loads (0: none).
-#ifndef XE_PREFETCH
-#define XE_PREFETCH 16
-#endif
-constexpr int kPrefetch = XE_PREFETCH;
 static_assert(kEpiWarps % 4 == 0, "drain warps cover the four tensor-memory lane quarters");
 
 struct RingCtrl {
@@ -568,33 +563,7 @@ __global__ void __launch_bounds__(kRingThreads, 1)
       if (a.tmaps) tensormap_acquire(tm);
       int nk = stages_of(in);
       bool stacked = in.rows_per_chan > 0;
-      // L2 prefetch cursor, kPrefetch stages ahead of the loads: a load is
-      // issued only when the MMAs have released its ring slot, so most of
-      // its latency would otherwise sit inside the ring's turnaround
-      int pj = 0, pk = 0, pS = 0;
-      HerkTask ptask = task;
-      const CUtensorMap* ptm = tm;
-      int pt0 = in.t0, pnk = nk;
-      bool pstacked = stacked;
       for (int S = 0;; ++S, ++k) {
-        for (; kPrefetch > 0 && !EIGHT && pj < n_my && pS <= S + kPrefetch; ++pS) {
-          const TaskGeom pg = task_geom(ptask);
-          const int pt = pt0 + pk * kRStageT;
-          for (int b = 0; b < pg.nblk; ++b)
-            tma_prefetch_3d(ptm, pt, pstacked ? 0 : 64 * slot_block(pg, b), ptask.chan0);
-          if (++pk == pnk) {
-            pk = 0;
-            if (++pj < n_my) {
-              ptask = my_task(a, pj);
-              const HerkInst pin = task_inst(a, ptask);
-              ptm = a.tmaps ? &a.tmaps[ptask.inst] : &tmap;
-              if (a.tmaps) tensormap_acquire(ptm);
-              pt0 = pin.t0;
-              pnk = stages_of(pin);
-              pstacked = pin.rows_per_chan > 0;
-            }
-          }
-        }
         if (k == nk) {  // next task
           if (++j == n_my) break;
           k = 0;
