@@ -459,11 +459,9 @@ constexpr int kEpiWarps = XE_EPI_WARPS;
 constexpr int kRingThreads = (kEpiWarp0 + kEpiWarps) * 32;
 // registers per thread: launch share, unpack warpgroups, the other warpgroups
 constexpr int kRegsLaunch = (65536 / kRingThreads) & ~7;
-// (the warpgroup of the MMA and TMA warps gets a few more than the drain)
-constexpr int kRegsUnpack = 88, kRegsCtl = 56, kRegsOther = 48;
+constexpr int kRegsUnpack = 88, kRegsOther = 48;
 static_assert(kRingThreads % 128 == 0, "whole warpgroups");
-static_assert(kUnpackWarps * 32 * kRegsUnpack + 128 * kRegsCtl +
-                      (kRingThreads - kUnpackWarps * 32 - 128) * kRegsOther <=
+static_assert(kUnpackWarps * 32 * kRegsUnpack + (kRingThreads - kUnpackWarps * 32) * kRegsOther <=
                   kRingThreads * kRegsLaunch,
               "the register split must fit in the launch allocation");
 #ifndef XE_MAX_SLOTS
@@ -551,7 +549,7 @@ __global__ void __launch_bounds__(kRingThreads, 1)
   // joined again would leave the compiler the smaller budget for all roles.
   if (warp == kTmaWarp) {
     // ------------------------------------------------------------ TMA loader
-    regs_shrink<kRegsCtl>();
+    regs_shrink<kRegsOther>();
     if (lane == 0 && n_my > 0) {
       if (!a.tmaps) tma_prefetch_desc(&tmap);
       // fault injection: this stage of CTA 0 is never loaded, so the waits
@@ -559,9 +557,6 @@ __global__ void __launch_bounds__(kRingThreads, 1)
       const int skip = (blockIdx.x == 0 && (a.in.fault & 0xFFFFFF) > 0) ? (a.in.fault & 0xFFFFFF) - 1 : -1;
       int s = 0, m = 0, j = 0, k = 0, issued = 0;
       HerkTask task = my_task(a, 0);
-      // every role reads task j + 1's descriptor while it works on task j, so
-      // no global-memory latency sits at a task boundary
-      HerkTask nxt = my_task(a, n_my > 1 ? 1 : 0);
       TaskGeom g = task_geom(task);
       HerkInst in = task_inst(a, task);
       const CUtensorMap* tm = a.tmaps ? &a.tmaps[task.inst] : &tmap;
@@ -572,8 +567,7 @@ __global__ void __launch_bounds__(kRingThreads, 1)
         if (k == nk) {  // next task
           if (++j == n_my) break;
           k = 0;
-          task = nxt;
-          if (j + 1 < n_my) nxt = my_task(a, j + 1);
+          task = my_task(a, j);
           g = task_geom(task);
           in = task_inst(a, task);
           tm = a.tmaps ? &a.tmaps[task.inst] : &tmap;
@@ -611,21 +605,15 @@ __global__ void __launch_bounds__(kRingThreads, 1)
     __syncwarp();
   } else if (warp == kMmaWarp) {
     // ------------------------------------------------------------ MMA issuer
-    regs_shrink<kRegsCtl>();
+    regs_shrink<kRegsOther>();
     if (lane == 0) {
       int s = 0, m = 0;
       bool ok = true;
-      HerkTask nxt = my_task(a, 0);
-      int nxt_nk = stages_of(task_inst(a, nxt));
       for (int j = 0; j < n_my && ok; ++j) {
         const int b = j & 1;
-        const HerkTask task = nxt;
-        const int nk = nxt_nk;
-        if (j + 1 < n_my) {
-          nxt = my_task(a, j + 1);
-          nxt_nk = stages_of(task_inst(a, nxt));
-        }
+        const HerkTask task = my_task(a, j);
         const TaskGeom g = task_geom(task);
+        const int nk = stages_of(task_inst(a, task));
         const uint32_t idesc = umma_idesc(0, 128, 128 * g.nb);
         if (j >= 2 && !mbar_wait(&sm.tmem_empty[b], (uint32_t)(((j >> 1) - 1) & 1), abort, budget)) {
           raise_timeout(a.status, abort);
@@ -676,23 +664,13 @@ __global__ void __launch_bounds__(kRingThreads, 1)
     int S = grp, s = grp, m = 0;
     uint32_t bad = 0;  // 8-bit: a byte equal to 0x80 (-128) was seen
     int S0 = 0;  // first stage of task j
-    // of each task the unpack needs only its resident blocks and length
-    int nxt_nblk, nxt_tn;
-    {
-      const HerkTask t0 = my_task(a, 0);
-      nxt_nblk = task_geom(t0).nblk;
-      nxt_tn = task_inst(a, t0).tn;
-    }
     for (int j = 0; j < n_my && ok; ++j) {
       const int b = j & 1;
-      const int nblk = nxt_nblk, tn = nxt_tn;
-      if (j + 1 < n_my) {
-        const HerkTask t1 = my_task(a, j + 1);
-        nxt_nblk = task_geom(t1).nblk;
-        nxt_tn = task_inst(a, t1).tn;
-      }
+      const HerkTask task = my_task(a, j);
+      const TaskGeom g = task_geom(task);
+      const int tn = task_inst(a, task).tn;
       const int S1 = S0 + (tn + kRStageT - 1) / kRStageT;
-      const int nit = nblk * 64 * kRChunks / kGroupThreads;
+      const int nit = g.nblk * 64 * kRChunks / kGroupThreads;
       int32_t sre[kItems], sim[kItems];
 #pragma unroll
       for (int it = 0; it < kItems; ++it) sre[it] = sim[it] = 0;
@@ -703,7 +681,7 @@ __global__ void __launch_bounds__(kRingThreads, 1)
                    mbar_wait(&sm.full_t[s], (uint32_t)(m & 1), abort, budget);
         if (!got) raise_timeout(a.status, abort);
         const uint32_t so = (uint32_t)(s * slot_bytes);
-        const uint32_t src = src0 + so + (uint32_t)(nblk * kRPkBlock);
+        const uint32_t src = src0 + so + (uint32_t)(g.nblk * kRPkBlock);
         const bool tail = (k + 1) * kRStageT > tn;
         uint32_t keep[4] = {~0u, ~0u, ~0u, ~0u};
         if (tail) time_keep(k * kRStageT + chunk * 16, tn, keep);
@@ -757,21 +735,19 @@ __global__ void __launch_bounds__(kRingThreads, 1)
     }
     if (EIGHT && __any_sync(0xFFFFFFFFu, bad != 0) && lane == 0) atomicOr(a.status, kStRange);
   } else if (warp < kEpiWarp0) {
-    regs_shrink<kRegsCtl>();  // the two idle warps of the MMA / TMA warpgroup
+    regs_shrink<kRegsOther>();  // the two idle warps of the MMA / TMA warpgroup
   } else {
     // ------------------------------------------------------------ drain
     regs_shrink<kRegsOther>();
     const int quad = warp & 3, part = (warp - kEpiWarp0) >> 2;
-    HerkTask nxt = my_task(a, 0);
     for (int j = 0; j < n_my; ++j) {
       const int b = j & 1;
       const uint32_t par = (uint32_t)((j >> 1) & 1);
-      const HerkTask task = nxt;
-      if (j + 1 < n_my) nxt = my_task(a, j + 1);
       const bool got = mbar_wait(&sm.tmem_full[b], par, abort, budget) && mbar_wait(&sm.usum_full[b], par, abort, budget);
       if (!got) raise_timeout(a.status, abort);
       if (!named_bar_and(1, kEpiWarps * 32, got)) break;  // the drain warps leave together
       tc_after_sync();
+      const HerkTask task = my_task(a, j);
       const HerkInst in = task_inst(a, task);
       if (EIGHT)
         epilogue8(in, task, task_geom(task), sm.usum[b], tmem + (uint32_t)(b * 256), quad, part,
