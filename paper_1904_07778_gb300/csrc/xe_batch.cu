@@ -24,6 +24,9 @@ using namespace xe;
 struct corr_batch {
   int n = 0, bits = 4;
   unsigned flags = 0;
+  // every array is read in payload order (no corner turns; the kernel
+  // transposes as it unpacks)
+  bool tci = false;
   std::vector<corr_shape> shapes;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
@@ -165,16 +168,21 @@ HerkArgs batched_args(const corr_batch* b) {
   return a;
 }
 
+// Whether array k is corner-turned before the cross-multiply.
+bool turns(const corr_batch* b, int k) {
+  return !b->tci && needs_turn(b->shapes[k].layout, b->shapes[k].bits);
+}
+
 // Enqueue one run: every array's corner turn, then the batched launch.
 cudaError_t enqueue_batched(corr_batch* b) {
   for (int k = 0; k < b->n; ++k) {
     const corr_shape& sh = b->shapes[k];
-    if (!needs_turn(sh.layout, sh.bits)) continue;
+    if (!turns(b, k)) continue;
     cudaError_t e = turn_rows(b->input[k], b->turned[k], sh.layout, sh.bits, sh.n_inputs,
                               sh.n_chans, sh.n_time, b->insts[k].row_stride, b->stream);
     if (e != cudaSuccess) return e;
   }
-  return herk4_launch(batched_args(b), nullptr, b->n_tasks, b->stream);
+  return herk4_launch(batched_args(b), nullptr, b->n_tasks, b->stream, b->tci);
 }
 
 // Enqueue one pipelined run: the split array's ranges are turned one after
@@ -198,7 +206,7 @@ cudaError_t enqueue_pipelined(corr_batch* b) {
   }
   for (int q = 0; q < b->n; ++q) {
     const corr_shape& s = b->shapes[q];
-    if (q == k || !needs_turn(s.layout, s.bits)) continue;
+    if (q == k || !turns(b, q)) continue;
     if ((e = turn_rows(b->input[q], b->turned[q], s.layout, s.bits, s.n_inputs, s.n_chans,
                        s.n_time, b->insts[q].row_stride, b->stream)) != cudaSuccess)
       return e;
@@ -374,6 +382,8 @@ int corr_batch_create(const corr_shape* shapes, int n, void* stream, int tune, c
   b->bits = shapes[0].bits;
   b->flags = shapes[0].flags;
   b->shapes.assign(shapes, shapes + n);
+  b->tci = true;
+  for (int k = 0; k < n; ++k) b->tci = b->tci && tci_direct(shapes[k].layout, shapes[k].bits, shapes[k].n_inputs);
   int st = CORR_OK;
   do {
     // graphs cannot be captured on the legacy or per-thread default streams:
@@ -405,7 +415,7 @@ int corr_batch_create(const corr_shape* shapes, int n, void* stream, int tune, c
           cudaMalloc(&b->acc[k], nbl * s.n_chans * 16) != cudaSuccess) { st = CORR_ENOMEM; break; }
       long long stride = s.n_time;
       const uint8_t* x = b->input[k];
-      if (needs_turn(s.layout, s.bits)) {
+      if (turns(b, k)) {
         stride = ((long long)s.n_time + 31) / 32 * 32;
         if (cudaMalloc(&b->turned[k], (size_t)stride * R * s.n_chans) != cudaSuccess) { st = CORR_ENOMEM; break; }
         x = b->turned[k];
@@ -425,8 +435,12 @@ int corr_batch_create(const corr_shape* shapes, int n, void* stream, int tune, c
       in.rows_per_chan = rpc;
       in.accumulate = 0;
       in.vec_ok = 1;
-      if (!make_sample_tmap(&b->tmaps[k], x, s.n_time, stride, R, s.n_chans, rpc ? rpc / 2 : 64,
-                            rpc ? 128 / rpc : 1)) { st = CORR_ECUDA; break; }
+      const bool mapped =
+          b->tci ? make_tci_tmap(&b->tmaps[k], x, R, s.n_chans, s.n_time, rpc ? rpc / 2 : 64,
+                                 rpc ? 128 / rpc : 1)
+                 : make_sample_tmap(&b->tmaps[k], x, s.n_time, stride, R, s.n_chans,
+                                    rpc ? rpc / 2 : 64, rpc ? 128 / rpc : 1);
+      if (!mapped) { st = CORR_ECUDA; break; }
       b->n_tasks_one[k] = (int)t.size();
       b->max_nblk_one[k] = tasks_max_nblk(t);
       if (cudaMalloc(&b->d_tasks_one[k], sizeof(HerkTask) * t.size()) != cudaSuccess) { st = CORR_ENOMEM; break; }
@@ -518,7 +532,7 @@ int corr_batch_run_plain(corr_batch* b) {
   if (!b) return CORR_EINVAL;
   for (int k = 0; k < b->n; ++k) {
     const corr_shape& sh = b->shapes[k];
-    if (needs_turn(sh.layout, sh.bits) &&
+    if (turns(b, k) &&
         turn_rows(b->input[k], b->turned[k], sh.layout, sh.bits, sh.n_inputs, sh.n_chans,
                   sh.n_time, b->insts[k].row_stride, b->stream) != cudaSuccess)
       return CORR_ECUDA;
@@ -531,7 +545,7 @@ int corr_batch_run_plain(corr_batch* b) {
     a.bits = b->bits;
     a.n_tasks = b->n_tasks_one[k];
     a.max_nblk = b->max_nblk_one[k];
-    if (herk4_launch(a, &b->tmaps[k], a.n_tasks, b->stream) != cudaSuccess) return CORR_ECUDA;
+    if (herk4_launch(a, &b->tmaps[k], a.n_tasks, b->stream, b->tci) != cudaSuccess) return CORR_ECUDA;
   }
   return CORR_OK;
 }
@@ -556,7 +570,7 @@ int corr_batch_set_pipeline(corr_batch* b, int turn_sms, int n_chunks) {
       k = q;
     }
   }
-  if (k < 0) return CORR_EINVAL;
+  if (k < 0 || b->tci) return CORR_EINVAL;  // no corner turn to overlap
   const corr_shape& sh = b->shapes[k];
   // ranges start on whole 128-byte tiles of the input rows: channel c0 starts
   // at byte c0 of a [t][i][c] row and at byte c0 N of a [t][c][i] row
@@ -653,12 +667,12 @@ int corr_batch_info_get(corr_batch* b, corr_batch_info* out) {
   out->n_tasks = b->n_tasks;
   out->n_ctas = b->n_ctas;
   int launches = 1;
-  for (const corr_shape& s : b->shapes) launches += needs_turn(s.layout, s.bits) ? 1 : 0;
+  for (int q = 0; q < b->n; ++q) launches += turns(b, q) ? 1 : 0;
   if (b->pipe_sms > 0) {  // the split array: one turn and one cross-multiply per range
     const int nch = (int)b->pipe_c.size() - 1;
     launches = 2 * nch;
     for (int q = 0; q < b->n; ++q)
-      if (q != b->pipe_inst && needs_turn(b->shapes[q].layout, b->shapes[q].bits)) ++launches;
+      if (q != b->pipe_inst && turns(b, q)) ++launches;
     if (b->n_pipe_tasks[0] > 0) ++launches;
   }
   out->launches_per_run = launches;

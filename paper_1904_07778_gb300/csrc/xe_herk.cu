@@ -146,6 +146,47 @@ __device__ __forceinline__ void publish_row_sums(int32_t (&sre)[NI], int32_t (&s
   }
 }
 
+// ---- payload-order ([t][c][i]) stages -------------------------------------
+// A stage of a block read straight from the payload order is [t][64 bytes]:
+// 128 spectra of 64 byte rows (the inputs of one block, or of the stacked
+// channels).  The unpack gathers each row's bytes across time with 32-bit
+// shared loads and 4 x 4 byte transposes.  Within a stage the operands'
+// K order is a permutation of time -- the same for every row, so the Gram
+// matrix and the row sums are unchanged: K position 16 c + j holds spectrum
+// tci_t(c, j), which makes both the gathers and the operand stores free of
+// bank conflicts (lanes 2q and 2q + 1 of a warp read opposite parities).
+__device__ __forceinline__ int tci_t(int c, int j) { return 32 * (c >> 1) + 2 * j + (c & 1); }
+
+__device__ __forceinline__ uint32_t lds32(uint32_t addr) {
+  uint32_t v;
+  asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void transpose4x4b(uint32_t& a0, uint32_t& a1, uint32_t& a2,
+                                              uint32_t& a3) {
+  const uint32_t t0 = __byte_perm(a0, a1, 0x5140), t1 = __byte_perm(a0, a1, 0x7362);
+  const uint32_t t2 = __byte_perm(a2, a3, 0x5140), t3 = __byte_perm(a2, a3, 0x7362);
+  a0 = __byte_perm(t0, t2, 0x5410);
+  a1 = __byte_perm(t0, t2, 0x7632);
+  a2 = __byte_perm(t1, t3, 0x5410);
+  a3 = __byte_perm(t1, t3, 0x7632);
+}
+
+// Masks of the 16 bytes (K positions 16 c .. 16 c + 15) of chunk c in a stage
+// starting at spectrum tk of a launch of tn spectra.
+__device__ __forceinline__ void tci_keep(int c, int tk, int tn, uint32_t (&keep)[4]) {
+  const int lim = tn - tk - 32 * (c >> 1) - (c & 1);  // byte j is valid if 2 j < lim
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    uint32_t m = 0;
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+      if (2 * (4 * q + b) < lim) m |= 0xFFu << (8 * b);
+    keep[q] = m;
+  }
+}
+
 // MMA issue loop (one thread): stage k of the operand ring holds the B rows
 // in slots 0..nb-1 (contiguous) and the A rows in slot a_slot.
 __device__ __forceinline__ void mma_loop(const TaskGeom& g, int nk, int nst, uint32_t ops_addr,
@@ -499,7 +540,9 @@ __device__ __forceinline__ int stages_of(const HerkInst& in) {
   return (in.tn + kRStageT - 1) / kRStageT;
 }
 
-template <bool LO_IS_REAL, bool EIGHT>
+// TCI: the tensor maps describe payload-order blocks ({byte row, channel,
+// time}, boxes of 64 byte rows x 128 spectra) and the unpack transposes.
+template <bool LO_IS_REAL, bool EIGHT, bool TCI>
 __global__ void __launch_bounds__(kRingThreads, 1)
     herk4_ring_kernel(const __grid_constant__ CUtensorMap tmap, const HerkArgs a) {
   extern __shared__ uint8_t dyn_raw[];
@@ -585,10 +628,11 @@ __global__ void __launch_bounds__(kRingThreads, 1)
           mbar_expect_tx(&sm.full_t[s], (uint32_t)(g.nblk * kRPkBlock));
           for (int b = 0; b < g.nblk; ++b) {
             const uint32_t dst = dst0 + (uint32_t)(b * kRPkBlock);
-            if (stacked)
-              tma_load_3d(dst, tm, t, 0, task.chan0, &sm.full_t[s]);
+            const int row0 = stacked ? 0 : 64 * slot_block(g, b);
+            if (TCI)
+              tma_load_3d(dst, tm, row0, task.chan0, t, &sm.full_t[s]);
             else
-              tma_load_3d(dst, tm, t, 64 * slot_block(g, b), task.chan0, &sm.full_t[s]);
+              tma_load_3d(dst, tm, t, row0, task.chan0, &sm.full_t[s]);
           }
         }
         ++issued;
@@ -653,6 +697,9 @@ __global__ void __launch_bounds__(kRingThreads, 1)
     const int grp = warp / kGroupWarps;
     const int gt = tid - grp * kGroupThreads;
     const int chunk = gt % kRChunks, g8 = gt / kRChunks;  // this thread's chunk and pair
+    // payload order: quad of byte rows and K chunk of this thread's items
+    const int tq = lane >> 1, tc = (lane + 2 * (gt >> 5)) & 7;
+    static_assert(!TCI || (kGroupThreads == 128 && kRStageT == 128), "payload order: 4-warp groups");
     const uint32_t src0 = ring_addr + (uint32_t)(kRStageT * g8 + 16 * chunk);
     // rows 2 g8 and 2 g8 + 1; later items add whole 8-row atoms, so the
     // swizzle position stays the same
@@ -681,8 +728,52 @@ __global__ void __launch_bounds__(kRingThreads, 1)
                    mbar_wait(&sm.full_t[s], (uint32_t)(m & 1), abort, budget);
         if (!got) raise_timeout(a.status, abort);
         const uint32_t so = (uint32_t)(s * slot_bytes);
-        const uint32_t src = src0 + so + (uint32_t)(g.nblk * kRPkBlock);
         const bool tail = (k + 1) * kRStageT > tn;
+        if constexpr (TCI) {
+          // item (quad tq, chunk tc) of every block: 4 byte rows x 16 spectra
+          uint32_t wv[kMaxBlocks][16];
+          const uint32_t pk = ring_addr + so + (uint32_t)(g.nblk * kRPkBlock + 4 * tq);
+#pragma unroll
+          for (int it = 0; it < kMaxBlocks; ++it)
+            if (it < g.nblk && got)
+#pragma unroll
+              for (int jj = 0; jj < 16; ++jj)
+                wv[it][jj] = lds32(pk + (uint32_t)(it * kRPkBlock + tci_t(tc, jj) * 64));
+          // every packed byte of the stage is in registers before any is
+          // overwritten; the group leaves together if any of its waits failed
+          if (!named_bar_and(2 + grp, kGroupThreads, got)) {
+            ok = false;
+            break;
+          }
+          uint32_t keep[4] = {~0u, ~0u, ~0u, ~0u};
+          if (tail) tci_keep(tc, k * kRStageT, tn, keep);
+#pragma unroll
+          for (int it = 0; it < kMaxBlocks; ++it) {
+            if (it < g.nblk) {
+#pragma unroll
+              for (int gg = 0; gg < 4; ++gg)
+                transpose4x4b(wv[it][4 * gg], wv[it][4 * gg + 1], wv[it][4 * gg + 2], wv[it][4 * gg + 3]);
+              const uint32_t ob = ring_addr + so + (uint32_t)(it * kROpBlock);
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                const uint32_t w[4] = {wv[it][u], wv[it][4 + u], wv[it][8 + u], wv[it][12 + u]};
+                uint32_t re[4], im[4];
+                unpack16<LO_IS_REAL, true, EIGHT>(w, keep, re, im, sre[4 * it + u], sim[4 * it + u]);
+                if (EIGHT) {
+#pragma unroll
+                  for (int q = 0; q < 4; ++q) {  // any valid byte equal to 0x80?
+                    const uint32_t z = (w[q] ^ 0x80808080u) | ~keep[q];
+                    bad |= (z - 0x01010101u) & ~z & 0x80808080u;
+                  }
+                }
+                const int r = 2 * (4 * tq + u);
+                sts128(ob + op_offset(r, tc), re[0], re[1], re[2], re[3]);
+                sts128(ob + op_offset(r + 1, tc), im[0], im[1], im[2], im[3]);
+              }
+            }
+          }
+        } else {
+        const uint32_t src = src0 + so + (uint32_t)(g.nblk * kRPkBlock);
         uint32_t keep[4] = {~0u, ~0u, ~0u, ~0u};
         if (tail) time_keep(k * kRStageT + chunk * 16, tn, keep);
         uint4 v[kItems];
@@ -714,6 +805,7 @@ __global__ void __launch_bounds__(kRingThreads, 1)
             sts128(dst_im + o, im[0], im[1], im[2], im[3]);
           }
         }
+        }
         fence_smem_to_async();
         __syncwarp();
         if (lane == 0) mbar_arrive(&sm.full_o[s]);
@@ -728,7 +820,25 @@ __global__ void __launch_bounds__(kRingThreads, 1)
       const bool freed = j < 2 || mbar_wait(&sm.usum_empty[b], (uint32_t)(((j >> 1) - 1) & 1), abort, budget);
       if (!freed) raise_timeout(a.status, abort);
       if (!named_bar_and(2 + grp, kGroupThreads, freed)) break;
-      publish_row_sums<kGroupThreads, kItems, kRChunks>(sre, sim, nit, gt, sm.usum[b]);
+      if constexpr (TCI) {
+        // the two lanes of a quad in a warp add, then one adds per warp
+#pragma unroll
+        for (int it = 0; it < kMaxBlocks; ++it) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            if (it < g.nblk) {
+              const int r = sre[4 * it + u] + __shfl_xor_sync(0xFFFFFFFFu, sre[4 * it + u], 1);
+              const int mm = sim[4 * it + u] + __shfl_xor_sync(0xFFFFFFFFu, sim[4 * it + u], 1);
+              if ((lane & 1) == 0) {
+                atomicAdd(&sm.usum[b][it * 128 + 2 * (4 * tq + u)], r);
+                atomicAdd(&sm.usum[b][it * 128 + 2 * (4 * tq + u) + 1], mm);
+              }
+            }
+          }
+        }
+      } else {
+        publish_row_sums<kGroupThreads, kItems, kRChunks>(sre, sim, nit, gt, sm.usum[b]);
+      }
       __syncwarp();
       if (lane == 0) mbar_arrive(&sm.usum_full[b]);
       S0 = S1;
@@ -917,23 +1027,26 @@ cudaError_t set_smem(K kernel, int bytes) {
 int ring_smem() {
   static int m = -1;
   if (m < 0)
-    m = std::min(std::min(max_dyn_smem((const void*)herk4_ring_kernel<false, false>),
-                          max_dyn_smem((const void*)herk4_ring_kernel<true, false>)),
-                 max_dyn_smem((const void*)herk4_ring_kernel<false, true>));
+    m = std::min(std::min(max_dyn_smem((const void*)herk4_ring_kernel<false, false, false>),
+                          max_dyn_smem((const void*)herk4_ring_kernel<true, false, false>)),
+                 max_dyn_smem((const void*)herk4_ring_kernel<false, true, false>));
+    m = std::min(m, std::min(std::min(max_dyn_smem((const void*)herk4_ring_kernel<false, false, true>),
+                                      max_dyn_smem((const void*)herk4_ring_kernel<true, false, true>)),
+                             max_dyn_smem((const void*)herk4_ring_kernel<false, true, true>)));
   return m;
 }
 
-template <bool LO, bool EIGHT>
+template <bool LO, bool EIGHT, bool TCI>
 cudaError_t ring_launch(const HerkArgs& a, const CUtensorMap* tmap, int grid, cudaStream_t s) {
   // the attribute persists: set it once, so that launches captured into a
   // CUDA graph are plain stream work
   static int set_bytes = -1;
   if (set_bytes != a.smem_bytes) {
-    cudaError_t e = set_smem(herk4_ring_kernel<LO, EIGHT>, a.smem_bytes);
+    cudaError_t e = set_smem(herk4_ring_kernel<LO, EIGHT, TCI>, a.smem_bytes);
     if (e != cudaSuccess) return e;
     set_bytes = a.smem_bytes;
   }
-  herk4_ring_kernel<LO, EIGHT><<<grid, kRingThreads, a.smem_bytes, s>>>(*tmap, a);
+  herk4_ring_kernel<LO, EIGHT, TCI><<<grid, kRingThreads, a.smem_bytes, s>>>(*tmap, a);
   return cudaGetLastError();
 }
 
@@ -948,7 +1061,7 @@ int herk4_max_smem() {
 }
 
 cudaError_t herk4_launch(const HerkArgs& args, const CUtensorMap* tmap, int n_tasks,
-                         cudaStream_t s) {
+                         cudaStream_t s, bool tci) {
   cudaError_t e;
   if (tmap || args.tmaps) {
     HerkArgs a = args;
@@ -969,12 +1082,17 @@ cudaError_t herk4_launch(const HerkArgs& args, const CUtensorMap* tmap, int n_ta
     if (grid < 1) return cudaSuccess;
     static const CUtensorMap unused{};  // batched launches read their maps from a.tmaps
     const CUtensorMap* m = tmap ? tmap : &unused;
-    if (a.bits == 8) return ring_launch<false, true>(a, m, grid, s);
-    return a.lo_is_real ? ring_launch<true, false>(a, m, grid, s)
-                        : ring_launch<false, false>(a, m, grid, s);
+    if (tci) {
+      if (a.bits == 8) return ring_launch<false, true, true>(a, m, grid, s);
+      return a.lo_is_real ? ring_launch<true, false, true>(a, m, grid, s)
+                          : ring_launch<false, false, true>(a, m, grid, s);
+    }
+    if (a.bits == 8) return ring_launch<false, true, false>(a, m, grid, s);
+    return a.lo_is_real ? ring_launch<true, false, false>(a, m, grid, s)
+                        : ring_launch<false, false, false>(a, m, grid, s);
   }
   const HerkArgs& a = args;
-  if (a.bits != 4) return cudaErrorInvalidValue;  // 8-bit rows are always TMA-aligned
+  if (a.bits != 4 || tci) return cudaErrorInvalidValue;  // 8-bit rows and payload order take TMA
   if (a.lo_is_real) {
     if ((e = set_smem(herk4_ldg_kernel<true>, a.smem_bytes)) != cudaSuccess) return e;
     herk4_ldg_kernel<true><<<n_tasks, kLdgThreads, a.smem_bytes, s>>>(a);

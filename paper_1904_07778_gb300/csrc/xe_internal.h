@@ -101,7 +101,20 @@ int herk_ring_stage();
 // describes a.in.x as a 3-D byte tensor {time (inner), byte row, channel} for
 // the ring kernel, or is null for the kernel that loads with plain global
 // loads (any alignment).
-cudaError_t herk4_launch(const HerkArgs& a, const CUtensorMap* tmap, int n_tasks, cudaStream_t s);
+// With tci the tensor maps describe payload-order ([t][c][i]) blocks
+// (make_tci_tmap) and the kernel transposes while it unpacks.
+cudaError_t herk4_launch(const HerkArgs& a, const CUtensorMap* tmap, int n_tasks, cudaStream_t s,
+                         bool tci = false);
+
+// Tensor map of a payload-order block [t][c][r] of R byte rows per (spectrum,
+// channel) (R a multiple of 16, base 16-byte aligned) for the payload-order
+// kernel: dims {R, C, T}, box {box_rows, box_chans, herk_ring_stage()} with
+// box_rows x box_chans = 64 byte rows.  Returns false if the driver rejects it.
+bool make_tci_tmap(CUtensorMap* m, const uint8_t* x, int R, int n_chans, int n_time, int box_rows,
+                   int box_chans);
+// Whether a block of this layout and width can be read in payload order
+// (no corner turn): [t][c][i] with R = N bits / 4 byte rows a multiple of 16.
+bool tci_direct(int layout, int bits, int n_inputs);
 
 // Build the tensor map of a [channel][input][time] byte array with rows of
 // row_stride bytes (a multiple of 16, base 16-byte aligned).  Box:

@@ -87,6 +87,7 @@ struct Req {
   int R = 0;                     // byte rows per channel
   size_t block_bytes = 0, acc_bytes = 0, turn_bytes = 0;
   bool has_turn = false;
+  bool tci = false;  // blocks read in payload order (no corner turn)
   long long stride = 0;
   // arena offsets of the pieces (valid while admitted)
   size_t off_acc = 0, off_in[2] = {0, 0}, off_turn = 0;
@@ -199,8 +200,12 @@ void admit(corr_svc* s) {
     if (!s->dry) {
       for (int b = 0; b < 2; ++b) {
         const uint8_t* x = q.has_turn ? s->base + q.off_turn : s->base + q.off_in[b];
-        make_sample_tmap(&q.tmap[b], x, q.r.block_spectra, q.stride, q.R, q.r.n_chans,
-                         q.rpc ? q.rpc / 2 : 64, q.rpc ? 128 / q.rpc : 1);
+        if (q.tci)
+          make_tci_tmap(&q.tmap[b], x, q.R, q.r.n_chans, q.r.block_spectra, q.rpc ? q.rpc / 2 : 64,
+                        q.rpc ? 128 / q.rpc : 1);
+        else
+          make_sample_tmap(&q.tmap[b], x, q.r.block_spectra, q.stride, q.R, q.r.n_chans,
+                           q.rpc ? q.rpc / 2 : 64, q.rpc ? 128 / q.rpc : 1);
         if (!q.ev_copy[b]) cudaEventCreateWithFlags(&q.ev_copy[b], cudaEventDisableTiming);
         if (!q.ev_used[b]) cudaEventCreateWithFlags(&q.ev_used[b], cudaEventDisableTiming);
       }
@@ -296,7 +301,8 @@ int corr_svc_submit(corr_svc* s, const corr_req* r, int64_t* id) {
   q->R = r->n_inputs * (r->bits / 4);
   q->block_bytes = (size_t)q->R * r->n_chans * r->block_spectra;
   q->acc_bytes = (size_t)r->n_inputs * (r->n_inputs + 1) / 2 * r->n_chans * 16;
-  q->has_turn = needs_turn(r->layout, r->bits);
+  q->tci = tci_direct(r->layout, r->bits, r->n_inputs);
+  q->has_turn = needs_turn(r->layout, r->bits) && !q->tci;
   q->stride = q->has_turn ? ((long long)r->block_spectra + 31) / 32 * 32 : r->block_spectra;
   q->turn_bytes = q->has_turn ? (size_t)q->stride * q->R * r->n_chans : 0;
   if (req_bytes(*q) > s->arena.cap) return CORR_EBUSY;
@@ -383,13 +389,16 @@ int corr_svc_tick(corr_svc* s, int* n_requests) {
       I.vec_ok = 1;
       s->h_tmaps[p][inst] = q->tmap[b];
     }
-    // one launch per (sample width, nibble order); tasks longest first
-    struct Cls { int bits, lo; std::vector<Req*> qs; };
+    // one launch per (sample width, nibble order, payload order read directly);
+    // tasks longest first
+    struct Cls { int bits, lo; bool tci; std::vector<Req*> qs; };
     std::vector<Cls> cls;
     for (Req* q : parts) {
       const int lo = (q->r.flags & CORR_F_LO_IS_REAL) ? 1 : 0;
-      auto c = std::find_if(cls.begin(), cls.end(), [&](const Cls& x) { return x.bits == q->r.bits && x.lo == lo; });
-      if (c == cls.end()) cls.push_back({q->r.bits, lo, {q}});
+      auto c = std::find_if(cls.begin(), cls.end(), [&](const Cls& x) {
+        return x.bits == q->r.bits && x.lo == lo && x.tci == q->tci;
+      });
+      if (c == cls.end()) cls.push_back({q->r.bits, lo, q->tci, {q}});
       else c->qs.push_back(q);
     }
     size_t ntask = 0;
@@ -399,7 +408,7 @@ int corr_svc_tick(corr_svc* s, int* n_requests) {
     if (!ensure(s->d_tasks[p], s->h_tasks[p], s->task_cap[p], ntask) ||
         !ensure(s->d_first[p], s->h_first[p], s->first_cap[p], cls.size() * (nsm + 1)))
       return CORR_ENOMEM;
-    struct Launch { size_t t0, f0; int nt, nc, max_nblk, bits, lo; };
+    struct Launch { size_t t0, f0; int nt, nc, max_nblk, bits, lo; bool tci; };
     std::vector<Launch> ls;
     size_t tpos = 0, fpos = 0;
     for (auto& c : cls) {
@@ -421,7 +430,7 @@ int corr_svc_tick(corr_svc* s, int* n_requests) {
       std::vector<int> order(nt);
       corr_plan_schedule(cost.data(), nt, nc, order.data(), s->h_first[p] + fpos);
       for (int j = 0; j < nt; ++j) s->h_tasks[p][tpos + j] = all[order[j]];
-      ls.push_back({tpos, fpos, nt, nc, mx, c.bits, c.lo});
+      ls.push_back({tpos, fpos, nt, nc, mx, c.bits, c.lo, c.tci});
       tpos += nt;
       fpos += nc + 1;
     }
@@ -447,7 +456,7 @@ int corr_svc_tick(corr_svc* s, int* n_requests) {
       a.n_tasks = l.nt;
       a.max_nblk = l.max_nblk;
       a.grid = l.nc;
-      if (herk4_launch(a, nullptr, l.nt, s->stream) != cudaSuccess) return CORR_ECUDA;
+      if (herk4_launch(a, nullptr, l.nt, s->stream, l.tci) != cudaSuccess) return CORR_ECUDA;
       ++launches;
     }
     if (cudaEventRecord(s->ev_tick[p], s->stream) != cudaSuccess) return CORR_ECUDA;

@@ -68,6 +68,28 @@ def test_batch_graph_replays_and_plain_form(xe, shapes):
         assert info["launches_per_run"] == 1 + sum(1 for s in shapes if s[4] != 2 or s[3] == 8)
 
 
+PAYLOAD4 = [(32, 64, 1024, 4, 0), (64, 48, 512, 4, 0), (192, 6, 256, 4, 0), (16, 20, 300, 4, 0)]
+PAYLOAD8 = [(16, 8, 128, 8, 0), (48, 4, 256, 8, 0), (192, 2, 96, 8, 0)]
+
+
+@pytest.mark.parametrize("shapes", [PAYLOAD4, PAYLOAD8], ids=["4bit", "8bit"])
+def test_batch_read_in_payload_order(xe, shapes):
+    """Every array in [t][c][i] with rows that suit TMA: no corner turns, the
+    batched kernel transposes as it unpacks -- one launch per run."""
+    with xe.Batch(shapes) as b:
+        assert b.info()["launches_per_run"] == 1
+        for rep in range(2):
+            blocks = _blocks(shapes, 700 + rep)
+            for k, blk in enumerate(blocks):
+                b.set_input(k, blk)
+            if rep == 0:
+                b.run()
+            else:
+                b.run_plain()
+            assert b.sync() == xe.CORR_OK
+            _check(b, shapes, blocks)
+
+
 def test_batch_autotune_every_schedule_exact(xe):
     blocks = _blocks(SHAPES4, 300)
     with xe.Batch(SHAPES4, tune=True) as b:

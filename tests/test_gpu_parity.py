@@ -56,6 +56,24 @@ def test_random_codes_bit_exact(xe, N, C, T, layout):
     assert np.array_equal(got, _oracle([blk], N, C, T, layout))
 
 
+PAYLOAD_SHAPES = [
+    # (N, C, T): [t][c][i] blocks read in payload order (16, 32 inputs stacked;
+    # 64 or more in 64-row boxes), ragged spectrum counts, odd channel counts
+    (16, 7, 77), (16, 9, 256), (32, 5, 200), (32, 3, 1), (64, 3, 130), (128, 2, 129),
+    (192, 2, 300), (256, 1, 513), (80, 3, 160),
+]
+
+
+@pytest.mark.parametrize("N,C,T", PAYLOAD_SHAPES)
+@pytest.mark.parametrize("lo", [False, True])
+def test_payload_order_read_directly(xe, N, C, T, lo):
+    """[t][c][i] blocks whose rows suit TMA are cross-multiplied without a
+    corner turn: the kernel gathers each input's bytes across time itself."""
+    blk = synth.random_bytes(3000 + N * 10 + C + T, N * C * T)
+    got = _run(xe, [blk, blk[::-1].copy()], N, C, T, 0, lo_is_real=lo, device_input=not lo)
+    assert np.array_equal(got, _oracle([blk, blk[::-1].copy()], N, C, T, 0, lo_is_real=lo))
+
+
 @pytest.mark.parametrize("lo", [False, True])
 def test_nibble_order(xe, lo):
     N, C, T = 8, 4, 64
@@ -240,8 +258,9 @@ def _run8(xe, blocks, N, C, T, layout, device_input=True):
 
 SHAPES8 = [
     # (N, C, T): stacked (4N <= 64), one block, several blocks, even and odd block counts
-    (1, 3, 5), (2, 5, 130), (7, 4, 257), (16, 3, 256), (17, 2, 100), (32, 2, 384),
-    (33, 2, 200), (48, 2, 129), (64, 2, 256), (100, 1, 300), (192, 1, 160),
+    # (8, 16, 32, 48, 64, 192 inputs in [t][c][i] are read in payload order)
+    (1, 3, 5), (2, 5, 130), (7, 4, 257), (8, 5, 99), (16, 3, 256), (17, 2, 100), (32, 2, 384),
+    (33, 2, 200), (48, 2, 129), (64, 2, 256), (100, 1, 300), (192, 1, 160), (192, 2, 77),
 ]
 
 

@@ -14,12 +14,15 @@ R4 = dict(n_inputs=32, n_chans=64, bits=4, layout=0, block_spectra=1024)
 
 def _bytes(n, c, bits, layout, t):
     """Device state of one request: int64 accumulator, two ingest buffers, the
-    corner-turn buffer (rows padded to 32 bytes), each rounded to 256 bytes."""
+    corner-turn buffer (rows padded to 32 bytes), each rounded to 256 bytes.
+    No turn buffer for [c][i][t] 4-bit blocks, nor for [t][c][i] blocks read in
+    payload order (byte rows per channel 16, 32 or a multiple of 16 from 64 to 384)."""
     r = lambda x: (x + 255) // 256 * 256
     rows = n * bits // 4
     acc = n * (n + 1) // 2 * c * 16
     blk = rows * c * t
-    turn = 0 if (layout == 2 and bits == 4) else rows * c * ((t + 31) // 32 * 32)
+    direct = layout == 0 and rows % 16 == 0 and (rows in (16, 32) or 64 <= rows <= 384)
+    turn = 0 if (layout == 2 and bits == 4) or direct else rows * c * ((t + 31) // 32 * 32)
     return r(acc) + 2 * r(blk) + r(turn)
 
 
