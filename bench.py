@@ -536,10 +536,22 @@ def run_gpu(args, w, world, rank, local):
     # a tensor-bound kernel confined to part of the GPU, also against that
     # part's share of the peak (HBM bandwidth does not divide by SMs)
     herk["frac_of_its_sms"] = herk["frac"] * n_sm / herk["sms"]
+    if N <= 32 and d["timed_turn"] == 0:
+        # the dish sizes (4 (N + 1) ops per input byte) are bounded by HBM: the
+        # cross-multiply reads the payload-order block itself, so its roofline is
+        # the block's bytes (plus the int64 visibilities it writes or adds) over
+        # its launch time, against the measured copy bandwidth
+        herk_bytes = N * C * T + (2 if per_dump > 1 else 1) * nb * C * 16 / per_dump
+        herk.update({"bound": "hbm", "unit": "GB/s", "achieved": herk_bytes / (herk_avg * 1e-3) / 1e9,
+                     "peak": pk["hbm"], "peak_note": "%s HBM copy" % pk["src"],
+                     "tensor_tflops": herk["achieved"], "tensor_frac": herk["frac"],
+                     "bytes_per_launch": herk_bytes})
+        herk["frac"] = herk["achieved"] / herk["peak"]
     dom = max(kernels, key=lambda k: k["avg_launch_ms"] * k["launches"])
     roof = {k: dom[k] for k in ("bound", "achieved", "peak", "unit", "frac", "traffic")}
     for k in ("executed_tflops", "executed_frac", "algorithmic_over_executed", "frac_of_its_sms",
-              "frac_of_sustained", "tensor_pipe_active_pct"):
+              "frac_of_sustained", "tensor_pipe_active_pct", "tensor_tflops", "tensor_frac",
+              "bytes_per_launch"):
         if k in dom:
             roof[k] = dom[k]
     roof["kernel"] = dom["kernel"]
@@ -559,6 +571,12 @@ def run_gpu(args, w, world, rank, local):
                         % (pipe, n_sm - pipe))
     ms_step = ms_max / args.steps
     value = world * ops_per_step(w) / (ms_step * 1e-3) / 1e12
+    # the input block's bytes over the whole step (each block is read from HBM
+    # at least once), against the measured copy bandwidth
+    in_bytes = N * C * T * per_dump
+    roof["input_bytes_over_step"] = {"bytes_per_step": in_bytes,
+                                     "gbs": in_bytes / (ms_step * 1e-3) / 1e9,
+                                     "frac": in_bytes / (ms_step * 1e-3) / 1e9 / pk["hbm"]}
     line = {
         "metric": xe_metric(N), "value": value, "unit": "Tops/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
