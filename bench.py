@@ -157,16 +157,25 @@ def kernel_traffic(name, launch_units, **shape):
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
+    d = _profile_entry(path, name, shape)
+    return None if d is None else d["dram_bytes"] * launch_units / d["units"]
+
+
+def _profile_entry(path, name, shape):
+    """The entry (or, of a list, the first entry) of a kernel in the committed
+    ncu summary whose source is unchanged and whose shape matches."""
     try:
-        d = json.load(open(path)).get(name)
-        src = open(os.path.join(ROOT, d["source"]), "rb").read()
-        if hashlib.sha256(src).hexdigest() != d["source_sha256"]:
-            return None
-        if any(k in d.get("shape", {}) and d["shape"][k] != v for k, v in shape.items()):
-            return None
-        return d["dram_bytes"] * launch_units / d["units"]
+        entries = json.load(open(path)).get(name)
+        for d in entries if isinstance(entries, list) else [entries]:
+            src = open(os.path.join(ROOT, d["source"]), "rb").read()
+            if hashlib.sha256(src).hexdigest() != d["source_sha256"]:
+                continue
+            if any(k in d.get("shape", {}) and d["shape"][k] != v for k, v in shape.items()):
+                continue
+            return d
     except Exception:
-        return None
+        pass
+    return None
 
 
 def kernel_metric(name, key, **shape):
@@ -176,16 +185,8 @@ def kernel_metric(name, key, **shape):
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
-    try:
-        d = json.load(open(path)).get(name)
-        src = open(os.path.join(ROOT, d["source"]), "rb").read()
-        if hashlib.sha256(src).hexdigest() != d["source_sha256"]:
-            return None
-        if any(k in d.get("shape", {}) and d["shape"][k] != v for k, v in shape.items()):
-            return None
-        return d.get(key)
-    except Exception:
-        return None
+    d = _profile_entry(path, name, shape)
+    return None if d is None else d.get(key)
 
 
 class ClockSampler:
@@ -530,7 +531,7 @@ def run_gpu(args, w, world, rank, local):
                 "unit": "GB/s", "sms": pipe or n_sm,
                 "achieved": tb / (turn_avg * 1e-3) / 1e9, "peak": pk["hbm"], "avg_launch_ms": turn_avg,
                 "launches": d["timed_turn"], "peak_note": "%s HBM copy" % pk["src"],
-                "traffic": kernel_traffic("turn_persist_kernel" if pipe else "turn_kernel", N * C * T)}
+                "traffic": None if pipe else kernel_traffic("turn_kernel", N * C * T)}
         turn["frac"] = turn["achieved"] / turn["peak"]
         kernels.append(turn)
     # a tensor-bound kernel confined to part of the GPU, also against that
