@@ -50,6 +50,8 @@ struct corr_batch {
   cudaGraphExec_t exec = nullptr;
   int* d_status = nullptr;
   int* h_status = nullptr;
+  int2* scratch = nullptr;  // 8-bit: per-CTA partial sums of the cross-multiply
+  int scratch_ctas = 0;
   // pipelined runs (corr_batch_set_pipeline): array pipe_inst is turned in
   // channel ranges pipe_c[j] .. pipe_c[j+1] on pipe_sms SMs of turn_stream;
   // task list 0 holds the other arrays' tasks, list 1 + j range j's
@@ -87,6 +89,7 @@ void free_batch(corr_batch* b) {
   cudaFree(b->d_tasks);
   cudaFree(b->d_cta_first);
   cudaFree(b->d_status);
+  cudaFree(b->scratch);
   if (b->h_status) cudaFreeHost(b->h_status);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
   delete b;
@@ -94,10 +97,11 @@ void free_batch(corr_batch* b) {
 
 // Cost of a task for the schedule: its stages times the 128-row blocks it
 // streams through shared memory (the unpack, not the MMA, bounds a stage).
-double task_cost(const HerkTask& t, const HerkInst& in) {
+double task_cost(const HerkTask& t, const HerkInst& in, int bits) {
   const int nb = t.cb[1] >= 0 ? 2 : 1;
   const bool a_in = t.rb == t.cb[0] || (nb == 2 && t.rb == t.cb[1]);
-  return (double)((in.tn + 127) / 128) * (a_in ? nb : nb + 1);
+  const int st = herk_ring_stage(bits);
+  return (double)((in.tn + st - 1) / st) * (a_in ? nb : nb + 1);
 }
 
 // Build and upload the batched task list of one schedule.
@@ -109,11 +113,11 @@ int build_schedule(corr_batch* b, int sched) {
     int rpc = 0;
     const corr_shape& sh = b->shapes[k];
     std::vector<HerkTask> t =
-        plan_tasks(sh.n_inputs * (sh.bits / 4), sh.n_chans, &rpc, sched == CORR_SCHED_SINGLES_LPT);
+        plan_tasks(sh.n_inputs, sh.n_chans, &rpc, sched == CORR_SCHED_SINGLES_LPT);
     max_nblk = std::max(max_nblk, tasks_max_nblk(t));
     for (HerkTask& x : t) {
       x.inst = k;
-      cost.push_back(task_cost(x, b->insts[k]));
+      cost.push_back(task_cost(x, b->insts[k], b->bits));
       all.push_back(x);
     }
   }
@@ -165,6 +169,8 @@ HerkArgs batched_args(const corr_batch* b) {
   a.n_tasks = b->n_tasks;
   a.max_nblk = b->max_nblk;
   a.grid = b->n_ctas;
+  a.scratch = b->scratch;
+  a.scratch_ctas = b->scratch_ctas;
   return a;
 }
 
@@ -398,6 +404,7 @@ int corr_batch_create(const corr_shape* shapes, int n, void* stream, int tune, c
     if (cudaMalloc(&b->d_status, sizeof(int)) != cudaSuccess) { st = CORR_ENOMEM; break; }
     if (cudaMemset(b->d_status, 0, sizeof(int)) != cudaSuccess) { st = CORR_ECUDA; break; }
     if (cudaMallocHost(&b->h_status, sizeof(int)) != cudaSuccess) { st = CORR_ENOMEM; break; }
+    if (b->bits == 8 && herk_scratch_alloc(&b->scratch, &b->scratch_ctas) != cudaSuccess) { st = CORR_ENOMEM; break; }
     b->input.assign(n, nullptr);
     b->turned.assign(n, nullptr);
     b->acc.assign(n, nullptr);
@@ -421,7 +428,7 @@ int corr_batch_create(const corr_shape* shapes, int n, void* stream, int tune, c
         x = b->turned[k];
       }
       int rpc = 0;
-      std::vector<HerkTask> t = plan_tasks(R, s.n_chans, &rpc);
+      std::vector<HerkTask> t = plan_tasks(s.n_inputs, s.n_chans, &rpc);
       HerkInst& in = b->insts[k];
       memset(&in, 0, sizeof(in));
       in.x = x;
@@ -435,12 +442,7 @@ int corr_batch_create(const corr_shape* shapes, int n, void* stream, int tune, c
       in.rows_per_chan = rpc;
       in.accumulate = 0;
       in.vec_ok = 1;
-      const bool mapped =
-          b->tci ? make_tci_tmap(&b->tmaps[k], x, R, s.n_chans, s.n_time, rpc ? rpc / 2 : 64,
-                                 rpc ? 128 / rpc : 1)
-                 : make_sample_tmap(&b->tmaps[k], x, s.n_time, stride, R, s.n_chans,
-                                    rpc ? rpc / 2 : 64, rpc ? 128 / rpc : 1);
-      if (!mapped) { st = CORR_ECUDA; break; }
+      if (!make_herk_tmap(&b->tmaps[k], x, b->tci, s.bits, R, s.n_chans, s.n_time, stride, rpc)) { st = CORR_ECUDA; break; }
       b->n_tasks_one[k] = (int)t.size();
       b->max_nblk_one[k] = tasks_max_nblk(t);
       if (cudaMalloc(&b->d_tasks_one[k], sizeof(HerkTask) * t.size()) != cudaSuccess) { st = CORR_ENOMEM; break; }
@@ -545,6 +547,8 @@ int corr_batch_run_plain(corr_batch* b) {
     a.bits = b->bits;
     a.n_tasks = b->n_tasks_one[k];
     a.max_nblk = b->max_nblk_one[k];
+    a.scratch = b->scratch;
+    a.scratch_ctas = b->scratch_ctas;
     if (herk4_launch(a, &b->tmaps[k], a.n_tasks, b->stream, b->tci) != cudaSuccess) return CORR_ECUDA;
   }
   return CORR_OK;
@@ -587,7 +591,7 @@ int corr_batch_set_pipeline(corr_batch* b, int turn_sms, int n_chunks) {
   for (int q = 0; q < b->n; ++q) {
     const corr_shape& s = b->shapes[q];
     int rpc = 0;
-    for (HerkTask x : plan_tasks(s.n_inputs * (s.bits / 4), s.n_chans, &rpc)) {
+    for (HerkTask x : plan_tasks(s.n_inputs, s.n_chans, &rpc)) {
       x.inst = q;
       int li = 0;
       if (q == k) {

@@ -1,19 +1,19 @@
 // X-engine cross-multiply-and-accumulate (Sec. 2 "CMAC"; Sec. 2.2) for
-// 4-bit complex samples on sm_103a tensor cores.
+// 4-bit and 8-bit complex samples on sm_103a tensor cores.
 //
 // Per channel, V_ij = sum_t x_i(t) conj(x_j(t)) for i >= j.  With Y the
 // real (2N x T) matrix whose row 2i is Re x_i and row 2i+1 is Im x_i, and
 // G = Y Y^T (symmetric), the visibilities are
 //     Re V_ij = G[2i][2j] + G[2i+1][2j+1],   Im V_ij = G[2i+1][2j] - G[2i][2j+1].
-// The kernels form 128 x 128 blocks of G with tcgen05.mma kind::f8f6f4
-// (E4M3 operands, FP32 accumulators in tensor memory), one or two column
-// blocks per task (128 x 128 or 128 x 256 MMAs).
+// The kernels form 128 x 128 blocks of G with tcgen05.mma (FP32 accumulators
+// in tensor memory), one or two column blocks per task (128 x 128 or
+// 128 x 256 MMAs).
 //
-// Operand encoding.  A 4-bit two's-complement nibble n (value v in -8..7)
-// is fed to the tensor core as the offset code u = n ^ 8 = v + 8 in 0..15.
-// The E4M3 byte with bit pattern u (exponent field 0 or 1) has the value
-// u * 2^-9 exactly, so unpacking a byte of two nibbles into two E4M3 bytes is
-// one mask and one XOR.  The tensor core then accumulates
+// 4-bit operands (kind::f8f6f4).  A 4-bit two's-complement nibble n (value
+// v in -8..7) is fed to the tensor core as the offset code u = n ^ 8 = v + 8
+// in 0..15.  The E4M3 byte with bit pattern u (exponent field 0 or 1) has
+// the value u * 2^-9 exactly, so unpacking a byte of two nibbles into two
+// E4M3 bytes is one mask and one XOR.  The tensor core then accumulates
 //     Gu[p][q] = 2^-18 sum_t u_p u_q,
 // exact in FP32 while the integer sum stays below 2^24 (at most 225 per
 // spectrum, so up to 65536 spectra per accumulation).  The signed Gram
@@ -22,16 +22,25 @@
 // Spectra outside the launch's time range use u = 0 and drop out of every
 // term; padded rows are computed but never written.
 //
+// 8-bit operands (kind::f16).  A byte in -127..127 is an FP16 value of the
+// same integer, so Y holds the samples themselves and G needs no
+// correction.  A product is at most 127^2 < 2^14, so an FP32 accumulation
+// stays exact over 1024 spectra (127^2 * 1024 < 2^24); longer tasks are
+// accumulated 1024 spectra at a time, and the drain adds the pieces as
+// integers.
+//
 // Kernels:
 //   herk4_ring_kernel (fast path) persistent, one CTA per SM: a TMA warp
 //       streams packed bytes into a ring of shared-memory slots, four groups
 //       of four warps unpack them in place into the 128-byte-swizzled K-major
 //       operand layout, one warp issues the MMAs into two alternating
-//       tensor-memory accumulators, and eight warps drain the previous task.
-//   herk4_ldg_kernel  (any alignment) four warps load with 16-byte or byte
-//       loads from global memory instead of TMA.
+//       tensor-memory accumulators, and eight warps drain the previous
+//       accumulation.
+//   herk4_ldg_kernel  (4-bit, any alignment) four warps load with 16-byte or
+//       byte loads from global memory instead of TMA.
 #include <algorithm>
 #include <cstring>
+#include <type_traits>
 
 #include "xe_device.cuh"
 
@@ -78,17 +87,16 @@ __device__ __forceinline__ uint32_t swz_offset(int row, int chunk) {
   return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + ((chunk ^ (row & 7)) << 4));
 }
 
-// Unpack 16 packed samples (4 words) into 16 real and 16 imaginary offset
-// codes and add them to the row sums; with MASK, `keep` zeroes samples
-// outside the time range.
-template <bool LO_IS_REAL, bool MASK, bool LO_UNSIGNED = false>
+// Unpack 16 packed 4-bit samples (4 words) into 16 real and 16 imaginary
+// offset codes and add them to the row sums; with MASK, `keep` zeroes
+// samples outside the time range.
+template <bool LO_IS_REAL, bool MASK>
 __device__ __forceinline__ void unpack16(const uint32_t (&w)[4], const uint32_t (&keep)[4],
                                          uint32_t (&re)[4], uint32_t (&im)[4], int32_t& sre,
                                          int32_t& sim) {
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    // 8-bit low nibbles are unsigned (0..15): their code is the nibble itself
-    uint32_t lo = (w[q] & 0x0F0F0F0Fu) ^ (LO_UNSIGNED ? 0u : 0x08080808u);
+    uint32_t lo = (w[q] & 0x0F0F0F0Fu) ^ 0x08080808u;
     uint32_t hi = ((w[q] >> 4) & 0x0F0F0F0Fu) ^ 0x08080808u;
     if (MASK) {
       lo &= keep[q];
@@ -100,6 +108,32 @@ __device__ __forceinline__ void unpack16(const uint32_t (&w)[4], const uint32_t 
   // bytes are <= 15, so four words add without carries between bytes
   sre = (int32_t)__dp4a(re[0] + re[1] + re[2] + re[3], 0x01010101u, (uint32_t)sre);
   sim = (int32_t)__dp4a(im[0] + im[1] + im[2] + im[3], 0x01010101u, (uint32_t)sim);
+}
+
+// a - b for two FP16 lanes
+__device__ __forceinline__ uint32_t f16x2_sub(uint32_t a, uint32_t b) {
+  uint32_t d;
+  asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+  return d;
+}
+
+// Sixteen 8-bit samples (4 little-endian words; `keep` zeroes samples outside
+// the time range) to sixteen FP16 values of the same integers, eight f16x2
+// words in sample order.  Byte b becomes the half with bit pattern
+// 0x6400 | (b ^ 0x80), whose value is 1024 + (v + 128), and 1152 is
+// subtracted in FP16: every operand and result is an integer below 2048 in
+// magnitude, so both steps are exact.  `bad` gets a bit if a kept byte is
+// 0x80 (-128, outside the symmetric range).
+__device__ __forceinline__ void s8_to_f16(const uint32_t (&w)[4], const uint32_t (&keep)[4],
+                                          uint32_t (&h)[8], uint32_t& bad) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const uint32_t z = (w[q] ^ 0x80808080u) | ~keep[q];  // a zero byte: a kept 0x80
+    bad |= (z - 0x01010101u) & ~z & 0x80808080u;
+    const uint32_t u = (w[q] & keep[q]) ^ 0x80808080u;
+    h[2 * q] = f16x2_sub(__byte_perm(u, 0x64646464u, 0x4140), 0x64806480u);
+    h[2 * q + 1] = f16x2_sub(__byte_perm(u, 0x64646464u, 0x4342), 0x64806480u);
+  }
 }
 
 __device__ __forceinline__ void store_pair(uint8_t* stage, int pair, int chunk,
@@ -187,6 +221,20 @@ __device__ __forceinline__ void tci_keep(int c, int tk, int tn, uint32_t (&keep)
   }
 }
 
+// 8-bit payload-order stages ([t][128 bytes], 64 spectra): a thread holds
+// byte j of its 16 gathered spectra at spectrum 16 c + (j ^ sw8) of the
+// stage; masks of those bytes for lim = valid spectra from the stage's start.
+__device__ __forceinline__ void tci8_keep(int c, int sw8, int lim, uint32_t (&keep)[4]) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    uint32_t m = 0;
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+      if (16 * c + ((4 * q + b) ^ sw8) < lim) m |= 0xFFu << (8 * b);
+    keep[q] = m;
+  }
+}
+
 // MMA issue loop (one thread): stage k of the operand ring holds the B rows
 // in slots 0..nb-1 (contiguous) and the A rows in slot a_slot.
 __device__ __forceinline__ void mma_loop(const TaskGeom& g, int nk, int nst, uint32_t ops_addr,
@@ -217,11 +265,11 @@ __device__ __forceinline__ void mma_loop(const TaskGeom& g, int nk, int nst, uin
   umma_commit(done);
 }
 
-// Drain the accumulators, correct the offset codes, fold 2 x 2 real blocks
-// into complex visibilities and store or add them into the int64
+// Drain the accumulators, correct the offset codes (4-bit), fold 2 x 2 real
+// blocks into complex visibilities and store or add them into the int64
 // integration buffer.  The calling warp reads tensor-memory lanes
 // 32 quad .. + 31 (rows of the A block; quad must be the warp index mod 4)
-// and the part-th of nparts shares of the 32-column chunks.  Column block
+// and the part-th of nparts shares of the 16-column chunks.  Column block
 // c < rb is a lower-triangle block, c == rb the diagonal block (entries
 // j <= i only), c > rb the transpose of block (c, rb): there the thread's
 // row is the second input of the baseline and the imaginary part changes
@@ -230,9 +278,17 @@ __device__ __forceinline__ void mma_loop(const TaskGeom& g, int nk, int nst, uin
 // chunk go to the lane of row 2i, the odd ones to row 2i + 1, and each
 // visibility is one 16-byte store (adjacent lanes fill 32 contiguous bytes
 // in lower blocks, 16 lanes fill 256 contiguous bytes in upper blocks).
+//
+// F16 (8-bit samples): the accumulators hold G itself.  A task is drained
+// once per accumulation of at most 1024 spectra; every accumulation but the
+// last leaves its int32 visibilities in the CTA's scratch (int2 per
+// position, entry (4 cc + u) 128 + p, written and read by the same thread),
+// which the next one adds in, and the last goes to the integration buffer.
+// The int32 sums stay below 2 * 127^2 * 32768 < 2^31 for the longest block.
+template <bool F16>
 __device__ __forceinline__ void epilogue(const HerkInst& a, const HerkTask& task, const TaskGeom& g,
                                          const int32_t* usum, uint32_t tmem, int quad, int part,
-                                         int nparts, int lane) {
+                                         int nparts, int lane, bool first, bool last, int2* scr) {
   const bool stacked = a.rows_per_chan > 0;
   const int p = quad * 32 + lane;
   const int n = a.n_inputs;
@@ -252,19 +308,26 @@ __device__ __forceinline__ void epilogue(const HerkInst& a, const HerkTask& task
     plane = prow & 1;
     row_ok = i < n;
   }
-  const int base_term = 64 * a.tn - 8 * usum[g.a_slot * 128 + p];
+  const int base_term = F16 ? 0 : 64 * a.tn - 8 * usum[g.a_slot * 128 + p];
   const long long nbl = (long long)n * (n + 1) / 2;
   int64_t* chp = a.acc + (long long)(row_ok ? ch : 0) * nbl * 2;
   const int tri_i = i * (i + 1) / 2;  // baselines per channel stay below 2^30 (inputs <= 32768)
   const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16);
   const int nch = g.nb * 8, per = nch / nparts;  // 16-column chunks
   for (int cc = part * per; cc < (part + 1) * per; ++cc) {
+    int2 prev[4];
+    int2* sp = scr + (cc * 4) * 128 + p;
+    if (F16 && !first) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) prev[u] = sp[u * 128];
+    }
     uint32_t r[16];
     tmem_load16(trow + (uint32_t)(cc * 16), r);
     int gv[16];
 #pragma unroll
     for (int k = 0; k < 16; ++k)
-      gv[k] = __float2int_rn(__uint_as_float(r[k]) * 262144.0f) + base_term - 8 * usum[cc * 16 + k];
+      gv[k] = F16 ? __float2int_rn(__uint_as_float(r[k]))
+                  : __float2int_rn(__uint_as_float(r[k]) * 262144.0f) + base_term - 8 * usum[cc * 16 + k];
     const int cblk = slot_block(g, cc >> 3);
     const bool upper = !stacked && cblk > task.rb;
     int vre[4], vim[4];
@@ -299,6 +362,20 @@ __device__ __forceinline__ void epilogue(const HerkInst& a, const HerkTask& task
       }
       off[u] = ok ? 2 * b : -1;
     }
+    if (F16) {
+      if (!first) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          vre[u] += prev[u].x;
+          vim[u] += prev[u].y;
+        }
+      }
+      if (!last) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) sp[u * 128] = make_int2(vre[u], vim[u]);
+        continue;
+      }
+    }
     if (a.accumulate) {
       // reductions at L2: nothing waits for the old value
 #pragma unroll
@@ -308,109 +385,6 @@ __device__ __forceinline__ void epilogue(const HerkInst& a, const HerkTask& task
 #pragma unroll
       for (int u = 0; u < 4; ++u)
         if (off[u] >= 0) st_s64x2(chp + off[u], vre[u], vim[u]);
-    }
-  }
-}
-
-// 8-bit drain.  Rows 4i + t of Y hold, for t = 0 .. 3, the signed high nibble
-// of Re x_i, its unsigned low nibble, and the same two for Im x_i (x = 16 h +
-// l).  High-nibble rows carry offset codes (offset 8), low-nibble rows plain
-// codes (offset 0), so G[p][q] = 2^18 Gu - o_q U_p - o_p U_q + o_p o_q T.  Each
-// visibility folds a 4 x 4 block of G with weights 16 (h) and 1 (l):
-//   Re V_ij = sum_{a,b} w_a w_b (G[Re_a i][Re_b j] + G[Im_a i][Im_b j])
-//   Im V_ij = sum_{a,b} w_a w_b (G[Im_a i][Re_b j] - G[Re_a i][Im_b j]).
-// A lane forms its row's share for the four inputs j of a 16-column chunk;
-// the four lanes of input i reduce-scatter them (six shuffles) so that lane
-// t ends with the visibility of the chunk's t-th input.
-__device__ __forceinline__ void epilogue8(const HerkInst& a, const HerkTask& task, const TaskGeom& g,
-                                          const int32_t* usum, uint32_t tmem, int quad, int part,
-                                          int nparts, int lane) {
-  const bool stacked = a.rows_per_chan > 0;
-  const int p = quad * 32 + lane;
-  const int n = a.n_inputs;
-  int ch, i, ra;
-  bool row_ok;
-  if (stacked) {
-    const int rpc = a.rows_per_chan;
-    ch = task.chan0 + p / rpc;
-    const int rr = p % rpc;
-    i = rr >> 2;
-    ra = rr & 3;
-    row_ok = i < n && ch < a.n_chans;
-  } else {
-    ch = task.chan0;
-    const int prow = task.rb * 128 + p;
-    i = prow >> 2;
-    ra = prow & 3;
-    row_ok = i < n;
-  }
-  const int op = (ra & 1) ? 0 : 8;      // offset of this row's codes
-  const int wa = (ra & 1) ? 1 : 16;     // weight of this row's nibble
-  const bool im_row = ra >= 2;
-  const int up = usum[g.a_slot * 128 + p];
-  const int t8 = 8 * a.tn;
-  const long long nbl = (long long)n * (n + 1) / 2;
-  int64_t* chp = a.acc + (long long)(row_ok ? ch : 0) * nbl * 2;
-  const int tri_i = i * (i + 1) / 2;
-  const int sel = lane & 3, bit1 = (lane >> 1) & 1, bit0 = lane & 1;
-  const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16);
-  const int nch = g.nb * 8, per = nch / nparts;  // 16-column chunks = 4 inputs each
-  for (int cc = part * per; cc < (part + 1) * per; ++cc) {
-    uint32_t r[16];
-    tmem_load16(trow + (uint32_t)(cc * 16), r);
-    int pre[4], pim[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      int gq[4];
-#pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        const int k = 4 * u + b;
-        const int oq = (b & 1) ? 0 : 8;
-        gq[b] = __float2int_rn(__uint_as_float(r[k]) * 262144.0f) - oq * up -
-                op * usum[cc * 16 + k] + oq * (op ? t8 : 0);
-      }
-      const int sre = 16 * gq[0] + gq[1], sim = 16 * gq[2] + gq[3];
-      pre[u] = wa * (im_row ? sim : sre);
-      pim[u] = wa * (im_row ? sre : -sim);
-    }
-    // reduce-scatter over the four lanes of input i: keep the half of the
-    // chunk's inputs named by bit 1 of the lane, then the one named by bit 0
-    int hre[2], him[2];
-#pragma unroll
-    for (int t = 0; t < 2; ++t) {
-      const int sr = bit1 ? pre[t] : pre[2 + t], si = bit1 ? pim[t] : pim[2 + t];
-      hre[t] = (bit1 ? pre[2 + t] : pre[t]) + __shfl_xor_sync(0xFFFFFFFFu, sr, 2);
-      him[t] = (bit1 ? pim[2 + t] : pim[t]) + __shfl_xor_sync(0xFFFFFFFFu, si, 2);
-    }
-    int vre = (bit0 ? hre[1] : hre[0]) + __shfl_xor_sync(0xFFFFFFFFu, bit0 ? hre[0] : hre[1], 1);
-    int vim = (bit0 ? him[1] : him[0]) + __shfl_xor_sync(0xFFFFFFFFu, bit0 ? him[0] : him[1], 1);
-    const int q = (cc & 7) * 16 + 4 * sel;  // first column of this lane's input j in its block
-    int b;
-    bool ok;
-    if (stacked) {
-      const int rpc = a.rows_per_chan;
-      const int j = (q % rpc) >> 2;
-      ok = row_ok && task.chan0 + q / rpc == ch && j <= i;
-      b = tri_i + j;
-    } else {
-      const int cblk = slot_block(g, cc >> 3);
-      const int j = (128 * cblk + q) >> 2;
-      if (cblk > task.rb) {
-        ok = row_ok && j < n;  // baseline (j, i), j > i: the conjugate
-        b = j * (j + 1) / 2 + i;
-        vim = -vim;
-      } else {
-        ok = row_ok && j <= i;
-        b = tri_i + j;
-      }
-    }
-    if (ok) {
-      int64_t* d = chp + 2 * b;
-      if (a.accumulate) {
-        red_s64x2(d, vre, vim);  // reduction at L2: nothing waits for the old value
-      } else {
-        st_s64x2(d, vre, vim);
-      }
     }
   }
 }
@@ -441,9 +415,9 @@ __device__ __forceinline__ void ctrl_init_common(Ctrl& sm, int tid) {
 
 // ------------------------------------------------------------- ring kernel
 // Persistent: one CTA per SM walks the tasks blockIdx.x, blockIdx.x + grid,
-// ...; stage S counts the 128-spectrum stages of all its tasks in order.
-// Shared memory is one ring of slots of max_nblk operand blocks.  Stage S
-// uses slot S mod ns:
+// ...; stage S counts the stages (128 spectra at 4 bits, 64 at 8 bits) of all
+// its tasks in order.  Shared memory is one ring of slots of max_nblk operand
+// blocks.  Stage S uses slot S mod ns:
 //   warp 17 (TMA)     waits until the MMAs of stage S - ns have finished with
 //                     the slot, then loads the packed bytes of stage S into
 //                     its upper half (packed block b at nblk + b eighths);
@@ -451,12 +425,14 @@ __device__ __forceinline__ void ctrl_init_common(Ctrl& sm, int tid) {
 //                     and for the bytes, reads all of them into registers,
 //                     meets at a group barrier, and writes the swizzled
 //                     operands over them, in place;
-//   warp 16 (MMA)     issues the four K = 32 MMAs of the stage into one of two
-//                     256-column tensor-memory accumulators (tasks alternate)
-//                     and commits the slot back;
-//   warps 20..27      (drain) convert the accumulators of task j while task
-//                     j + 1 is being multiplied (warps 18, 19 only complete
-//                     the warpgroup of warps 16, 17).
+//   warp 16 (MMA)     issues the four MMAs of the stage into one of two
+//                     256-column tensor-memory accumulators (accumulations
+//                     alternate) and commits the slot back;
+//   warps 20..27      (drain) convert accumulation v while accumulation v + 1
+//                     is being multiplied (warps 18, 19 only complete the
+//                     warpgroup of warps 16, 17).
+// An accumulation is a whole task at 4 bits, and at 8 bits up to 1024
+// spectra of one (a task of T spectra takes ceil(T / 1024) in a row).
 // The unpack warpgroups take registers from the others (setmaxnreg): the
 // unpack loop holds a whole stage in registers across the group barrier.
 // Every wait on a slot barrier for phase m is preceded by a completed wait
@@ -473,43 +449,51 @@ constexpr int kGroups = XE_GROUPS;            // unpack groups (stages S = g mod
 constexpr int kGroupWarps = 16 / kGroups;
 constexpr int kGroupThreads = kGroupWarps * 32;
 constexpr int kUnpackWarps = kGroups * kGroupWarps;
-// Ring stages: kRStageT spectra (128: 128-byte-swizzled operand rows; 64:
-// 64-byte-swizzled rows and twice the slots for the same shared memory).
-#ifndef XE_STAGE_T
-#define XE_STAGE_T 128
-#endif
-constexpr int kRStageT = XE_STAGE_T;
-static_assert(kRStageT == 128 || kRStageT == 64, "stage of 128 or 64 spectra");
-constexpr int kROpBlock = 128 * kRStageT;  // unpacked 128-row block of a stage
-constexpr int kRPkBlock = 64 * kRStageT;   // packed 64-input block of a stage
-constexpr int kRChunks = kRStageT / 16;    // 16-byte chunks per row
-constexpr int kRKSteps = kRStageT / 32;    // K = 32 MMAs per stage
-constexpr int kItems = kMaxBlocks * 64 * kRChunks / kGroupThreads;  // 16-byte items per thread
-constexpr int kPairsPerItem = kGroupThreads / kRChunks;             // inputs per item index
-
-// Byte offset of 16-byte chunk c of row r in a swizzled operand block.
-__device__ __forceinline__ uint32_t op_offset(int r, int c) {
-  const int sw = kRStageT == 128 ? (r & 7) : ((r >> 1) & 3);
-  return (uint32_t)((r >> 3) * (8 * kRStageT) + (r & 7) * kRStageT + ((c ^ sw) << 4));
+// Ring stages.  Every row of Y gets one 128-byte swizzled operand row per
+// stage: 128 spectra of E4M3 codes (4-bit samples) or 64 spectra of FP16
+// values (8-bit samples).  Either way a 128-row block is 16 KB of operands
+// made from 8 KB of packed bytes (64 byte rows x 128 spectra, or 128 byte
+// rows x 64 spectra), and a stage takes four MMAs of K = 32 bytes per row.
+constexpr int kROpBlock = 128 * 128;  // operands of a 128-row block
+constexpr int kRPkBlock = 64 * 128;   // packed bytes of a 128-row block
+constexpr int kRKSteps = 4;           // MMAs per stage
+template <bool EIGHT>
+__host__ __device__ constexpr int stage_t() {  // spectra per stage
+  return EIGHT ? 64 : 128;
 }
-__device__ __forceinline__ uint64_t op_desc(uint32_t saddr) {
-  return kRStageT == 128 ? umma_desc_sw128(saddr) : umma_desc_sw64(saddr);
-}
+// 8-bit: spectra per tensor-memory accumulation (FP32 sums of products of at
+// most 127^2 stay exact integers: 127^2 * 1024 < 2^24)
+constexpr int kPiece8 = 1024;
+constexpr int kPieceStages8 = kPiece8 / stage_t<true>();
+constexpr int kItems = kMaxBlocks * 4;  // 16-byte packed items per unpack thread and stage
+static_assert(kGroupThreads == 128, "an unpack group covers a packed block in four items a thread");
 constexpr int kMmaWarp = kUnpackWarps, kTmaWarp = kUnpackWarps + 1, kEpiWarp0 = kUnpackWarps + 4;
 constexpr int kEpiWarps = XE_EPI_WARPS;
 constexpr int kRingThreads = (kEpiWarp0 + kEpiWarps) * 32;
 // registers per thread: launch share, unpack warpgroups, the other warpgroups
+// (the 8-bit drain, which adds the accumulations' partial sums, takes more,
+// the 8-bit unpack less)
 constexpr int kRegsLaunch = (65536 / kRingThreads) & ~7;
-constexpr int kRegsUnpack = 88, kRegsOther = 48;
+template <bool EIGHT>
+__host__ __device__ constexpr int regs_unpack() { return EIGHT ? 72 : 80; }
+template <bool EIGHT>
+__host__ __device__ constexpr int regs_other() { return EIGHT ? 64 : 56; }
 static_assert(kRingThreads % 128 == 0, "whole warpgroups");
-static_assert(kUnpackWarps * 32 * kRegsUnpack + (kRingThreads - kUnpackWarps * 32) * kRegsOther <=
-                  kRingThreads * kRegsLaunch,
+template <bool EIGHT>
+constexpr bool regs_fit() {
+  return kUnpackWarps * 32 * regs_unpack<EIGHT>() +
+             (kRingThreads - kUnpackWarps * 32) * regs_other<EIGHT>() <=
+         kRingThreads * kRegsLaunch;
+}
+static_assert(regs_fit<false>() && regs_fit<true>(),
               "the register split must fit in the launch allocation");
 #ifndef XE_MAX_SLOTS
 #define XE_MAX_SLOTS 16
 #endif
 constexpr int kMaxSlots = XE_MAX_SLOTS;  // ring slots at most (shared memory sets the count)
 static_assert(kEpiWarps % 4 == 0, "drain warps cover the four tensor-memory lane quarters");
+static_assert(kEpiWarps / 4 <= 2 && 16 * 4 * 128 == kHerkScratchInt2,
+              "the 8-bit scratch holds 4 values of 128 rows for each of 16 column chunks");
 
 struct RingCtrl {
   uint64_t full_t[kMaxSlots];    // packed bytes of the slot landed (TMA transaction count)
@@ -536,15 +520,24 @@ __device__ __forceinline__ int my_task_count(const HerkArgs& a) {
 __device__ __forceinline__ HerkInst task_inst(const HerkArgs& a, const HerkTask& t) {
   return a.insts ? a.insts[t.inst] : a.in;
 }
+template <bool EIGHT>
 __device__ __forceinline__ int stages_of(const HerkInst& in) {
-  return (in.tn + kRStageT - 1) / kRStageT;
+  return (in.tn + stage_t<EIGHT>() - 1) / stage_t<EIGHT>();
+}
+// Accumulations of a task of nk stages (at least one, so that every role
+// counts the same sequence).
+template <bool EIGHT>
+__device__ __forceinline__ int pieces_of(int nk) {
+  return EIGHT ? max(1, (nk + kPieceStages8 - 1) / kPieceStages8) : 1;
 }
 
 // TCI: the tensor maps describe payload-order blocks ({byte row, channel,
-// time}, boxes of 64 byte rows x 128 spectra) and the unpack transposes.
+// time}) and the unpack transposes.  EIGHT: 8-bit samples as FP16 operands.
 template <bool LO_IS_REAL, bool EIGHT, bool TCI>
 __global__ void __launch_bounds__(kRingThreads, 1)
     herk4_ring_kernel(const __grid_constant__ CUtensorMap tmap, const HerkArgs a) {
+  constexpr int kT = stage_t<EIGHT>();             // spectra per stage
+  constexpr int kPkRowBytes = kT;                  // packed bytes of a byte row in a stage
   extern __shared__ uint8_t dyn_raw[];
   // control block at the end of dynamic shared memory, ring from the first
   // 1024-byte boundary (swizzle atoms) up to it
@@ -592,7 +585,7 @@ __global__ void __launch_bounds__(kRingThreads, 1)
   // joined again would leave the compiler the smaller budget for all roles.
   if (warp == kTmaWarp) {
     // ------------------------------------------------------------ TMA loader
-    regs_shrink<kRegsOther>();
+    regs_shrink<regs_other<EIGHT>()>();
     if (lane == 0 && n_my > 0) {
       if (!a.tmaps) tma_prefetch_desc(&tmap);
       // fault injection: this stage of CTA 0 is never loaded, so the waits
@@ -604,7 +597,7 @@ __global__ void __launch_bounds__(kRingThreads, 1)
       HerkInst in = task_inst(a, task);
       const CUtensorMap* tm = a.tmaps ? &a.tmaps[task.inst] : &tmap;
       if (a.tmaps) tensormap_acquire(tm);
-      int nk = stages_of(in);
+      int nk = stages_of<EIGHT>(in);
       bool stacked = in.rows_per_chan > 0;
       for (int S = 0;; ++S, ++k) {
         if (k == nk) {  // next task
@@ -615,20 +608,21 @@ __global__ void __launch_bounds__(kRingThreads, 1)
           in = task_inst(a, task);
           tm = a.tmaps ? &a.tmaps[task.inst] : &tmap;
           if (a.tmaps) tensormap_acquire(tm);
-          nk = stages_of(in);
+          nk = stages_of<EIGHT>(in);
           stacked = in.rows_per_chan > 0;
         }
         if (m > 0 && !mbar_wait(&sm.empty[s], (uint32_t)((m - 1) & 1), abort, budget)) {
           raise_timeout(a.status, abort);
           break;
         }
-        const int t = in.t0 + k * kRStageT;
+        const int t = in.t0 + k * kT;
         const uint32_t dst0 = ring_addr + (uint32_t)(s * slot_bytes + g.nblk * kRPkBlock);
         if (S != skip) {
           mbar_expect_tx(&sm.full_t[s], (uint32_t)(g.nblk * kRPkBlock));
           for (int b = 0; b < g.nblk; ++b) {
             const uint32_t dst = dst0 + (uint32_t)(b * kRPkBlock);
-            const int row0 = stacked ? 0 : 64 * slot_block(g, b);
+            // byte rows of a 128-row block: 64 (4-bit) or 128 (8-bit)
+            const int row0 = stacked ? 0 : (kRPkBlock / kPkRowBytes) * slot_block(g, b);
             if (TCI)
               tma_load_3d(dst, tm, row0, task.chan0, t, &sm.full_t[s]);
             else
@@ -649,42 +643,52 @@ __global__ void __launch_bounds__(kRingThreads, 1)
     __syncwarp();
   } else if (warp == kMmaWarp) {
     // ------------------------------------------------------------ MMA issuer
-    regs_shrink<kRegsOther>();
+    regs_shrink<regs_other<EIGHT>()>();
     if (lane == 0) {
-      int s = 0, m = 0;
+      int s = 0, m = 0, v = 0;  // v: accumulations so far (tensor-memory buffer v & 1)
       bool ok = true;
       for (int j = 0; j < n_my && ok; ++j) {
-        const int b = j & 1;
         const HerkTask task = my_task(a, j);
         const TaskGeom g = task_geom(task);
-        const int nk = stages_of(task_inst(a, task));
+        const int nk = stages_of<EIGHT>(task_inst(a, task));
+        const int np = pieces_of<EIGHT>(nk);
         const uint32_t idesc = umma_idesc(0, 128, 128 * g.nb);
-        if (j >= 2 && !mbar_wait(&sm.tmem_empty[b], (uint32_t)(((j >> 1) - 1) & 1), abort, budget)) {
-          raise_timeout(a.status, abort);
-          break;
-        }
-        tc_after_sync();
-        const uint32_t d = tmem + (uint32_t)(b * 256);
-        for (int k = 0; k < nk; ++k) {
-          if (!mbar_wait(&sm.full_o[s], (uint32_t)(m & 1), abort, budget)) {
+        for (int q = 0; q < np && ok; ++q, ++v) {
+          const int b = v & 1;
+          const int k0 = EIGHT ? q * kPieceStages8 : 0;
+          const int k1 = EIGHT ? min(nk, k0 + kPieceStages8) : nk;
+          if (v >= 2 && !mbar_wait(&sm.tmem_empty[b], (uint32_t)(((v >> 1) - 1) & 1), abort, budget)) {
             raise_timeout(a.status, abort);
             ok = false;
             break;
           }
           tc_after_sync();
-          const uint32_t st = ring_addr + (uint32_t)(s * slot_bytes);
-          const uint64_t adesc = op_desc(st + (uint32_t)(g.a_slot * kROpBlock));
-          const uint64_t bdesc = op_desc(st);
+          const uint32_t d = tmem + (uint32_t)(b * 256);
+          for (int k = k0; k < k1; ++k) {
+            if (!mbar_wait(&sm.full_o[s], (uint32_t)(m & 1), abort, budget)) {
+              raise_timeout(a.status, abort);
+              ok = false;
+              break;
+            }
+            tc_after_sync();
+            const uint32_t st = ring_addr + (uint32_t)(s * slot_bytes);
+            const uint64_t adesc = umma_desc_sw128(st + (uint32_t)(g.a_slot * kROpBlock));
+            const uint64_t bdesc = umma_desc_sw128(st);
 #pragma unroll
-          for (int kk = 0; kk < kRKSteps; ++kk)
-            umma_f8(d, adesc + 2 * kk, bdesc + 2 * kk, idesc, (k | kk) != 0);
-          umma_commit(&sm.empty[s]);
-          if (++s == ns) {
-            s = 0;
-            ++m;
+            for (int kk = 0; kk < kRKSteps; ++kk) {
+              if (EIGHT)
+                umma_f16(d, adesc + 2 * kk, bdesc + 2 * kk, idesc, (k != k0 || kk != 0));
+              else
+                umma_f8(d, adesc + 2 * kk, bdesc + 2 * kk, idesc, (k != k0 || kk != 0));
+            }
+            umma_commit(&sm.empty[s]);
+            if (++s == ns) {
+              s = 0;
+              ++m;
+            }
           }
+          if (ok) umma_commit(&sm.tmem_full[b]);
         }
-        if (ok) umma_commit(&sm.tmem_full[b]);
       }
       umma_commit(&sm.done);
       int never = 0;
@@ -693,18 +697,29 @@ __global__ void __launch_bounds__(kRingThreads, 1)
     __syncwarp();
   } else if (warp < kUnpackWarps) {
     // ------------------------------------------------------------ unpackers
-    regs_grow<kRegsUnpack>();
+    regs_grow<regs_unpack<EIGHT>()>();
     const int grp = warp / kGroupWarps;
     const int gt = tid - grp * kGroupThreads;
-    const int chunk = gt % kRChunks, g8 = gt / kRChunks;  // this thread's chunk and pair
-    // payload order: quad of byte rows and K chunk of this thread's items
+    // Item geometry of this thread (four 16-byte items per packed block).
+    //   4-bit, [c][row][t]: byte row g8 + 16 it' of the block, spectra
+    //     16 chunk .. + 15 -> operand rows 2 (g8 + 16 it') and + 1, chunk
+    //     `chunk`; payload order: rows 4 tq .. + 3, K chunk tc (see tci_t).
+    //   8-bit, [c][row][t]: byte row r32 + 32 it', spectra 16 c4 .. + 15 ->
+    //     operand row r32 + 32 it', chunks 2 c4 and 2 c4 + 1; payload order:
+    //     rows 4 lane .. + 3, spectra 16 c8 .. + 15 gathered with the halves
+    //     swapped on odd lanes (sw8), which keeps the stores free of bank
+    //     conflicts (the gathers are: a row of 128 bytes per spectrum puts
+    //     lane l's word in bank l).
+    const int chunk = gt & 7, g8 = gt >> 3;
     const int tq = lane >> 1, tc = (lane + 2 * (gt >> 5)) & 7;
-    static_assert(!TCI || (kGroupThreads == 128 && kRStageT == 128), "payload order: 4-warp groups");
-    const uint32_t src0 = ring_addr + (uint32_t)(kRStageT * g8 + 16 * chunk);
-    // rows 2 g8 and 2 g8 + 1; later items add whole 8-row atoms, so the
-    // swizzle position stays the same
-    const uint32_t dst_re = ring_addr + op_offset(2 * g8, chunk);
-    const uint32_t dst_im = ring_addr + op_offset(2 * g8 + 1, chunk);
+    const int c4 = gt & 3, r32 = gt >> 2;
+    const int c8 = ((gt >> 5) + (lane >> 1)) & 3, sw8 = 8 * (lane & 1);
+    const uint32_t src0 =
+        ring_addr + (uint32_t)(EIGHT ? kPkRowBytes * r32 + 16 * c4 : kPkRowBytes * g8 + 16 * chunk);
+    static_assert(kMaxBlocks == 2, "a stage holds at most two 128-row blocks");
+    // later items add whole 8-row atoms, so the swizzle position stays the same
+    const uint32_t dst_a = ring_addr + (EIGHT ? swz_offset(r32, 2 * c4) : swz_offset(2 * g8, chunk));
+    const uint32_t dst_b = ring_addr + (EIGHT ? swz_offset(r32, 2 * c4 + 1) : swz_offset(2 * g8 + 1, chunk));
     bool ok = true;
     // next stage of this group, its slot s = S mod ns and use m = S / ns,
     // advanced by additions (kGroups <= ns)
@@ -716,8 +731,8 @@ __global__ void __launch_bounds__(kRingThreads, 1)
       const HerkTask task = my_task(a, j);
       const TaskGeom g = task_geom(task);
       const int tn = task_inst(a, task).tn;
-      const int S1 = S0 + (tn + kRStageT - 1) / kRStageT;
-      const int nit = g.nblk * 64 * kRChunks / kGroupThreads;
+      const int S1 = S0 + (tn + kT - 1) / kT;
+      const int nit = g.nblk * 4;
       int32_t sre[kItems], sim[kItems];
 #pragma unroll
       for (int it = 0; it < kItems; ++it) sre[it] = sim[it] = 0;
@@ -728,84 +743,101 @@ __global__ void __launch_bounds__(kRingThreads, 1)
                    mbar_wait(&sm.full_t[s], (uint32_t)(m & 1), abort, budget);
         if (!got) raise_timeout(a.status, abort);
         const uint32_t so = (uint32_t)(s * slot_bytes);
-        const bool tail = (k + 1) * kRStageT > tn;
-        if constexpr (TCI) {
-          // item (quad tq, chunk tc) of every block: 4 byte rows x 16 spectra
-          uint32_t wv[kMaxBlocks][16];
-          const uint32_t pk = ring_addr + so + (uint32_t)(g.nblk * kRPkBlock + 4 * tq);
+        const bool tail = (k + 1) * kT > tn;
+        // Operand block 0 of a two-block stage overlaps neither packed block
+        // (operands [0, 16 KB) and [16, 32 KB), packed bytes [16, 32 KB)), so
+        // it is written before the group barrier; the barrier then only
+        // guards the block whose operands cover packed bytes.
+        uint32_t keep[4] = {~0u, ~0u, ~0u, ~0u};
+        if (tail) {
+          if (TCI && EIGHT)
+            tci8_keep(c8, sw8, tn - k * kT, keep);
+          else if (TCI)
+            tci_keep(tc, k * kT, tn, keep);
+          else
+            time_keep(k * kT + (EIGHT ? c4 : chunk) * 16, tn, keep);
+        }
+        const uint32_t pk = ring_addr + so + (uint32_t)(g.nblk * kRPkBlock);
+        uint32_t wv[16];  // this thread's 64 packed bytes of one block
+        // load the items of block it
+        auto load = [&](int it) {
+          if constexpr (TCI) {  // 4 byte rows x 16 spectra, gathered
 #pragma unroll
-          for (int it = 0; it < kMaxBlocks; ++it)
-            if (it < g.nblk && got)
+            for (int jj = 0; jj < 16; ++jj)
+              wv[jj] = lds32(pk + (uint32_t)(it * kRPkBlock) +
+                             (uint32_t)(EIGHT ? (16 * c8 + (jj ^ sw8)) * 128 + 4 * lane
+                                              : tci_t(tc, jj) * 64 + 4 * tq));
+          } else {  // 4 items of 16 bytes: byte rows 16 (4-bit) or 32 (8-bit) apart
 #pragma unroll
-              for (int jj = 0; jj < 16; ++jj)
-                wv[it][jj] = lds32(pk + (uint32_t)(it * kRPkBlock + tci_t(tc, jj) * 64));
-          // every packed byte of the stage is in registers before any is
-          // overwritten; the group leaves together if any of its waits failed
-          if (!named_bar_and(2 + grp, kGroupThreads, got)) {
-            ok = false;
-            break;
+            for (int q = 0; q < 4; ++q) {
+              const uint4 v = lds128(src0 + so + (uint32_t)(g.nblk * kRPkBlock) +
+                                     (uint32_t)(2048 * (4 * it + q)));
+              wv[4 * q] = v.x, wv[4 * q + 1] = v.y, wv[4 * q + 2] = v.z, wv[4 * q + 3] = v.w;
+            }
           }
-          uint32_t keep[4] = {~0u, ~0u, ~0u, ~0u};
-          if (tail) tci_keep(tc, k * kRStageT, tn, keep);
+        };
+        // convert block IT and write its operands (IT a constant: the row
+        // sums stay in registers)
+        auto store = [&](auto IT) {
+          constexpr int it = decltype(IT)::value;
+          const uint32_t ob = ring_addr + so + (uint32_t)(it * kROpBlock);
+          if constexpr (TCI) {
 #pragma unroll
-          for (int it = 0; it < kMaxBlocks; ++it) {
-            if (it < g.nblk) {
+            for (int gg = 0; gg < 4; ++gg)
+              transpose4x4b(wv[4 * gg], wv[4 * gg + 1], wv[4 * gg + 2], wv[4 * gg + 3]);
+          }
 #pragma unroll
-              for (int gg = 0; gg < 4; ++gg)
-                transpose4x4b(wv[it][4 * gg], wv[it][4 * gg + 1], wv[it][4 * gg + 2], wv[it][4 * gg + 3]);
-              const uint32_t ob = ring_addr + so + (uint32_t)(it * kROpBlock);
+          for (int u = 0; u < 4; ++u) {
+            // TCI: byte row 4 t + u (t = lane or tq); otherwise item u
+            uint32_t w[4];
 #pragma unroll
-              for (int u = 0; u < 4; ++u) {
-                const uint32_t w[4] = {wv[it][u], wv[it][4 + u], wv[it][8 + u], wv[it][12 + u]};
-                uint32_t re[4], im[4];
-                unpack16<LO_IS_REAL, true, EIGHT>(w, keep, re, im, sre[4 * it + u], sim[4 * it + u]);
-                if (EIGHT) {
-#pragma unroll
-                  for (int q = 0; q < 4; ++q) {  // any valid byte equal to 0x80?
-                    const uint32_t z = (w[q] ^ 0x80808080u) | ~keep[q];
-                    bad |= (z - 0x01010101u) & ~z & 0x80808080u;
-                  }
-                }
+            for (int q = 0; q < 4; ++q) w[q] = TCI ? wv[4 * q + u] : wv[4 * u + q];
+            if constexpr (EIGHT) {
+              uint32_t h[8];
+              s8_to_f16(w, keep, h, bad);
+              if constexpr (TCI) {
+                const int r = 4 * lane + u, sw = sw8 >> 3;
+                sts128(ob + swz_offset(r, 2 * c8 + sw), h[0], h[1], h[2], h[3]);
+                sts128(ob + swz_offset(r, 2 * c8 + 1 - sw), h[4], h[5], h[6], h[7]);
+              } else {
+                const uint32_t o = (uint32_t)(4096 * u);  // 32 operand rows on
+                sts128(dst_a + so + (uint32_t)(it * kROpBlock) + o, h[0], h[1], h[2], h[3]);
+                sts128(dst_b + so + (uint32_t)(it * kROpBlock) + o, h[4], h[5], h[6], h[7]);
+              }
+            } else {
+              uint32_t re[4], im[4];
+              // always masked (all ones before the last stage): no branch inside the unrolled loop
+              unpack16<LO_IS_REAL, true>(w, keep, re, im, sre[4 * it + u], sim[4 * it + u]);
+              if constexpr (TCI) {
                 const int r = 2 * (4 * tq + u);
-                sts128(ob + op_offset(r, tc), re[0], re[1], re[2], re[3]);
-                sts128(ob + op_offset(r + 1, tc), im[0], im[1], im[2], im[3]);
+                sts128(ob + swz_offset(r, tc), re[0], re[1], re[2], re[3]);
+                sts128(ob + swz_offset(r + 1, tc), im[0], im[1], im[2], im[3]);
+              } else {
+                const uint32_t o = (uint32_t)(4096 * u);
+                sts128(dst_a + so + (uint32_t)(it * kROpBlock) + o, re[0], re[1], re[2], re[3]);
+                sts128(dst_b + so + (uint32_t)(it * kROpBlock) + o, im[0], im[1], im[2], im[3]);
               }
             }
           }
-        } else {
-        const uint32_t src = src0 + so + (uint32_t)(g.nblk * kRPkBlock);
-        uint32_t keep[4] = {~0u, ~0u, ~0u, ~0u};
-        if (tail) time_keep(k * kRStageT + chunk * 16, tn, keep);
-        uint4 v[kItems];
-#pragma unroll
-        for (int it = 0; it < kItems; ++it)
-          if (it < nit && got) v[it] = lds128(src + (uint32_t)(kRStageT * kPairsPerItem * it));
-        // every packed byte of the stage is in registers before any is
-        // overwritten; the group leaves together if any of its waits failed
+        };
+        const bool two = g.nblk == 2;
+        if (got) {
+          load(0);
+          if (two) {
+            store(std::integral_constant<int, 0>{});
+            load(1);
+          }
+        }
+        // every packed byte of the stage is in registers or converted before
+        // any is overwritten; the group leaves together if any wait failed
         if (!named_bar_and(2 + grp, kGroupThreads, got)) {
           ok = false;
           break;
         }
-#pragma unroll
-        for (int it = 0; it < kItems; ++it) {
-          if (it < nit) {
-            const uint32_t w[4] = {v[it].x, v[it].y, v[it].z, v[it].w};
-            uint32_t re[4], im[4];
-            // always masked (all ones before the last stage): no branch inside the unrolled loop
-            unpack16<LO_IS_REAL, true, EIGHT>(w, keep, re, im, sre[it], sim[it]);
-            if (EIGHT) {
-#pragma unroll
-              for (int q = 0; q < 4; ++q) {  // any valid byte equal to 0x80?
-                const uint32_t z = (w[q] ^ 0x80808080u) | ~keep[q];
-                bad |= (z - 0x01010101u) & ~z & 0x80808080u;
-              }
-            }
-            const uint32_t o = so + (uint32_t)(2 * kRStageT * kPairsPerItem * it);
-            sts128(dst_re + o, re[0], re[1], re[2], re[3]);
-            sts128(dst_im + o, im[0], im[1], im[2], im[3]);
-          }
-        }
-        }
+        if (two)
+          store(std::integral_constant<int, 1>{});
+        else
+          store(std::integral_constant<int, 0>{});
         fence_smem_to_async();
         __syncwarp();
         if (lane == 0) mbar_arrive(&sm.full_o[s]);
@@ -816,6 +848,8 @@ __global__ void __launch_bounds__(kRingThreads, 1)
         }
       }
       if (!ok) break;
+      S0 = S1;
+      if constexpr (EIGHT) continue;  // signed operands: no row sums
       // publish this task's row sums once the buffer is free again
       const bool freed = j < 2 || mbar_wait(&sm.usum_empty[b], (uint32_t)(((j >> 1) - 1) & 1), abort, budget);
       if (!freed) raise_timeout(a.status, abort);
@@ -837,43 +871,51 @@ __global__ void __launch_bounds__(kRingThreads, 1)
           }
         }
       } else {
-        publish_row_sums<kGroupThreads, kItems, kRChunks>(sre, sim, nit, gt, sm.usum[b]);
+        publish_row_sums<kGroupThreads, kItems, 8>(sre, sim, nit, gt, sm.usum[b]);
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&sm.usum_full[b]);
-      S0 = S1;
     }
     if (EIGHT && __any_sync(0xFFFFFFFFu, bad != 0) && lane == 0) atomicOr(a.status, kStRange);
   } else if (warp < kEpiWarp0) {
-    regs_shrink<kRegsOther>();  // the two idle warps of the MMA / TMA warpgroup
+    regs_shrink<regs_other<EIGHT>()>();  // the two idle warps of the MMA / TMA warpgroup
   } else {
     // ------------------------------------------------------------ drain
-    regs_shrink<kRegsOther>();
+    regs_shrink<regs_other<EIGHT>()>();
     const int quad = warp & 3, part = (warp - kEpiWarp0) >> 2;
-    for (int j = 0; j < n_my; ++j) {
-      const int b = j & 1;
-      const uint32_t par = (uint32_t)((j >> 1) & 1);
-      const bool got = mbar_wait(&sm.tmem_full[b], par, abort, budget) && mbar_wait(&sm.usum_full[b], par, abort, budget);
-      if (!got) raise_timeout(a.status, abort);
-      if (!named_bar_and(1, kEpiWarps * 32, got)) break;  // the drain warps leave together
-      tc_after_sync();
+    int2* scr = EIGHT ? a.scratch + (size_t)blockIdx.x * kHerkScratchInt2 : nullptr;
+    int v = 0;
+    bool ok = true;
+    for (int j = 0; j < n_my && ok; ++j) {
       const HerkTask task = my_task(a, j);
       const HerkInst in = task_inst(a, task);
-      if (EIGHT)
-        epilogue8(in, task, task_geom(task), sm.usum[b], tmem + (uint32_t)(b * 256), quad, part,
-                  kEpiWarps / 4, lane);
-      else
-        epilogue(in, task, task_geom(task), sm.usum[b], tmem + (uint32_t)(b * 256), quad, part,
-                 kEpiWarps / 4, lane);
-      tc_before_sync();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&sm.tmem_empty[b]);
-      // every drain warp has read the sums: clear them for task j + 2
-      named_bar_sync(1, kEpiWarps * 32);
-      for (int i = tid - kEpiWarp0 * 32; i < kMaxBlocks * 128; i += kEpiWarps * 32)
-        sm.usum[b][i] = 0;
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&sm.usum_empty[b]);
+      const TaskGeom g = task_geom(task);
+      const int np = pieces_of<EIGHT>(stages_of<EIGHT>(in));
+      for (int q = 0; q < np; ++q, ++v) {
+        const int b = v & 1;
+        const uint32_t par = (uint32_t)((v >> 1) & 1);
+        const bool got = mbar_wait(&sm.tmem_full[b], par, abort, budget) &&
+                         (EIGHT || mbar_wait(&sm.usum_full[b], par, abort, budget));
+        if (!got) raise_timeout(a.status, abort);
+        if (!named_bar_and(1, kEpiWarps * 32, got)) {  // the drain warps leave together
+          ok = false;
+          break;
+        }
+        tc_after_sync();
+        epilogue<EIGHT>(in, task, g, sm.usum[b], tmem + (uint32_t)(b * 256), quad, part,
+                        kEpiWarps / 4, lane, q == 0, q == np - 1, scr);
+        tc_before_sync();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&sm.tmem_empty[b]);
+        if (!EIGHT) {
+          // every drain warp has read the sums: clear them for task j + 2
+          named_bar_sync(1, kEpiWarps * 32);
+          for (int i = tid - kEpiWarp0 * 32; i < kMaxBlocks * 128; i += kEpiWarps * 32)
+            sm.usum[b][i] = 0;
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&sm.usum_empty[b]);
+        }
+      }
     }
   }
 #undef budget
@@ -1003,7 +1045,8 @@ __global__ void __launch_bounds__(kLdgThreads, 1) herk4_ldg_kernel(const HerkArg
     good = __all_sync(0xFFFFFFFFu, good);
     if (!good && lane == 0) raise_timeout(args.status, abort);
     tc_after_sync();
-    if (good && !*abort) epilogue(a, task, g, sm.usum, tmem, warp & 3, 0, 1, lane);
+    if (good && !*abort)
+      epilogue<false>(a, task, g, sm.usum, tmem, warp & 3, 0, 1, lane, true, true, nullptr);
   }
   tc_before_sync();
   __syncthreads();
@@ -1052,7 +1095,7 @@ cudaError_t ring_launch(const HerkArgs& a, const CUtensorMap* tmap, int grid, cu
 
 }  // namespace
 
-int herk_ring_stage() { return kRStageT; }
+int herk_ring_stage(int bits) { return bits == 8 ? stage_t<true>() : stage_t<false>(); }
 
 int herk4_max_smem() {
   int m = max_dyn_smem((const void*)herk4_ldg_kernel<false>);
@@ -1080,6 +1123,7 @@ cudaError_t herk4_launch(const HerkArgs& args, const CUtensorMap* tmap, int n_ta
       if (a.grid > 0) grid = std::min(grid, a.grid);
     }
     if (grid < 1) return cudaSuccess;
+    if (a.bits == 8 && (!a.scratch || grid > a.scratch_ctas)) return cudaErrorInvalidValue;
     static const CUtensorMap unused{};  // batched launches read their maps from a.tmaps
     const CUtensorMap* m = tmap ? tmap : &unused;
     if (tci) {

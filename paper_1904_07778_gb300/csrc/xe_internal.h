@@ -36,11 +36,9 @@ enum : int {
 // stacked in one 128-row block (rows_per_chan = 2N rounded up to a power of
 // two) and the task covers channels chan0 .. chan0 + 128 / rows_per_chan - 1.
 //
-// 8-bit samples use the same machinery on byte rows: the block is first laid
-// out as [channel][input][re/im byte][time], and every byte splits into a
-// signed high nibble h and an unsigned low nibble l (value 16 h + l), so an
-// input owns four rows of Y (Re h, Re l, Im h, Im l) and the blocks above
-// count 4N rows.
+// 8-bit samples have the same Y: the block is first laid out as
+// [channel][input][re/im byte][time] (byte row 2i + p), each byte is one
+// FP16 operand, and the blocks above count 2N rows as at 4 bits.
 struct HerkTask {
   int chan0;
   int rb;
@@ -75,7 +73,12 @@ struct HerkArgs {
                              // otherwise task j of CTA b is b + j * gridDim.x
   int* status;
   int lo_is_real;            // 4-bit: real part in the low nibble (whole launch)
-  int bits;                  // 4, or 8 (byte rows: 2 per input, 4 rows of Y per input)
+  int bits;                  // 4, or 8 (byte rows: 2 per input, each one row of Y)
+  // 8-bit: per-CTA partial sums of tasks longer than one accumulation,
+  // kHerkScratchInt2 int2 for each of scratch_ctas CTAs (the launch's grid
+  // must not exceed it)
+  int2* scratch;
+  int scratch_ctas;
   int smem_bytes;            // dynamic shared memory of the launch
   int n_tasks;               // tasks in `tasks`
   int max_nblk;              // largest number of resident 128-row blocks of any task
@@ -87,41 +90,46 @@ struct HerkArgs {
 // with 4-bit offset codes u <= 15 a partial sum is at most 225 per spectrum,
 // and FP32 holds every integer below 2^24 exactly (225 * 65536 < 2^24).
 constexpr int kMaxChunk4 = 65536;
-// 8-bit: the same FP32 bound holds per nibble product, and the drain folds
-// 16 products into int32 sums that stay below 2^31 for up to 32768 spectra
-// (|Re V| <= 2 * 127^2 * 32768 and every partial sum is smaller than that bound
-// times 1.3).
+// Largest number of 8-bit spectra per launch.  The kernel accumulates 1024
+// spectra at a time in FP32 (127^2 * 1024 < 2^24) and adds the pieces in
+// int32, which holds |V| <= 2 * 127^2 * 32768 < 2^31.
 constexpr int kMaxChunk8 = 32768;
+// int2 partial sums per CTA of an 8-bit launch (a 128 x 256 task: 64 x 128
+// visibilities).
+constexpr int kHerkScratchInt2 = 8192;
 
 int herk4_max_smem();
-// Spectra per stage of the ring kernel: the time extent of its TMA boxes.
-int herk_ring_stage();
+// Spectra per stage of the ring kernel (128 at 4 bits, 64 at 8 bits): the
+// time extent of its TMA boxes.
+int herk_ring_stage(int bits);
 // Launch the cross-multiply.  Batched (a.insts and a.tmaps set): the ring
 // kernel over every array's tasks in one persistent launch.  Otherwise tmap
-// describes a.in.x as a 3-D byte tensor {time (inner), byte row, channel} for
-// the ring kernel, or is null for the kernel that loads with plain global
-// loads (any alignment).
-// With tci the tensor maps describe payload-order ([t][c][i]) blocks
-// (make_tci_tmap) and the kernel transposes while it unpacks.
+// (make_herk_tmap) describes a.in.x for the ring kernel, or is null for the
+// 4-bit kernel that loads with plain global loads (any alignment).
+// With tci the tensor maps describe payload-order ([t][c][i]) blocks and the
+// kernel transposes while it unpacks.  8-bit launches need a.scratch for
+// every CTA of the grid (cudaErrorInvalidValue otherwise).
 cudaError_t herk4_launch(const HerkArgs& a, const CUtensorMap* tmap, int n_tasks, cudaStream_t s,
                          bool tci = false);
 
-// Tensor map of a payload-order block [t][c][r] of R byte rows per (spectrum,
-// channel) (R a multiple of 16, base 16-byte aligned) for the payload-order
-// kernel: dims {R, C, T}, box {box_rows, box_chans, herk_ring_stage()} with
-// box_rows x box_chans = 64 byte rows.  Returns false if the driver rejects it.
-bool make_tci_tmap(CUtensorMap* m, const uint8_t* x, int R, int n_chans, int n_time, int box_rows,
-                   int box_chans);
+// Tensor map of one block for the ring kernel, R byte rows per channel
+// (N at 4 bits, 2N at 8 bits), rpc = rows_per_chan of the task plan.  A box
+// is one 128-row operand block of one stage: herk_ring_stage(bits) spectra
+// of 128 * bits / 8 byte rows, or for stacked arrays rpc * bits / 8 byte rows
+// of 128 / rpc channels.
+//   tci = false: x is [channel][byte row][time] with rows row_stride bytes
+//     apart (a multiple of 16, base 16-byte aligned); dims {T, R, C}.
+//   tci = true: x is the payload order [time][channel][byte row] (R a
+//     multiple of 16, base 16-byte aligned); dims {R, C, T}.
+// Returns false if the driver rejects it.
+bool make_herk_tmap(CUtensorMap* m, const uint8_t* x, bool tci, int bits, int R, int n_chans,
+                    int n_time, long long row_stride, int rpc);
+// Device scratch for the 8-bit partial sums of a launch on this device: one
+// kHerkScratchInt2 region per SM (*ctas = the SM count).
+cudaError_t herk_scratch_alloc(int2** p, int* ctas);
 // Whether a block of this layout and width can be read in payload order
 // (no corner turn): [t][c][i] with R = N bits / 4 byte rows a multiple of 16.
 bool tci_direct(int layout, int bits, int n_inputs);
-
-// Build the tensor map of a [channel][input][time] byte array with rows of
-// row_stride bytes (a multiple of 16, base 16-byte aligned).  Box:
-// herk_ring_stage() spectra x box_inputs x box_chans.  Returns false if the
-// driver rejects it.
-bool make_sample_tmap(CUtensorMap* m, const uint8_t* x, int n_time, long long row_stride,
-                      int n_inputs, int n_chans, int box_inputs, int box_chans);
 
 // Corner turn of byte samples: in[t][g][k] -> out[k][g][t], output rows of
 // out_stride >= T bytes (32-byte aligned rows take the fast path).
@@ -165,9 +173,10 @@ cudaError_t turn_rows_chans(const uint8_t* in, uint8_t* out, int layout, int bit
                             int n_chans, int n_time, int c0, int c1, long long out_stride,
                             cudaStream_t s, int persist_ctas = 0);
 
-// Tasks of one array (see HerkTask): rows_per_chan is set for stacked
-// arrays.  With singles, every task has one column block (128 x 128).
-std::vector<HerkTask> plan_tasks(int byte_rows, int n_chans, int* rows_per_chan, bool singles = false);
+// Tasks of one array of n_inputs inputs (2 n_inputs rows of Y; see
+// HerkTask): rows_per_chan is set for stacked arrays.  With singles, every
+// task has one column block (128 x 128).
+std::vector<HerkTask> plan_tasks(int n_inputs, int n_chans, int* rows_per_chan, bool singles = false);
 // Largest number of resident 128-row blocks of any task in the list.
 int tasks_max_nblk(const std::vector<HerkTask>& tasks);
 

@@ -201,8 +201,7 @@ extern "C" int corr_correlate_noalloc(const void* block, int n_inputs, int n_cha
   a.bits = 4;
   CUtensorMap tmap;
   const bool aligned = stride % 16 == 0 && reinterpret_cast<uintptr_t>(src) % 16 == 0;
-  const bool use_tma = aligned && make_sample_tmap(&tmap, src, T, stride, N, C,
-                                                   rpc ? rpc / 2 : 64, rpc ? 128 / rpc : 1);
+  const bool use_tma = aligned && make_herk_tmap(&tmap, src, false, 4, N, C, T, stride, rpc);
   for (int t0 = 0; t0 < T; t0 += kMaxChunk4) {
     a.in.t0 = t0;
     a.in.tn = std::min(kMaxChunk4, T - t0);

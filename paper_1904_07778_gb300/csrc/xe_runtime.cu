@@ -17,8 +17,8 @@ using namespace xe;
 
 namespace xe {
 
-bool make_sample_tmap(CUtensorMap* m, const uint8_t* x, int n_time, long long row_stride,
-                      int n_inputs, int n_chans, int box_inputs, int box_chans) {
+bool make_herk_tmap(CUtensorMap* m, const uint8_t* x, bool tci, int bits, int R, int n_chans,
+                    int n_time, long long row_stride, int rpc) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
     void* fn = nullptr;
@@ -29,51 +29,52 @@ bool make_sample_tmap(CUtensorMap* m, const uint8_t* x, int n_time, long long ro
       return false;
     encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
   }
-  const cuuint64_t dims[3] = {(cuuint64_t)n_time, (cuuint64_t)n_inputs, (cuuint64_t)n_chans};
-  const cuuint64_t strides[2] = {(cuuint64_t)row_stride, (cuuint64_t)row_stride * n_inputs};
-  const cuuint32_t box[3] = {(cuuint32_t)herk_ring_stage(), (cuuint32_t)box_inputs,
-                             (cuuint32_t)box_chans};
+  // a box: one 128-row operand block of one stage (8 KB of packed bytes)
+  const cuuint32_t box_t = (cuuint32_t)herk_ring_stage(bits);
+  const cuuint32_t box_rows = (cuuint32_t)((rpc ? rpc : 128) * bits / 8);
+  const cuuint32_t box_chans = (cuuint32_t)(rpc ? 128 / rpc : 1);
+  cuuint64_t dims[3], strides[2];
+  cuuint32_t box[3];
+  if (tci) {
+    dims[0] = (cuuint64_t)R, dims[1] = (cuuint64_t)n_chans, dims[2] = (cuuint64_t)n_time;
+    strides[0] = (cuuint64_t)R, strides[1] = (cuuint64_t)R * n_chans;
+    box[0] = box_rows, box[1] = box_chans, box[2] = box_t;
+  } else {
+    dims[0] = (cuuint64_t)n_time, dims[1] = (cuuint64_t)R, dims[2] = (cuuint64_t)n_chans;
+    strides[0] = (cuuint64_t)row_stride, strides[1] = (cuuint64_t)row_stride * R;
+    box[0] = box_t, box[1] = box_rows, box[2] = box_chans;
+  }
   const cuuint32_t estr[3] = {1u, 1u, 1u};
   return encode(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<uint8_t*>(x), dims, strides, box,
                 estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-bool make_tci_tmap(CUtensorMap* m, const uint8_t* x, int R, int n_chans, int n_time, int box_rows,
-                   int box_chans) {
-  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-  if (!encode) {
-    void* fn = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
-                                         &q) != cudaSuccess ||
-        q != cudaDriverEntryPointSuccess || !fn)
-      return false;
-    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-  }
-  const cuuint64_t dims[3] = {(cuuint64_t)R, (cuuint64_t)n_chans, (cuuint64_t)n_time};
-  const cuuint64_t strides[2] = {(cuuint64_t)R, (cuuint64_t)R * n_chans};
-  const cuuint32_t box[3] = {(cuuint32_t)box_rows, (cuuint32_t)box_chans,
-                             (cuuint32_t)herk_ring_stage()};
-  const cuuint32_t estr[3] = {1u, 1u, 1u};
-  return encode(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<uint8_t*>(x), dims, strides, box,
-                estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+cudaError_t herk_scratch_alloc(int2** p, int* ctas) {
+  int dev = 0, nsm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  *ctas = nsm;
+  return cudaMalloc(p, (size_t)nsm * kHerkScratchInt2 * sizeof(int2));
 }
 
 bool tci_direct(int layout, int bits, int n_inputs) {
   const int R = n_inputs * (bits / 4);  // byte rows per (spectrum, channel)
-  // The channel stride (R bytes) must suit TMA; stacked arrays fill a box
-  // exactly (16 or 32 byte rows), larger ones take boxes of 64 rows.  Above
-  // 384 byte rows (six row blocks) every block is read by many tasks, whose
-  // short time-major boxes then cost more than turning the block once
-  // (measured: 512 inputs at 8 bits, 2048 channels, 53 against 40 ms a block).
-  return layout == CORR_L_TCI && R % 16 == 0 && (R == 16 || R == 32 || (R >= 64 && R <= 384));
+  // The channel stride (R bytes) must suit TMA.  Stacked arrays fill a box
+  // exactly (R byte rows = one channel's rows of the 128-row block: 16 or 32
+  // at 4 bits, 16, 32 or 64 at 8 bits); larger ones take whole boxes of 64
+  // (4-bit) or 128 (8-bit) byte rows.  Above 384 byte rows every block is read by
+  // many tasks, whose short time-major boxes then cost more than turning the
+  // block once (measured at 4 bits; 512 inputs at 8 bits, 2048 channels: 53
+  // against 40 ms a block with the nibble-split operands).
+  if (layout != CORR_L_TCI || R % 16 != 0 || R > 384) return false;
+  const int box = bits == 8 ? 128 : 64;  // byte rows of a 128-row block
+  return R >= box || R == 16 || R == 32 || (bits == 8 && R == 64);
 }
 
-// Tasks of the real Gram matrix (n byte rows: 2n rows of Y): every 128 x 128
-// block (r, c), c <= r, of
-// the lower triangle exactly once.  Row block r takes the column blocks
+// Tasks of the real Gram matrix (n inputs: 2n rows of Y): every 128 x 128
+// block (r, c), c <= r, of the lower triangle exactly once.  Row block r takes the column blocks
 // r, r+1, ..., r + (nrb-1)/2 (mod nrb) -- for even nrb, r + nrb/2 goes to
 // the smaller of the two -- so the work is spread evenly over the row
 // blocks.  Columns r and r+1 form one 128 x 256 MMA task; further columns
@@ -173,6 +174,8 @@ struct corr_ctx {
   HerkTask* tasks = nullptr;
   int n_tasks = 0;
   int max_nblk = 1;
+  int2* scratch = nullptr;  // 8-bit: per-CTA partial sums of the cross-multiply
+  int scratch_ctas = 0;
   int rows_per_chan = 0;
   int smem_bytes = 0;
   int* d_status = nullptr;
@@ -296,6 +299,7 @@ void free_ctx(corr_ctx* x) {
   }
   cudaFree(x->turned);
   cudaFree(x->tasks);
+  cudaFree(x->scratch);
   cudaFree(x->d_status);
   cudaFree(x->rho_tmp);
   cudaFree(x->flag_tmp);
@@ -440,8 +444,9 @@ int corr_create(int n_inputs, int n_chans, int n_time, int bits, int layout, uns
       }
     }
     if (st != CORR_OK) break;
-    std::vector<HerkTask> tasks = plan_tasks(byte_rows, n_chans, &x->rows_per_chan);
+    std::vector<HerkTask> tasks = plan_tasks(n_inputs, n_chans, &x->rows_per_chan);
     x->n_tasks = (int)tasks.size();
+    if (bits == 8 && herk_scratch_alloc(&x->scratch, &x->scratch_ctas) != cudaSuccess) { st = CORR_ENOMEM; break; }
     x->max_nblk = tasks_max_nblk(tasks);
     if (cudaMalloc(&x->tasks, tasks.size() * sizeof(HerkTask)) != cudaSuccess) { st = CORR_ENOMEM; break; }
     if (cudaMemcpy(x->tasks, tasks.data(), tasks.size() * sizeof(HerkTask), cudaMemcpyHostToDevice) != cudaSuccess) { st = CORR_ECUDA; break; }
@@ -542,14 +547,13 @@ int corr_push(corr_ctx* x, const void* block, size_t nbytes, uint64_t seq) {
   a.n_tasks = x->n_tasks;
   a.max_nblk = x->max_nblk;
   a.bits = x->bits;
+  a.scratch = x->scratch;
+  a.scratch_ctas = x->scratch_ctas;
   // The TMA kernel needs 16-byte aligned rows; otherwise plain loads.
   CUtensorMap tmap;
   const bool aligned = row_stride % 16 == 0 && reinterpret_cast<uintptr_t>(src) % 16 == 0;
-  const int box_in = x->rows_per_chan ? x->rows_per_chan / 2 : 64;
-  const int box_ch = x->rows_per_chan ? 128 / x->rows_per_chan : 1;
-  const bool use_tma =
-      tci ? make_tci_tmap(&tmap, src, R, C, T, box_in, box_ch)
-          : aligned && make_sample_tmap(&tmap, src, T, row_stride, R, C, box_in, box_ch);
+  const bool use_tma = (tci || aligned) && make_herk_tmap(&tmap, src, tci, x->bits, R, C, T,
+                                                          row_stride, x->rows_per_chan);
   if ((eight || tci) && !use_tma) return CORR_ECUDA;  // these are always TMA-aligned
   const int chunk = eight ? kMaxChunk8 : kMaxChunk4;
   if (int g = guard_acc_write(x, hs)) return g;

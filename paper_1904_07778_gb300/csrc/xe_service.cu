@@ -136,6 +136,8 @@ struct corr_svc {
   int parity = 0;
   int* d_status = nullptr;
   int* h_status = nullptr;
+  int2* scratch = nullptr;  // 8-bit: per-CTA partial sums (the tick's launches run in order)
+  int scratch_ctas = 0;
   corr_svc_stats st{};
   std::vector<double> lat;
 };
@@ -195,17 +197,13 @@ void admit(corr_svc* s) {
     q.off_turn = t;
     q.slot = s->free_slots.back();
     s->free_slots.pop_back();
-    q.tasks = plan_tasks(q.R, q.r.n_chans, &q.rpc);
+    q.tasks = plan_tasks(q.r.n_inputs, q.r.n_chans, &q.rpc);
     q.max_nblk = tasks_max_nblk(q.tasks);
     if (!s->dry) {
       for (int b = 0; b < 2; ++b) {
         const uint8_t* x = q.has_turn ? s->base + q.off_turn : s->base + q.off_in[b];
-        if (q.tci)
-          make_tci_tmap(&q.tmap[b], x, q.R, q.r.n_chans, q.r.block_spectra, q.rpc ? q.rpc / 2 : 64,
-                        q.rpc ? 128 / q.rpc : 1);
-        else
-          make_sample_tmap(&q.tmap[b], x, q.r.block_spectra, q.stride, q.R, q.r.n_chans,
-                           q.rpc ? q.rpc / 2 : 64, q.rpc ? 128 / q.rpc : 1);
+        make_herk_tmap(&q.tmap[b], x, q.tci, q.r.bits, q.R, q.r.n_chans, q.r.block_spectra,
+                       q.stride, q.rpc);
         if (!q.ev_copy[b]) cudaEventCreateWithFlags(&q.ev_copy[b], cudaEventDisableTiming);
         if (!q.ev_used[b]) cudaEventCreateWithFlags(&q.ev_used[b], cudaEventDisableTiming);
       }
@@ -273,6 +271,7 @@ int corr_svc_create(size_t hbm_budget, unsigned flags, void* stream, corr_svc** 
       if (cudaMalloc(&s->d_status, sizeof(int)) != cudaSuccess ||
           cudaMallocHost(&s->h_status, sizeof(int)) != cudaSuccess) { st = CORR_ENOMEM; break; }
       if (cudaMemset(s->d_status, 0, sizeof(int)) != cudaSuccess) { st = CORR_ECUDA; break; }
+      if (herk_scratch_alloc(&s->scratch, &s->scratch_ctas) != cudaSuccess) { st = CORR_ENOMEM; break; }
       for (int p = 0; p < 2 && st == CORR_OK; ++p) {
         if (cudaMalloc(&s->d_insts[p], sizeof(HerkInst) * 2 * kMaxSlots) != cudaSuccess ||
             cudaMalloc(&s->d_tmaps[p], sizeof(CUtensorMap) * 2 * kMaxSlots) != cudaSuccess ||
@@ -422,7 +421,8 @@ int corr_svc_tick(corr_svc* s, int* n_requests) {
           t.inst = inst;
           const int nb = t.cb[1] >= 0 ? 2 : 1;
           const bool a_in = t.rb == t.cb[0] || (nb == 2 && t.rb == t.cb[1]);
-          cost.push_back((double)((q->r.block_spectra + 127) / 128) * (a_in ? nb : nb + 1));
+          const int st = herk_ring_stage(q->r.bits);
+          cost.push_back((double)((q->r.block_spectra + st - 1) / st) * (a_in ? nb : nb + 1));
           all.push_back(t);
         }
       }
@@ -456,6 +456,8 @@ int corr_svc_tick(corr_svc* s, int* n_requests) {
       a.n_tasks = l.nt;
       a.max_nblk = l.max_nblk;
       a.grid = l.nc;
+      a.scratch = s->scratch;
+      a.scratch_ctas = s->scratch_ctas;
       if (herk4_launch(a, nullptr, l.nt, s->stream, l.tci) != cudaSuccess) return CORR_ECUDA;
       ++launches;
     }
@@ -579,6 +581,7 @@ void corr_svc_destroy(corr_svc* s) {
   }
   cudaFree(s->base);
   cudaFree(s->d_status);
+  cudaFree(s->scratch);
   if (s->h_status) cudaFreeHost(s->h_status);
   if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
   if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);

@@ -69,7 +69,7 @@ def test_batch_graph_replays_and_plain_form(xe, shapes):
 
 
 PAYLOAD4 = [(32, 64, 1024, 4, 0), (64, 48, 512, 4, 0), (192, 6, 256, 4, 0), (16, 20, 300, 4, 0)]
-PAYLOAD8 = [(16, 8, 128, 8, 0), (48, 4, 256, 8, 0), (192, 2, 96, 8, 0)]
+PAYLOAD8 = [(16, 8, 128, 8, 0), (32, 6, 1100, 8, 0), (64, 4, 256, 8, 0), (192, 2, 96, 8, 0)]
 
 
 @pytest.mark.parametrize("shapes", [PAYLOAD4, PAYLOAD8], ids=["4bit", "8bit"])

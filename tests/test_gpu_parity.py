@@ -257,10 +257,12 @@ def _run8(xe, blocks, N, C, T, layout, device_input=True):
 
 
 SHAPES8 = [
-    # (N, C, T): stacked (4N <= 64), one block, several blocks, even and odd block counts
-    # (8, 16, 32, 48, 64, 192 inputs in [t][c][i] are read in payload order)
+    # (N, C, T): stacked (2N <= 64), one block, several blocks, even and odd block counts,
+    # ragged 64-spectrum stages (8, 16, 32, 64, 96, 192 inputs in [t][c][i] are read in
+    # payload order)
     (1, 3, 5), (2, 5, 130), (7, 4, 257), (8, 5, 99), (16, 3, 256), (17, 2, 100), (32, 2, 384),
-    (33, 2, 200), (48, 2, 129), (64, 2, 256), (100, 1, 300), (192, 1, 160), (192, 2, 77),
+    (33, 2, 200), (48, 2, 129), (64, 2, 256), (96, 3, 65), (100, 1, 300), (192, 1, 160),
+    (192, 2, 77),
 ]
 
 
@@ -272,6 +274,33 @@ def test_eight_bit_bit_exact(xe, N, C, T, layout):
     got = _run8(xe, [blk], N, C, T, layout)
     want = oracle.correlate(blk, N, C, T, bits=8, layout=layout)
     assert np.array_equal(got, want)
+
+
+LONG8 = [
+    # (N, C, T): tasks of several 1024-spectrum accumulations, a ragged last one
+    (8, 3, 2100), (16, 2, 1025), (32, 2, 3000), (40, 2, 2049), (64, 2, 1500), (192, 1, 2500),
+]
+
+
+@pytest.mark.parametrize("N,C,T", LONG8)
+@pytest.mark.parametrize("layout", [0, 1, 2])
+def test_eight_bit_long_tasks(xe, N, C, T, layout):
+    """8-bit tasks longer than one 1024-spectrum accumulation: the pieces are
+    added as integers in the CTA's scratch before the last goes out."""
+    blk = _sym8(8000 + N * 10 + T + layout, 2 * N * C * T)
+    got = _run8(xe, [blk], N, C, T, layout)
+    assert np.array_equal(got, oracle.correlate(blk, N, C, T, bits=8, layout=layout))
+
+
+def test_eight_bit_full_scale_accumulations(xe):
+    """Full-scale codes at the limit of one FP32 accumulation (127^2 x 1024
+    spectra, just below 2^24) and a block that ends one spectrum later, in
+    both the payload order and the turned layout."""
+    for N, C, T, layout in [(32, 2, 1024, 0), (32, 2, 1025, 0), (64, 1, 1088, 1)]:
+        a = np.full(2 * N * C * T, 127, np.int8).view(np.uint8)
+        a[1::7] = np.uint8(0x81)  # -127 mixed in
+        got = _run8(xe, [a], N, C, T, layout)
+        assert np.array_equal(got, oracle.correlate(a, N, C, T, bits=8, layout=layout)), (N, T)
 
 
 def test_eight_bit_extremes_and_chunking(xe):
@@ -306,7 +335,7 @@ def test_eight_bit_minus_128_reported(xe):
 
 
 def test_eight_bit_512_inputs(xe):
-    """512 inputs (2048 rows of the real Gram, 16 row blocks), full parity."""
+    """512 inputs (1024 rows of the real Gram, 8 row blocks), full parity."""
     N, C, T = 512, 2, 1024
     blk = _sym8(512, 2 * N * C * T)
     got = _run8(xe, [blk], N, C, T, 0)
@@ -353,8 +382,8 @@ def test_dump_leaves_neighbouring_memory_alone(xe):
 
 @pytest.mark.parametrize("bits,N,C,T", [(4, 1024, 2, 256), (8, 1024, 1, 128)])
 def test_maximum_input_count(xe, bits, N, C, T):
-    """1024 inputs, the largest the ABI accepts: 16 (4-bit) and 32 (8-bit)
-    row blocks of the real Gram, every tile kind of the schedule."""
+    """1024 inputs, the largest the ABI accepts: 16 row blocks of the real
+    Gram at either width, every tile kind of the schedule."""
     if bits == 4:
         blk = synth.random_bytes(1024 + bits, N * C * T)
     else:
