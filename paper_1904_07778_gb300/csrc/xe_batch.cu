@@ -39,10 +39,10 @@ struct corr_batch {
   // batched launch: all tasks, grouped per CTA
   HerkTask* d_tasks = nullptr;
   int* d_cta_first = nullptr;
-  int n_tasks = 0, n_ctas = 0, max_nblk = 1;
+  int n_tasks = 0, n_ctas = 0;
   // plain form: each array's own task list
   std::vector<HerkTask*> d_tasks_one;
-  std::vector<int> n_tasks_one, max_nblk_one;
+  std::vector<int> n_tasks_one;
   int schedule = CORR_SCHED_PAIRS_LPT;
   double tuned_ms[3] = {0, 0, 0};
   int tune_source = 0;
@@ -58,7 +58,7 @@ struct corr_batch {
   int pipe_sms = 0, pipe_inst = -1;
   std::vector<int> pipe_c;
   std::vector<HerkTask*> d_pipe_tasks;
-  std::vector<int> n_pipe_tasks, max_nblk_pipe;
+  std::vector<int> n_pipe_tasks;
   cudaStream_t turn_stream = nullptr;
   std::vector<cudaEvent_t> pipe_ev;  // [0] fork, [1 + j] range j turned
 };
@@ -108,13 +108,11 @@ double task_cost(const HerkTask& t, const HerkInst& in, int bits) {
 int build_schedule(corr_batch* b, int sched) {
   std::vector<HerkTask> all;
   std::vector<double> cost;
-  int max_nblk = 1;
   for (int k = 0; k < b->n; ++k) {
     int rpc = 0;
     const corr_shape& sh = b->shapes[k];
     std::vector<HerkTask> t =
         plan_tasks(sh.n_inputs, sh.n_chans, &rpc, sched == CORR_SCHED_SINGLES_LPT);
-    max_nblk = std::max(max_nblk, tasks_max_nblk(t));
     for (HerkTask& x : t) {
       x.inst = k;
       cost.push_back(task_cost(x, b->insts[k], b->bits));
@@ -151,7 +149,6 @@ int build_schedule(corr_batch* b, int sched) {
     return CORR_ECUDA;
   b->n_tasks = nt;
   b->n_ctas = nc;
-  b->max_nblk = max_nblk;
   b->schedule = sched;
   return CORR_OK;
 }
@@ -167,7 +164,6 @@ HerkArgs batched_args(const corr_batch* b) {
   a.lo_is_real = (b->flags & CORR_F_LO_IS_REAL) ? 1 : 0;
   a.bits = b->bits;
   a.n_tasks = b->n_tasks;
-  a.max_nblk = b->max_nblk;
   a.grid = b->n_ctas;
   a.scratch = b->scratch;
   a.scratch_ctas = b->scratch_ctas;
@@ -226,7 +222,6 @@ cudaError_t enqueue_pipelined(corr_batch* b) {
     if (b->n_pipe_tasks[j] == 0) continue;
     a.tasks = b->d_pipe_tasks[j];
     a.n_tasks = b->n_pipe_tasks[j];
-    a.max_nblk = b->max_nblk_pipe[j];
     if ((e = herk4_launch(a, nullptr, a.n_tasks, b->stream)) != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -412,7 +407,6 @@ int corr_batch_create(const corr_shape* shapes, int n, void* stream, int tune, c
     b->tmaps.resize(n);
     b->d_tasks_one.assign(n, nullptr);
     b->n_tasks_one.assign(n, 0);
-    b->max_nblk_one.assign(n, 1);
     for (int k = 0; k < n && st == CORR_OK; ++k) {
       const corr_shape& s = shapes[k];
       const int R = s.n_inputs * (s.bits / 4);
@@ -444,7 +438,6 @@ int corr_batch_create(const corr_shape* shapes, int n, void* stream, int tune, c
       in.vec_ok = 1;
       if (!make_herk_tmap(&b->tmaps[k], x, b->tci, s.bits, R, s.n_chans, s.n_time, stride, rpc)) { st = CORR_ECUDA; break; }
       b->n_tasks_one[k] = (int)t.size();
-      b->max_nblk_one[k] = tasks_max_nblk(t);
       if (cudaMalloc(&b->d_tasks_one[k], sizeof(HerkTask) * t.size()) != cudaSuccess) { st = CORR_ENOMEM; break; }
       if (cudaMemcpy(b->d_tasks_one[k], t.data(), sizeof(HerkTask) * t.size(), cudaMemcpyHostToDevice) != cudaSuccess) { st = CORR_ECUDA; break; }
     }
@@ -546,7 +539,6 @@ int corr_batch_run_plain(corr_batch* b) {
     a.lo_is_real = (b->flags & CORR_F_LO_IS_REAL) ? 1 : 0;
     a.bits = b->bits;
     a.n_tasks = b->n_tasks_one[k];
-    a.max_nblk = b->max_nblk_one[k];
     a.scratch = b->scratch;
     a.scratch_ctas = b->scratch_ctas;
     if (herk4_launch(a, &b->tmaps[k], a.n_tasks, b->stream, b->tci) != cudaSuccess) return CORR_ECUDA;
@@ -606,7 +598,7 @@ int corr_batch_set_pipeline(corr_batch* b, int turn_sms, int n_chunks) {
   // replaced it; on an early error the old graph and its lists stay as they
   // were.
   std::vector<HerkTask*> d_new(lists.size(), nullptr);
-  std::vector<int> n_new(lists.size(), 0), nblk_new(lists.size(), 1);
+  std::vector<int> n_new(lists.size(), 0);
   auto drop_new = [&](int st) {
     for (auto p : d_new) cudaFree(p);
     cudaGetLastError();
@@ -615,7 +607,6 @@ int corr_batch_set_pipeline(corr_batch* b, int turn_sms, int n_chunks) {
   for (size_t j = 0; j < lists.size(); ++j) {
     n_new[j] = (int)lists[j].size();
     if (lists[j].empty()) continue;
-    nblk_new[j] = tasks_max_nblk(lists[j]);
     if (cudaMalloc(&d_new[j], sizeof(HerkTask) * lists[j].size()) != cudaSuccess) {
       d_new[j] = nullptr;
       return drop_new(CORR_ENOMEM);
@@ -637,7 +628,6 @@ int corr_batch_set_pipeline(corr_batch* b, int turn_sms, int n_chunks) {
   d_old.swap(b->d_pipe_tasks);
   b->d_pipe_tasks = d_new;
   b->n_pipe_tasks = n_new;
-  b->max_nblk_pipe = nblk_new;
   b->pipe_inst = k;
   b->pipe_c = c;
   b->pipe_sms = turn_sms;

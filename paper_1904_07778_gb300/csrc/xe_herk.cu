@@ -54,10 +54,11 @@ constexpr int kOpBlockBytes = 128 * kStageT;  // unpacked: 128 rows x 128 spectr
 
 struct TaskGeom {
   int nb;       // column blocks (1 or 2) = B slots 0..nb-1
-  int nblk;     // resident 128-row blocks per stage
+  int nblk;     // distinct 128-row blocks of the task
   int a_slot;   // slot holding the A rows
   int rb;       // A row block
   int cb0, cb1; // column blocks of slots 0 and 1
+  int dbl;      // ring kernel: one block (A = B), a stage holds two time ranges of it
   uint32_t ncols;
 };
 
@@ -69,6 +70,7 @@ __device__ __forceinline__ TaskGeom task_geom(const HerkTask& t) {
   g.cb1 = t.cb[1];
   g.a_slot = t.rb == t.cb[0] ? 0 : (g.nb == 2 && t.rb == t.cb[1] ? 1 : g.nb);
   g.nblk = g.a_slot == g.nb ? g.nb + 1 : g.nb;
+  g.dbl = g.nblk == 1 ? 1 : 0;
   g.ncols = g.nb == 1 ? 128u : 256u;
   return g;
 }
@@ -415,19 +417,20 @@ __device__ __forceinline__ void ctrl_init_common(Ctrl& sm, int tid) {
 
 // ------------------------------------------------------------- ring kernel
 // Persistent: one CTA per SM walks the tasks blockIdx.x, blockIdx.x + grid,
-// ...; stage S counts the stages (128 spectra at 4 bits, 64 at 8 bits) of all
-// its tasks in order.  Shared memory is one ring of slots of max_nblk operand
-// blocks.  Stage S uses slot S mod ns:
+// ...; stage S counts the stages of all its tasks in order (128 spectra at 4
+// bits, 64 at 8 bits, twice that for the double stages of one-block tasks).
+// Shared memory is one ring of 32 KB slots, each holding the two units of a
+// stage (see kSlotBytes).  Stage S uses slot S mod ns:
 //   warp 17 (TMA)     waits until the MMAs of stage S - ns have finished with
 //                     the slot, then loads the packed bytes of stage S into
-//                     its upper half (packed block b at nblk + b eighths);
+//                     its upper half;
 //   group S mod 4     (warps 4g .. 4g + 3) waits for the same MMA completion
-//                     and for the bytes, reads all of them into registers,
-//                     meets at a group barrier, and writes the swizzled
-//                     operands over them, in place;
-//   warp 16 (MMA)     issues the four MMAs of the stage into one of two
-//                     256-column tensor-memory accumulators (accumulations
-//                     alternate) and commits the slot back;
+//                     and for the bytes, converts unit 0 into the lower half,
+//                     reads unit 1 into registers, meets at a group barrier,
+//                     and writes unit 1's operands over the packed bytes;
+//   warp 16 (MMA)     issues the four (double stage: eight) MMAs of the stage
+//                     into one of two 256-column tensor-memory accumulators
+//                     (accumulations alternate) and commits the slot back;
 //   warps 20..27      (drain) convert accumulation v while accumulation v + 1
 //                     is being multiplied (warps 18, 19 only complete the
 //                     warpgroup of warps 16, 17).
@@ -456,7 +459,13 @@ constexpr int kUnpackWarps = kGroups * kGroupWarps;
 // rows x 64 spectra), and a stage takes four MMAs of K = 32 bytes per row.
 constexpr int kROpBlock = 128 * 128;  // operands of a 128-row block
 constexpr int kRPkBlock = 64 * 128;   // packed bytes of a 128-row block
-constexpr int kRKSteps = 4;           // MMAs per stage
+constexpr int kRKSteps = 4;           // MMAs per 128-row block and time range
+// A ring slot holds two units of one stage: the two 128-row blocks of a
+// two-block task, or for a one-block task (A = B) the same rows over two
+// consecutive time ranges ("double" stages: half the stages, so half the
+// per-stage hand-offs, for tasks that would move only 8 KB a stage).
+// Operands of unit u at [16 u, 16 u + 16) KB, packed bytes at [16 + 8 u, 24 + 8 u) KB.
+constexpr int kSlotBytes = 2 * kROpBlock;
 template <bool EIGHT>
 __host__ __device__ constexpr int stage_t() {  // spectra per stage
   return EIGHT ? 64 : 128;
@@ -470,22 +479,23 @@ static_assert(kGroupThreads == 128, "an unpack group covers a packed block in fo
 constexpr int kMmaWarp = kUnpackWarps, kTmaWarp = kUnpackWarps + 1, kEpiWarp0 = kUnpackWarps + 4;
 constexpr int kEpiWarps = XE_EPI_WARPS;
 constexpr int kRingThreads = (kEpiWarp0 + kEpiWarps) * 32;
-// registers per thread: launch share, unpack warpgroups, the other warpgroups
-// (the 8-bit drain, which adds the accumulations' partial sums, takes more,
-// the 8-bit unpack less)
+// registers per thread: launch share, unpack warpgroups, the other warpgroups.
+// Chosen per instance from the compiler's spill report and measured times:
+// the 8-bit drain, which adds the accumulations' partial sums, takes more,
+// the 8-bit unpack less; the low-nibble-real 4-bit unpack needs 88.
 constexpr int kRegsLaunch = (65536 / kRingThreads) & ~7;
-template <bool EIGHT>
-__host__ __device__ constexpr int regs_unpack() { return EIGHT ? 72 : 80; }
-template <bool EIGHT>
-__host__ __device__ constexpr int regs_other() { return EIGHT ? 64 : 56; }
+template <bool LO, bool EIGHT>
+__host__ __device__ constexpr int regs_unpack() { return EIGHT ? 72 : (LO ? 88 : 80); }
+template <bool LO, bool EIGHT>
+__host__ __device__ constexpr int regs_other() { return EIGHT ? 64 : (LO ? 48 : 56); }
 static_assert(kRingThreads % 128 == 0, "whole warpgroups");
-template <bool EIGHT>
+template <bool LO, bool EIGHT>
 constexpr bool regs_fit() {
-  return kUnpackWarps * 32 * regs_unpack<EIGHT>() +
-             (kRingThreads - kUnpackWarps * 32) * regs_other<EIGHT>() <=
+  return kUnpackWarps * 32 * regs_unpack<LO, EIGHT>() +
+             (kRingThreads - kUnpackWarps * 32) * regs_other<LO, EIGHT>() <=
          kRingThreads * kRegsLaunch;
 }
-static_assert(regs_fit<false>() && regs_fit<true>(),
+static_assert(regs_fit<false, false>() && regs_fit<true, false>() && regs_fit<false, true>(),
               "the register split must fit in the launch allocation");
 #ifndef XE_MAX_SLOTS
 #define XE_MAX_SLOTS 16
@@ -520,15 +530,21 @@ __device__ __forceinline__ int my_task_count(const HerkArgs& a) {
 __device__ __forceinline__ HerkInst task_inst(const HerkArgs& a, const HerkTask& t) {
   return a.insts ? a.insts[t.inst] : a.in;
 }
+// Stages of a task: stage_t spectra each, twice that for double stages.
 template <bool EIGHT>
-__device__ __forceinline__ int stages_of(const HerkInst& in) {
-  return (in.tn + stage_t<EIGHT>() - 1) / stage_t<EIGHT>();
+__device__ __forceinline__ int stages_of(const HerkInst& in, int dbl) {
+  const int ts = stage_t<EIGHT>() << dbl;
+  return (in.tn + ts - 1) / ts;
 }
 // Accumulations of a task of nk stages (at least one, so that every role
-// counts the same sequence).
+// counts the same sequence) and the stages of one.
 template <bool EIGHT>
-__device__ __forceinline__ int pieces_of(int nk) {
-  return EIGHT ? max(1, (nk + kPieceStages8 - 1) / kPieceStages8) : 1;
+__device__ __forceinline__ int piece_stages(int dbl) {
+  return kPieceStages8 >> dbl;
+}
+template <bool EIGHT>
+__device__ __forceinline__ int pieces_of(int nk, int dbl) {
+  return EIGHT ? max(1, (nk + piece_stages<EIGHT>(dbl) - 1) / piece_stages<EIGHT>(dbl)) : 1;
 }
 
 // TCI: the tensor maps describe payload-order blocks ({byte row, channel,
@@ -546,7 +562,7 @@ __global__ void __launch_bounds__(kRingThreads, 1)
   uint8_t* ring = align1024(dyn_raw);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int n_my = my_task_count(a);  // tasks of this CTA; stage counts vary per array
-  const int slot_bytes = a.max_nblk * kROpBlock;
+  constexpr int slot_bytes = kSlotBytes;
   int ns = (int)(reinterpret_cast<uint8_t*>(&sm) - ring) / slot_bytes;
   if (ns > kMaxSlots) ns = kMaxSlots;
   if (ns < kGroups) {  // the host sizes shared memory for at least four slots
@@ -585,7 +601,7 @@ __global__ void __launch_bounds__(kRingThreads, 1)
   // joined again would leave the compiler the smaller budget for all roles.
   if (warp == kTmaWarp) {
     // ------------------------------------------------------------ TMA loader
-    regs_shrink<regs_other<EIGHT>()>();
+    regs_shrink<regs_other<LO_IS_REAL, EIGHT>()>();
     if (lane == 0 && n_my > 0) {
       if (!a.tmaps) tma_prefetch_desc(&tmap);
       // fault injection: this stage of CTA 0 is never loaded, so the waits
@@ -597,7 +613,7 @@ __global__ void __launch_bounds__(kRingThreads, 1)
       HerkInst in = task_inst(a, task);
       const CUtensorMap* tm = a.tmaps ? &a.tmaps[task.inst] : &tmap;
       if (a.tmaps) tensormap_acquire(tm);
-      int nk = stages_of<EIGHT>(in);
+      int nk = stages_of<EIGHT>(in, g.dbl);
       bool stacked = in.rows_per_chan > 0;
       for (int S = 0;; ++S, ++k) {
         if (k == nk) {  // next task
@@ -608,25 +624,27 @@ __global__ void __launch_bounds__(kRingThreads, 1)
           in = task_inst(a, task);
           tm = a.tmaps ? &a.tmaps[task.inst] : &tmap;
           if (a.tmaps) tensormap_acquire(tm);
-          nk = stages_of<EIGHT>(in);
+          nk = stages_of<EIGHT>(in, g.dbl);
           stacked = in.rows_per_chan > 0;
         }
         if (m > 0 && !mbar_wait(&sm.empty[s], (uint32_t)((m - 1) & 1), abort, budget)) {
           raise_timeout(a.status, abort);
           break;
         }
-        const int t = in.t0 + k * kT;
-        const uint32_t dst0 = ring_addr + (uint32_t)(s * slot_bytes + g.nblk * kRPkBlock);
+        const int t = in.t0 + k * (kT << g.dbl);
+        const uint32_t dst0 = ring_addr + (uint32_t)(s * slot_bytes + 2 * kRPkBlock);
         if (S != skip) {
-          mbar_expect_tx(&sm.full_t[s], (uint32_t)(g.nblk * kRPkBlock));
-          for (int b = 0; b < g.nblk; ++b) {
-            const uint32_t dst = dst0 + (uint32_t)(b * kRPkBlock);
-            // byte rows of a 128-row block: 64 (4-bit) or 128 (8-bit)
-            const int row0 = stacked ? 0 : (kRPkBlock / kPkRowBytes) * slot_block(g, b);
+          mbar_expect_tx(&sm.full_t[s], (uint32_t)(2 * kRPkBlock));
+          for (int u = 0; u < 2; ++u) {
+            const uint32_t dst = dst0 + (uint32_t)(u * kRPkBlock);
+            // unit u: block u, or the block's second time range
+            // (byte rows of a 128-row block: 64 at 4 bits, 128 at 8 bits)
+            const int row0 = stacked ? 0 : (kRPkBlock / kPkRowBytes) * slot_block(g, g.dbl ? 0 : u);
+            const int tu = t + (g.dbl ? u * kT : 0);
             if (TCI)
-              tma_load_3d(dst, tm, row0, task.chan0, t, &sm.full_t[s]);
+              tma_load_3d(dst, tm, row0, task.chan0, tu, &sm.full_t[s]);
             else
-              tma_load_3d(dst, tm, t, row0, task.chan0, &sm.full_t[s]);
+              tma_load_3d(dst, tm, tu, row0, task.chan0, &sm.full_t[s]);
           }
         }
         ++issued;
@@ -643,20 +661,20 @@ __global__ void __launch_bounds__(kRingThreads, 1)
     __syncwarp();
   } else if (warp == kMmaWarp) {
     // ------------------------------------------------------------ MMA issuer
-    regs_shrink<regs_other<EIGHT>()>();
+    regs_shrink<regs_other<LO_IS_REAL, EIGHT>()>();
     if (lane == 0) {
       int s = 0, m = 0, v = 0;  // v: accumulations so far (tensor-memory buffer v & 1)
       bool ok = true;
       for (int j = 0; j < n_my && ok; ++j) {
         const HerkTask task = my_task(a, j);
         const TaskGeom g = task_geom(task);
-        const int nk = stages_of<EIGHT>(task_inst(a, task));
-        const int np = pieces_of<EIGHT>(nk);
+        const int nk = stages_of<EIGHT>(task_inst(a, task), g.dbl);
+        const int np = pieces_of<EIGHT>(nk, g.dbl);
         const uint32_t idesc = umma_idesc(0, 128, 128 * g.nb);
         for (int q = 0; q < np && ok; ++q, ++v) {
           const int b = v & 1;
-          const int k0 = EIGHT ? q * kPieceStages8 : 0;
-          const int k1 = EIGHT ? min(nk, k0 + kPieceStages8) : nk;
+          const int k0 = EIGHT ? q * piece_stages<EIGHT>(g.dbl) : 0;
+          const int k1 = EIGHT ? min(nk, k0 + piece_stages<EIGHT>(g.dbl)) : nk;
           if (v >= 2 && !mbar_wait(&sm.tmem_empty[b], (uint32_t)(((v >> 1) - 1) & 1), abort, budget)) {
             raise_timeout(a.status, abort);
             ok = false;
@@ -664,29 +682,42 @@ __global__ void __launch_bounds__(kRingThreads, 1)
           }
           tc_after_sync();
           const uint32_t d = tmem + (uint32_t)(b * 256);
-          for (int k = k0; k < k1; ++k) {
-            if (!mbar_wait(&sm.full_o[s], (uint32_t)(m & 1), abort, budget)) {
-              raise_timeout(a.status, abort);
-              ok = false;
-              break;
-            }
-            tc_after_sync();
-            const uint32_t st = ring_addr + (uint32_t)(s * slot_bytes);
-            const uint64_t adesc = umma_desc_sw128(st + (uint32_t)(g.a_slot * kROpBlock));
-            const uint64_t bdesc = umma_desc_sw128(st);
+          // the stages of this accumulation, DBL a constant (no per-MMA selects)
+          auto issue = [&](auto DBL) {
+            constexpr bool dbl = decltype(DBL)::value;
+            for (int k = k0; k < k1; ++k) {
+              if (!mbar_wait(&sm.full_o[s], (uint32_t)(m & 1), abort, budget)) {
+                raise_timeout(a.status, abort);
+                ok = false;
+                break;
+              }
+              tc_after_sync();
+              const uint32_t st = ring_addr + (uint32_t)(s * slot_bytes);
+              // two-block task: A in slot a_slot, B in both; double stage:
+              // A = B, the second time range in unit 1
+              const uint64_t bdesc = umma_desc_sw128(st);
+              const uint64_t adesc = dbl ? bdesc : umma_desc_sw128(st + (uint32_t)(g.a_slot * kROpBlock));
 #pragma unroll
-            for (int kk = 0; kk < kRKSteps; ++kk) {
-              if (EIGHT)
-                umma_f16(d, adesc + 2 * kk, bdesc + 2 * kk, idesc, (k != k0 || kk != 0));
-              else
-                umma_f8(d, adesc + 2 * kk, bdesc + 2 * kk, idesc, (k != k0 || kk != 0));
+              for (int kk = 0; kk < (dbl ? 2 : 1) * kRKSteps; ++kk) {
+                const uint64_t da = dbl ? bdesc + (uint64_t)((kk >> 2) * (kROpBlock >> 4) + 2 * (kk & 3))
+                                        : adesc + 2 * kk;
+                const uint64_t db = dbl ? da : bdesc + 2 * kk;
+                if (EIGHT)
+                  umma_f16(d, da, db, idesc, (k != k0 || kk != 0));
+                else
+                  umma_f8(d, da, db, idesc, (k != k0 || kk != 0));
+              }
+              umma_commit(&sm.empty[s]);
+              if (++s == ns) {
+                s = 0;
+                ++m;
+              }
             }
-            umma_commit(&sm.empty[s]);
-            if (++s == ns) {
-              s = 0;
-              ++m;
-            }
-          }
+          };
+          if (g.dbl)
+            issue(std::true_type{});
+          else
+            issue(std::false_type{});
           if (ok) umma_commit(&sm.tmem_full[b]);
         }
       }
@@ -697,7 +728,7 @@ __global__ void __launch_bounds__(kRingThreads, 1)
     __syncwarp();
   } else if (warp < kUnpackWarps) {
     // ------------------------------------------------------------ unpackers
-    regs_grow<regs_unpack<EIGHT>()>();
+    regs_grow<regs_unpack<LO_IS_REAL, EIGHT>()>();
     const int grp = warp / kGroupWarps;
     const int gt = tid - grp * kGroupThreads;
     // Item geometry of this thread (four 16-byte items per packed block).
@@ -731,7 +762,8 @@ __global__ void __launch_bounds__(kRingThreads, 1)
       const HerkTask task = my_task(a, j);
       const TaskGeom g = task_geom(task);
       const int tn = task_inst(a, task).tn;
-      const int S1 = S0 + (tn + kT - 1) / kT;
+      const int kTs = kT << g.dbl;  // spectra per stage of this task
+      const int S1 = S0 + (tn + kTs - 1) / kTs;
       const int nit = g.nblk * 4;
       int32_t sre[kItems], sim[kItems];
 #pragma unroll
@@ -743,21 +775,12 @@ __global__ void __launch_bounds__(kRingThreads, 1)
                    mbar_wait(&sm.full_t[s], (uint32_t)(m & 1), abort, budget);
         if (!got) raise_timeout(a.status, abort);
         const uint32_t so = (uint32_t)(s * slot_bytes);
-        const bool tail = (k + 1) * kT > tn;
-        // Operand block 0 of a two-block stage overlaps neither packed block
+        const bool tail = (k + 1) * kTs > tn;
+        // The operands of unit 0 overlap neither unit's packed bytes
         // (operands [0, 16 KB) and [16, 32 KB), packed bytes [16, 32 KB)), so
-        // it is written before the group barrier; the barrier then only
-        // guards the block whose operands cover packed bytes.
-        uint32_t keep[4] = {~0u, ~0u, ~0u, ~0u};
-        if (tail) {
-          if (TCI && EIGHT)
-            tci8_keep(c8, sw8, tn - k * kT, keep);
-          else if (TCI)
-            tci_keep(tc, k * kT, tn, keep);
-          else
-            time_keep(k * kT + (EIGHT ? c4 : chunk) * 16, tn, keep);
-        }
-        const uint32_t pk = ring_addr + so + (uint32_t)(g.nblk * kRPkBlock);
+        // they are written before the group barrier; the barrier then only
+        // guards unit 1, whose operands cover packed bytes.
+        const uint32_t pk = ring_addr + so + (uint32_t)(2 * kRPkBlock);
         uint32_t wv[16];  // this thread's 64 packed bytes of one block
         // load the items of block it
         auto load = [&](int it) {
@@ -770,17 +793,29 @@ __global__ void __launch_bounds__(kRingThreads, 1)
           } else {  // 4 items of 16 bytes: byte rows 16 (4-bit) or 32 (8-bit) apart
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-              const uint4 v = lds128(src0 + so + (uint32_t)(g.nblk * kRPkBlock) +
+              const uint4 v = lds128(src0 + so + (uint32_t)(2 * kRPkBlock) +
                                      (uint32_t)(2048 * (4 * it + q)));
               wv[4 * q] = v.x, wv[4 * q + 1] = v.y, wv[4 * q + 2] = v.z, wv[4 * q + 3] = v.w;
             }
           }
         };
-        // convert block IT and write its operands (IT a constant: the row
-        // sums stay in registers)
+        // convert unit IT and write its operands (IT a constant: the row
+        // sums stay in registers; a double stage's second time range adds to
+        // the sums of unit 1 and is folded into unit 0's at the task's end)
         auto store = [&](auto IT) {
           constexpr int it = decltype(IT)::value;
-          const uint32_t ob = ring_addr + so + (uint32_t)(it * kROpBlock);
+          [[maybe_unused]] const uint32_t ob = ring_addr + so + (uint32_t)(it * kROpBlock);
+          // masks of the unit's spectra (off: the unit's first spectrum in the task)
+          uint32_t keep[4] = {~0u, ~0u, ~0u, ~0u};
+          if (tail) {
+            const int off = k * kTs + (it == 1 && g.dbl ? kT : 0);
+            if (TCI && EIGHT)
+              tci8_keep(c8, sw8, tn - off, keep);
+            else if (TCI)
+              tci_keep(tc, off, tn, keep);
+            else
+              time_keep(off + (EIGHT ? c4 : chunk) * 16, tn, keep);
+          }
           if constexpr (TCI) {
 #pragma unroll
             for (int gg = 0; gg < 4; ++gg)
@@ -800,9 +835,9 @@ __global__ void __launch_bounds__(kRingThreads, 1)
                 sts128(ob + swz_offset(r, 2 * c8 + sw), h[0], h[1], h[2], h[3]);
                 sts128(ob + swz_offset(r, 2 * c8 + 1 - sw), h[4], h[5], h[6], h[7]);
               } else {
-                const uint32_t o = (uint32_t)(4096 * u);  // 32 operand rows on
-                sts128(dst_a + so + (uint32_t)(it * kROpBlock) + o, h[0], h[1], h[2], h[3]);
-                sts128(dst_b + so + (uint32_t)(it * kROpBlock) + o, h[4], h[5], h[6], h[7]);
+                const uint32_t o = so + (uint32_t)(it * kROpBlock + 4096 * u);  // 32 operand rows on
+                sts128(dst_a + o, h[0], h[1], h[2], h[3]);
+                sts128(dst_b + o, h[4], h[5], h[6], h[7]);
               }
             } else {
               uint32_t re[4], im[4];
@@ -813,20 +848,17 @@ __global__ void __launch_bounds__(kRingThreads, 1)
                 sts128(ob + swz_offset(r, tc), re[0], re[1], re[2], re[3]);
                 sts128(ob + swz_offset(r + 1, tc), im[0], im[1], im[2], im[3]);
               } else {
-                const uint32_t o = (uint32_t)(4096 * u);
-                sts128(dst_a + so + (uint32_t)(it * kROpBlock) + o, re[0], re[1], re[2], re[3]);
-                sts128(dst_b + so + (uint32_t)(it * kROpBlock) + o, im[0], im[1], im[2], im[3]);
+                const uint32_t o = so + (uint32_t)(it * kROpBlock + 4096 * u);
+                sts128(dst_a + o, re[0], re[1], re[2], re[3]);
+                sts128(dst_b + o, im[0], im[1], im[2], im[3]);
               }
             }
           }
         };
-        const bool two = g.nblk == 2;
         if (got) {
           load(0);
-          if (two) {
-            store(std::integral_constant<int, 0>{});
-            load(1);
-          }
+          store(std::integral_constant<int, 0>{});
+          load(1);
         }
         // every packed byte of the stage is in registers or converted before
         // any is overwritten; the group leaves together if any wait failed
@@ -834,10 +866,7 @@ __global__ void __launch_bounds__(kRingThreads, 1)
           ok = false;
           break;
         }
-        if (two)
-          store(std::integral_constant<int, 1>{});
-        else
-          store(std::integral_constant<int, 0>{});
+        store(std::integral_constant<int, 1>{});
         fence_smem_to_async();
         __syncwarp();
         if (lane == 0) mbar_arrive(&sm.full_o[s]);
@@ -850,6 +879,13 @@ __global__ void __launch_bounds__(kRingThreads, 1)
       if (!ok) break;
       S0 = S1;
       if constexpr (EIGHT) continue;  // signed operands: no row sums
+      if (g.dbl) {  // both time ranges of a double stage are block 0's rows
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          sre[u] += sre[4 + u];
+          sim[u] += sim[4 + u];
+        }
+      }
       // publish this task's row sums once the buffer is free again
       const bool freed = j < 2 || mbar_wait(&sm.usum_empty[b], (uint32_t)(((j >> 1) - 1) & 1), abort, budget);
       if (!freed) raise_timeout(a.status, abort);
@@ -878,10 +914,10 @@ __global__ void __launch_bounds__(kRingThreads, 1)
     }
     if (EIGHT && __any_sync(0xFFFFFFFFu, bad != 0) && lane == 0) atomicOr(a.status, kStRange);
   } else if (warp < kEpiWarp0) {
-    regs_shrink<regs_other<EIGHT>()>();  // the two idle warps of the MMA / TMA warpgroup
+    regs_shrink<regs_other<LO_IS_REAL, EIGHT>()>();  // the two idle warps of the MMA / TMA warpgroup
   } else {
     // ------------------------------------------------------------ drain
-    regs_shrink<regs_other<EIGHT>()>();
+    regs_shrink<regs_other<LO_IS_REAL, EIGHT>()>();
     const int quad = warp & 3, part = (warp - kEpiWarp0) >> 2;
     int2* scr = EIGHT ? a.scratch + (size_t)blockIdx.x * kHerkScratchInt2 : nullptr;
     int v = 0;
@@ -890,7 +926,7 @@ __global__ void __launch_bounds__(kRingThreads, 1)
       const HerkTask task = my_task(a, j);
       const HerkInst in = task_inst(a, task);
       const TaskGeom g = task_geom(task);
-      const int np = pieces_of<EIGHT>(stages_of<EIGHT>(in));
+      const int np = pieces_of<EIGHT>(stages_of<EIGHT>(in, g.dbl), g.dbl);
       for (int q = 0; q < np; ++q, ++v) {
         const int b = v & 1;
         const uint32_t par = (uint32_t)((v >> 1) & 1);
@@ -1109,8 +1145,8 @@ cudaError_t herk4_launch(const HerkArgs& args, const CUtensorMap* tmap, int n_ta
   if (tmap || args.tmaps) {
     HerkArgs a = args;
     a.smem_bytes = ring_smem();
-    // four slots of the largest stage, the control block and the alignment pad
-    if (a.smem_bytes < kGroups * a.max_nblk * kROpBlock + (int)sizeof(RingCtrl) + 1024)
+    // four slots, the control block and the alignment pad
+    if (a.smem_bytes < kGroups * kSlotBytes + (int)sizeof(RingCtrl) + 1024)
       return cudaErrorInvalidConfiguration;
     int grid;
     if (a.cta_first) {

@@ -81,7 +81,6 @@ struct HerkArgs {
   int scratch_ctas;
   int smem_bytes;            // dynamic shared memory of the launch
   int n_tasks;               // tasks in `tasks`
-  int max_nblk;              // largest number of resident 128-row blocks of any task
   int grid;                  // CTAs of a launch with cta_first; otherwise, if > 0,
                              // the most CTAs (SMs) a single-array launch may use
 };
@@ -177,8 +176,6 @@ cudaError_t turn_rows_chans(const uint8_t* in, uint8_t* out, int layout, int bit
 // HerkTask): rows_per_chan is set for stacked arrays.  With singles, every
 // task has one column block (128 x 128).
 std::vector<HerkTask> plan_tasks(int n_inputs, int n_chans, int* rows_per_chan, bool singles = false);
-// Largest number of resident 128-row blocks of any task in the list.
-int tasks_max_nblk(const std::vector<HerkTask>& tasks);
 
 // FP64 correlation coefficients from int64 visibilities; zero_flag (may be
 // null) gets 1 per baseline whose denominator V_ii V_jj is zero, else 0.

@@ -197,7 +197,6 @@ extern "C" int corr_correlate_noalloc(const void* block, int n_inputs, int n_cha
   a.lo_is_real = (flags & CORR_F_LO_IS_REAL) ? 1 : 0;
   a.smem_bytes = smem;
   a.n_tasks = (int)n_tasks;
-  a.max_nblk = (rpc == 0 && nrb >= 2) ? 2 : 1;  // row blocks resident per task (see planner)
   a.bits = 4;
   CUtensorMap tmap;
   const bool aligned = stride % 16 == 0 && reinterpret_cast<uintptr_t>(src) % 16 == 0;

@@ -113,16 +113,6 @@ std::vector<HerkTask> plan_tasks(int n, int c, int* rows_per_chan, bool singles)
   return t;
 }
 
-int tasks_max_nblk(const std::vector<HerkTask>& tasks) {
-  int m = 1;
-  for (const HerkTask& t : tasks) {
-    const int nb = t.cb[1] >= 0 ? 2 : 1;
-    const bool a_in = t.rb == t.cb[0] || (nb == 2 && t.rb == t.cb[1]);
-    m = std::max(m, a_in ? nb : nb + 1);
-  }
-  return m;
-}
-
 }  // namespace xe
 
 struct corr_ctx {
@@ -173,7 +163,6 @@ struct corr_ctx {
   long long turned_stride = 0;  // bytes per (channel, input) row of `turned`
   HerkTask* tasks = nullptr;
   int n_tasks = 0;
-  int max_nblk = 1;
   int2* scratch = nullptr;  // 8-bit: per-CTA partial sums of the cross-multiply
   int scratch_ctas = 0;
   int rows_per_chan = 0;
@@ -447,7 +436,6 @@ int corr_create(int n_inputs, int n_chans, int n_time, int bits, int layout, uns
     std::vector<HerkTask> tasks = plan_tasks(n_inputs, n_chans, &x->rows_per_chan);
     x->n_tasks = (int)tasks.size();
     if (bits == 8 && herk_scratch_alloc(&x->scratch, &x->scratch_ctas) != cudaSuccess) { st = CORR_ENOMEM; break; }
-    x->max_nblk = tasks_max_nblk(tasks);
     if (cudaMalloc(&x->tasks, tasks.size() * sizeof(HerkTask)) != cudaSuccess) { st = CORR_ENOMEM; break; }
     if (cudaMemcpy(x->tasks, tasks.data(), tasks.size() * sizeof(HerkTask), cudaMemcpyHostToDevice) != cudaSuccess) { st = CORR_ECUDA; break; }
     x->smem_bytes = herk4_max_smem();
@@ -545,7 +533,6 @@ int corr_push(corr_ctx* x, const void* block, size_t nbytes, uint64_t seq) {
   a.lo_is_real = (x->flags & CORR_F_LO_IS_REAL) ? 1 : 0;
   a.smem_bytes = x->smem_bytes;
   a.n_tasks = x->n_tasks;
-  a.max_nblk = x->max_nblk;
   a.bits = x->bits;
   a.scratch = x->scratch;
   a.scratch_ctas = x->scratch_ctas;

@@ -94,7 +94,7 @@ struct Req {
   int slot = -1;
   int64_t pushed = 0, ticked = 0;
   std::vector<HerkTask> tasks;   // inst filled per tick
-  int rpc = 0, max_nblk = 1;
+  int rpc = 0;
   CUtensorMap tmap[2];
   cudaEvent_t ev_copy[2] = {nullptr, nullptr}, ev_used[2] = {nullptr, nullptr};
   double t_submit = 0.0;
@@ -198,7 +198,6 @@ void admit(corr_svc* s) {
     q.slot = s->free_slots.back();
     s->free_slots.pop_back();
     q.tasks = plan_tasks(q.r.n_inputs, q.r.n_chans, &q.rpc);
-    q.max_nblk = tasks_max_nblk(q.tasks);
     if (!s->dry) {
       for (int b = 0; b < 2; ++b) {
         const uint8_t* x = q.has_turn ? s->base + q.off_turn : s->base + q.off_in[b];
@@ -407,16 +406,14 @@ int corr_svc_tick(corr_svc* s, int* n_requests) {
     if (!ensure(s->d_tasks[p], s->h_tasks[p], s->task_cap[p], ntask) ||
         !ensure(s->d_first[p], s->h_first[p], s->first_cap[p], cls.size() * (nsm + 1)))
       return CORR_ENOMEM;
-    struct Launch { size_t t0, f0; int nt, nc, max_nblk, bits, lo; bool tci; };
+    struct Launch { size_t t0, f0; int nt, nc, bits, lo; bool tci; };
     std::vector<Launch> ls;
     size_t tpos = 0, fpos = 0;
     for (auto& c : cls) {
       std::vector<HerkTask> all;
       std::vector<double> cost;
-      int mx = 1;
       for (Req* q : c.qs) {
         const int inst = q->slot * 2 + (int)(q->ticked & 1);
-        mx = std::max(mx, q->max_nblk);
         for (HerkTask t : q->tasks) {
           t.inst = inst;
           const int nb = t.cb[1] >= 0 ? 2 : 1;
@@ -430,7 +427,7 @@ int corr_svc_tick(corr_svc* s, int* n_requests) {
       std::vector<int> order(nt);
       corr_plan_schedule(cost.data(), nt, nc, order.data(), s->h_first[p] + fpos);
       for (int j = 0; j < nt; ++j) s->h_tasks[p][tpos + j] = all[order[j]];
-      ls.push_back({tpos, fpos, nt, nc, mx, c.bits, c.lo, c.tci});
+      ls.push_back({tpos, fpos, nt, nc, c.bits, c.lo, c.tci});
       tpos += nt;
       fpos += nc + 1;
     }
@@ -454,7 +451,6 @@ int corr_svc_tick(corr_svc* s, int* n_requests) {
       a.lo_is_real = l.lo;
       a.bits = l.bits;
       a.n_tasks = l.nt;
-      a.max_nblk = l.max_nblk;
       a.grid = l.nc;
       a.scratch = s->scratch;
       a.scratch_ctas = s->scratch_ctas;

@@ -31,7 +31,9 @@ def xe():
     return xengine
 
 
-@pytest.mark.parametrize("N,C,T,stage", [(192, 4, 1024, 2), (64, 8, 2048, 0), (32, 16, 512, 3)])
+# stages count per CTA over its tasks: 128 spectra a stage for a two-block
+# task, 256 for a one-block (A = B) task; the withheld stage must exist
+@pytest.mark.parametrize("N,C,T,stage", [(192, 4, 1024, 2), (64, 8, 2048, 0), (32, 16, 1024, 3)])
 def test_withheld_stage_times_out_and_context_recovers(xe, N, C, T, stage):
     blocks = [synth.random_bytes(900 + k, N * C * T) for k in range(2)]
     with xe.Correlator(N, C, T, bits=4, layout=xe.CORR_L_CIT) as cor:
