@@ -315,8 +315,20 @@ __device__ __forceinline__ void epilogue(const HerkInst& a, const HerkTask& task
   int64_t* chp = a.acc + (long long)(row_ok ? ch : 0) * nbl * 2;
   const int tri_i = i * (i + 1) / 2;  // baselines per channel stay below 2^30 (inputs <= 32768)
   const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16);
-  const int nch = g.nb * 8, per = nch / nparts;  // 16-column chunks
-  for (int cc = part * per; cc < (part + 1) * per; ++cc) {
+  // 16-column chunks of this warp's share.  In a stacked tile a lane's row
+  // only meets columns of its own channel: the rows 32 quad .. + 31 of this
+  // warp belong to one channel (rows_per_chan >= 32), whose columns are
+  // rows_per_chan / 16 chunks, or to channels whose columns are the two
+  // chunks 2 quad, 2 quad + 1; the other chunks hold no visibility.
+  int c0 = 0, c1 = g.nb * 8;
+  if (stacked) {
+    const int rpc = a.rows_per_chan;
+    c0 = rpc >= 32 ? (quad * 32 / rpc) * (rpc / 16) : 2 * quad;
+    c1 = c0 + (rpc >= 32 ? rpc / 16 : 2);
+  }
+  const int per = (c1 - c0 + nparts - 1) / nparts;
+  const int cbeg = c0 + part * per, cend = min(c1, cbeg + per);
+  for (int cc = cbeg; cc < cend; ++cc) {
     int2 prev[4];
     int2* sp = scr + (cc * 4) * 128 + p;
     if (F16 && !first) {
