@@ -1143,6 +1143,18 @@ cudaError_t ring_launch(const HerkArgs& a, const CUtensorMap* tmap, int grid, cu
 
 }  // namespace
 
+int device_sm_count() {
+  static int count[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+  if (count[dev] <= 0) {
+    int nsm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    count[dev] = nsm > 0 ? nsm : 1;
+  }
+  return count[dev];
+}
+
 int herk_ring_stage(int bits) { return bits == 8 ? stage_t<true>() : stage_t<false>(); }
 
 int herk4_max_smem() {
@@ -1164,10 +1176,7 @@ cudaError_t herk4_launch(const HerkArgs& args, const CUtensorMap* tmap, int n_ta
     if (a.cta_first) {
       grid = a.grid;
     } else {
-      int dev = 0, nsm = 0;
-      cudaGetDevice(&dev);
-      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-      grid = std::min(n_tasks, nsm);
+      grid = std::min(n_tasks, device_sm_count());
       if (a.grid > 0) grid = std::min(grid, a.grid);
     }
     if (grid < 1) return cudaSuccess;

@@ -177,6 +177,12 @@ cudaError_t turn_rows_chans(const uint8_t* in, uint8_t* out, int layout, int bit
 // task has one column block (128 x 128).
 std::vector<HerkTask> plan_tasks(int n_inputs, int n_chans, int* rows_per_chan, bool singles = false);
 
+// Snapshot the device status word into host_slot (pinned host memory, written
+// by the device through its mapping; read it once the stream has passed this
+// point) and clear it.
+cudaError_t take_status_launch(int* status, int* host_slot, cudaStream_t s);
+// SM count of the current device (queried once per device).
+int device_sm_count();
 // FP64 correlation coefficients from int64 visibilities; zero_flag (may be
 // null) gets 1 per baseline whose denominator V_ii V_jj is zero, else 0.
 cudaError_t normalise_launch(const int64_t* acc, double* rho, uint8_t* zero_flag, int n_inputs,

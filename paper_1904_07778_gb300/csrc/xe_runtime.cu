@@ -148,6 +148,7 @@ struct corr_ctx {
   cudaEvent_t dump_ready = nullptr;
   std::vector<cudaEvent_t> done_pool;
   int* h_dump_status = nullptr;  // pinned, kMaxAsyncDumps status snapshots
+  int* d_dump_status = nullptr;  // the same slots as the device writes them (mapped)
   uint8_t* stage[2] = {nullptr, nullptr};
   cudaEvent_t stage_free[2] = {nullptr, nullptr};
   cudaEvent_t stage_ready[2] = {nullptr, nullptr};
@@ -168,6 +169,17 @@ struct corr_ctx {
   int n_tasks = 0;
   int2* scratch = nullptr;  // 8-bit: per-CTA partial sums of the cross-multiply
   int scratch_ctas = 0;
+  // host-side caches of the push path: two block addresses known to be device
+  // memory, and the tensor maps of the last two sources (the other parameters
+  // of a map are fixed per context)
+  const void* dev_seen[2] = {nullptr, nullptr};
+  int dev_seen_next = 0;
+  struct MapCache {
+    const uint8_t* src = nullptr;
+    bool tci = false;
+    CUtensorMap map;
+  } map_cache[2];
+  int map_next = 0;
   int rows_per_chan = 0;
   int smem_bytes = 0;
   int* d_status = nullptr;
@@ -477,7 +489,13 @@ int corr_push(corr_ctx* x, const void* block, size_t nbytes, uint64_t seq) {
                cudaStreamWaitEvent(ts, x->herk_done[pk], 0) != cudaSuccess))
     return CORR_ECUDA;
   int slot = -1;
-  if (!is_device_ptr(block)) {
+  bool on_device = block == x->dev_seen[0] || block == x->dev_seen[1];
+  if (!on_device && is_device_ptr(block)) {
+    on_device = true;
+    x->dev_seen[x->dev_seen_next] = block;
+    x->dev_seen_next ^= 1;
+  }
+  if (!on_device) {
     slot = x->stage_next;
     x->stage_next ^= 1;
     if (!x->stage[slot] && cudaMalloc(&x->stage[slot], x->block_bytes) != cudaSuccess)
@@ -540,26 +558,34 @@ int corr_push(corr_ctx* x, const void* block, size_t nbytes, uint64_t seq) {
   a.scratch = x->scratch;
   a.scratch_ctas = x->scratch_ctas;
   // The TMA kernel needs 16-byte aligned rows; otherwise plain loads.
-  CUtensorMap tmap;
   const bool aligned = row_stride % 16 == 0 && reinterpret_cast<uintptr_t>(src) % 16 == 0;
-  const bool use_tma = (tci || aligned) && make_herk_tmap(&tmap, src, tci, x->bits, R, C, T,
-                                                          row_stride, x->rows_per_chan);
+  const CUtensorMap* tmap = nullptr;
+  if (tci || aligned) {
+    for (const corr_ctx::MapCache& c : x->map_cache)
+      if (c.src == src && c.tci == tci) tmap = &c.map;
+    if (!tmap) {
+      corr_ctx::MapCache& c = x->map_cache[x->map_next];
+      c.src = nullptr;
+      if (make_herk_tmap(&c.map, src, tci, x->bits, R, C, T, row_stride, x->rows_per_chan)) {
+        c.src = src;
+        c.tci = tci;
+        tmap = &c.map;
+        x->map_next ^= 1;
+      }
+    }
+  }
+  const bool use_tma = tmap != nullptr;
   if ((eight || tci) && !use_tma) return CORR_ECUDA;  // these are always TMA-aligned
   const int chunk = eight ? kMaxChunk8 : kMaxChunk4;
   if (int g = guard_acc_write(x, hs)) return g;
-  if (pipe) {
-    int dev = 0, nsm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    a.grid = nsm - x->pipe_sms;  // the SMs the next block's turn leaves free
-  }
+  if (pipe) a.grid = device_sm_count() - x->pipe_sms;  // the SMs the next block's turn leaves free
   for (int t0 = 0; t0 < T; t0 += chunk) {
     a.in.t0 = t0;
     a.in.tn = std::min(chunk, T - t0);
     a.in.accumulate = x->acc_live ? 1 : 0;
     a.in.vec_ok = aligned ? 1 : 0;
     cudaEvent_t th = phase_begin(x, hs);
-    cudaError_t e = herk4_launch(a, use_tma ? &tmap : nullptr, x->n_tasks, hs, tci);
+    cudaError_t e = herk4_launch(a, tmap, x->n_tasks, hs, tci);
     if (e != cudaSuccess) return cuda_fail(e);
     phase_end(x, kHerk, th, hs);
     ++x->stats.herk_launches;
@@ -640,10 +666,17 @@ int corr_dump_async(corr_ctx* x, int64_t* vis, int reset) {
       x->acc_free[i] = nullptr;
       return CORR_ECUDA;
     }
-  if (!x->h_dump_status &&
-      cudaMallocHost(&x->h_dump_status, CORR_MAX_ASYNC_DUMPS * sizeof(int)) != cudaSuccess) {
-    x->h_dump_status = nullptr;
-    return CORR_ENOMEM;
+  if (!x->h_dump_status) {
+    if (cudaHostAlloc(&x->h_dump_status, CORR_MAX_ASYNC_DUMPS * sizeof(int), cudaHostAllocMapped) !=
+        cudaSuccess) {
+      x->h_dump_status = nullptr;
+      return CORR_ENOMEM;
+    }
+    if (cudaHostGetDevicePointer(&x->d_dump_status, x->h_dump_status, 0) != cudaSuccess) {
+      cudaFreeHost(x->h_dump_status);
+      x->h_dump_status = nullptr;
+      return CORR_ECUDA;
+    }
   }
   if (reset && !x->acc_buf[1] && cudaMalloc(&x->acc_buf[1], x->acc_bytes) != cudaSuccess)
     return CORR_ENOMEM;
@@ -671,9 +704,7 @@ int corr_dump_async(corr_ctx* x, int64_t* vis, int reset) {
     return CORR_ECUDA;
   }
   int st = CORR_OK;
-  if (cudaMemcpyAsync(x->h_dump_status + slot, x->d_status, sizeof(int), cudaMemcpyDeviceToHost,
-                      as) != cudaSuccess ||
-      cudaMemsetAsync(x->d_status, 0, sizeof(int), as) != cudaSuccess ||
+  if (take_status_launch(x->d_status, x->d_dump_status + slot, as) != cudaSuccess ||
       cudaEventRecord(ready, as) != cudaSuccess ||
       cudaStreamWaitEvent(x->dump_stream, ready, 0) != cudaSuccess)
     st = CORR_ECUDA;

@@ -461,6 +461,18 @@ cudaError_t turn_rows_chans(const uint8_t* in, uint8_t* out, int layout, int bit
   return cudaErrorInvalidValue;
 }
 
+// One thread: copy the status word into a slot of pinned host memory
+// (written through its device mapping) and clear it, in stream order.
+__global__ void take_status_kernel(int* status, int* host_slot) {
+  *host_slot = *status;
+  *status = 0;
+}
+
+cudaError_t take_status_launch(int* status, int* host_slot, cudaStream_t s) {
+  take_status_kernel<<<1, 1, 0, s>>>(status, host_slot);
+  return cudaGetLastError();
+}
+
 cudaError_t normalise_launch(const int64_t* acc, double* rho, uint8_t* zero_flag, int n_inputs,
                              int n_chans, cudaStream_t s) {
   const long long nbl = (long long)n_inputs * (n_inputs + 1) / 2;
