@@ -64,14 +64,12 @@ bool tci_direct(int layout, int bits, int n_inputs) {
   // The channel stride (R bytes) must suit TMA.  Stacked arrays fill a box
   // exactly (R byte rows = one channel's rows of the 128-row block: 16 or 32
   // at 4 bits, 16, 32 or 64 at 8 bits); larger ones take whole boxes of 64
-  // (4-bit) or 128 (8-bit) byte rows.  At 4 bits, above 384 byte rows every
-  // block is read by many tasks, whose short time-major boxes then cost more
-  // than turning the block once (measured on 4-bit nibble-split operands:
-  // 53 against 40 ms a block at 1024 byte rows, 2048 channels).  The 8-bit
-  // boxes carry 128-byte rows, and reading them directly beats the turn at
-  // every size (512 inputs, 2048 channels, 4096 spectra: 17.3 against
-  // 18.9 ms a block).
-  if (layout != CORR_L_TCI || R % 16 != 0 || R > (bits == 8 ? 2048 : 384)) return false;
+  // (4-bit) or 128 (8-bit) byte rows.  Reading the block directly beats
+  // turning it first at every size measured (512 inputs, 1024 channels,
+  // 4096 spectra, 4-bit: 3.15 against 3.46 ms a block; 8-bit, 2048 channels:
+  // 17.3 against 18.9 ms), although many tasks then read each block's short
+  // time-major boxes.
+  if (layout != CORR_L_TCI || R % 16 != 0) return false;
   const int box = bits == 8 ? 128 : 64;  // byte rows of a 128-row block
   return R >= box || R == 16 || R == 32 || (bits == 8 && R == 64);
 }

@@ -16,15 +16,15 @@ def _bytes(n, c, bits, layout, t):
     """Device state of one request: int64 accumulator, two ingest buffers, the
     corner-turn buffer (rows padded to 32 bytes), each rounded to 256 bytes.
     No turn buffer for [c][i][t] 4-bit blocks, nor for [t][c][i] blocks read in
-    payload order (byte rows per channel 16, 32 or a multiple of 16 from 64 to 384 at 4 bits;
-    16, 32, 64 or a multiple of 16 from 128 to 2048 at 8 bits)."""
+    payload order (byte rows per channel 16, 32 or a multiple of 16 from 64 at 4 bits; 16, 32, 64
+    or a multiple of 16 from 128 at 8 bits)."""
     r = lambda x: (x + 255) // 256 * 256
     rows = n * bits // 4
     acc = n * (n + 1) // 2 * c * 16
     blk = rows * c * t
     box = 128 if bits == 8 else 64                                     # byte rows of a 128-row block
     stacked = (16, 32, 64) if bits == 8 else (16, 32)
-    direct = layout == 0 and rows % 16 == 0 and (rows in stacked or box <= rows <= (2048 if bits == 8 else 384))
+    direct = layout == 0 and rows % 16 == 0 and (rows in stacked or rows >= box)
     turn = 0 if (layout == 2 and bits == 4) or direct else rows * c * ((t + 31) // 32 * 32)
     return r(acc) + 2 * r(blk) + r(turn)
 
