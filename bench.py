@@ -441,28 +441,45 @@ def run_gpu(args, w, world, rank, local):
               for _ in range(min(nalt, 2))]
         for h, b in zip(hb, blocks):
             h.copy_(b)
-        hv = [torch.empty((C, nb, 2), dtype=torch.int64, pin_memory=True) for _ in range(2)]
+        depth = max(1, min(args.e2e_depth, 3))   # at most 4 dumps outstanding
+        hv = [torch.empty((C, nb, 2), dtype=torch.int64, pin_memory=True) for _ in range(depth + 1)]
 
-        # one step of lookahead: step k queues its pushes and an overlapped
-        # dump, then waits for step k-1's visibilities to reach the host
+        # `depth` steps of lookahead: step k queues its pushes and an
+        # overlapped dump, then waits for step k-depth's visibilities to reach
+        # the host, so a host hiccup shorter than depth steps leaves the
+        # copy engine busy
         def step_host(k):
             for p in range(per_dump):
                 cor.push(hb[(k * per_dump + p) % len(hb)])
-            cor.dump_async(hv[k % 2], reset=True)
-            if k > 0:
+            cor.dump_async(hv[k % (depth + 1)], reset=True)
+            if k >= depth:
                 cor.dump_wait()
 
-        for k in range(max(2, args.warmup // 4)):
+        def drain_host(n_steps):
+            for _ in range(min(n_steps, depth)):
+                cor.dump_wait()
+
+        nw = max(depth + 1, args.warmup // 4)
+        for k in range(nw):
             step_host(k)
-        cor.dump_wait()
+        drain_host(nw)
         ke = max(3, min(args.steps, args.e2e_steps))
+        cor.set_timing(True)
+        se0 = cor.stats()
         barrier(world)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
+        t_k = [t0]
         for k in range(ke):
             step_host(k)
-        cor.dump_wait()
+            t_k.append(time.perf_counter())
+        drain_host(ke)
         e2e_wall = time.perf_counter() - t0
+        se1 = cor.stats()
+        cor.set_timing(False)
+        # host time of each step (queue its pushes, wait for the previous
+        # step's visibilities): shows whether a slow run is slow throughout
+        e_iv = sorted(1e3 * (b_ - a_) for a_, b_ in zip(t_k, t_k[1:]))
         # the host link alone: one pinned block in and one result out, timed
         # with events (plain copies, for the e2e floor)
         l_in, l_out = [], []
@@ -484,7 +501,9 @@ def run_gpu(args, w, world, rank, local):
         e2e = {"value": world * ops_per_step(w) / (e2e_ms * 1e-3) / 1e12, "unit": "Tops/s",
                "h2d_bytes_per_step": blocks[0].numel() * per_dump, "d2h_bytes_per_step": vis.numel() * 8,
                "ms_per_step": e2e_ms, "steps": ke,
-               "pipeline": "step k's dump overlaps step k+1's pushes (corr_dump_async)",
+               "step_ms": {"min": e_iv[0], "p50": e_iv[len(e_iv) // 2], "max": e_iv[-1]},
+               "copy_in_ms_per_step": (se1["copy_in_ms"] - se0["copy_in_ms"]) / ke,
+               "pipeline": "step k's dump overlaps the pushes of the next %d step(s) (corr_dump_async)" % depth,
                "link": dict(link, floor_ms_per_step=max(
                    blocks[0].numel() * per_dump / link["h2d_gbs"] / 1e6,
                    vis.numel() * 8 / link["d2h_gbs"] / 1e6))}
@@ -1434,6 +1453,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="cylinder192")
     ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--e2e-depth", type=int, default=2,
+                    help="steps the host runs ahead of the oldest outstanding dump in the e2e leg (1-3)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--pipeline-sms", type=int, default=-1,
