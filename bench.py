@@ -936,37 +936,42 @@ def run_fengine(args, w, world, rank, local):
     clocks = sampler.stop() if sampler else None
     ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world)
 
-    # end to end: pinned ADC block in, codes out, every step; step k's copy
-    # in and step k-1's copy out overlap step k's channelisation
+    # end to end: pinned ADC block in, codes out, every step, on three
+    # streams (copy in, channelise, copy out) over depth + 1 buffer slots; the
+    # host waits for step k-depth's codes, so copies in and out overlap the
+    # channelisation and a short host hiccup leaves the copy engines busy
     e2e = None
     if not args.no_e2e:
+        depth = max(1, min(args.e2e_depth, 3))
+        ns = depth + 1
         h_adc = torch.empty((N, S), dtype=torch.int8, pin_memory=True)
         h_adc.copy_(blocks[0])
-        h_out = [torch.empty(C * N * T, dtype=torch.uint8, pin_memory=True) for _ in range(2)]
-        d_out = [out, torch.empty_like(out)]
+        h_out = [torch.empty(C * N * T, dtype=torch.uint8, pin_memory=True) for _ in range(ns)]
+        d_in = blocks + [torch.empty_like(blocks[0]) for _ in range(ns - len(blocks))]
+        d_out = [out] + [torch.empty_like(out) for _ in range(ns - 1)]
         cin, cout = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
-        ev_in = [torch.cuda.Event() for _ in range(2)]
-        ev_used = [torch.cuda.Event() for _ in range(2)]
-        ev_out = [torch.cuda.Event() for _ in range(2)]
+        ev_in = [torch.cuda.Event() for _ in range(ns)]
+        ev_used = [torch.cuda.Event() for _ in range(ns)]
+        ev_out = [torch.cuda.Event() for _ in range(ns)]
 
         def step(k):
-            s_ = k % 2
+            s_ = k % ns
             cin.wait_event(ev_used[s_])
             with torch.cuda.stream(cin):
-                blocks[s_].copy_(h_adc, non_blocking=True)
+                d_in[s_].copy_(h_adc, non_blocking=True)
             ev_in[s_].record(cin)
             stream.wait_event(ev_in[s_])
             stream.wait_event(ev_out[s_])
-            f.channelise(blocks[s_], T, out=d_out[s_])
+            f.channelise(d_in[s_], T, out=d_out[s_])
             ev_used[s_].record(stream)
             cout.wait_event(ev_used[s_])
             with torch.cuda.stream(cout):
                 h_out[s_].copy_(d_out[s_], non_blocking=True)
             ev_out[s_].record(cout)
-            if k > 0:
-                ev_out[(k - 1) % 2].synchronize()
+            if k >= depth:
+                ev_out[(k - depth) % ns].synchronize()
 
-        for k in range(3):
+        for k in range(ns + 1):
             step(k)
         torch.cuda.synchronize()
         ke = max(3, min(args.steps, args.e2e_steps))
@@ -974,13 +979,41 @@ def run_fengine(args, w, world, rank, local):
         t0 = time.perf_counter()
         for k in range(ke):
             step(k)
-        ev_out[(ke - 1) % 2].synchronize()
+        ev_out[(ke - 1) % ns].synchronize()
         e2e_ms = max_over_ranks(1e3 * (time.perf_counter() - t0) / ke, world)
+        # the host link, one block each way alone and both ways at once
+        # (events on the copy streams; the floor of a step is the slower)
+        lk = {}
+        for name, ins, outs in (("h2d", True, False), ("d2h", False, True), ("both", True, True)):
+            best = None
+            for _ in range(3):
+                torch.cuda.synchronize()
+                g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                g0.record(stream)
+                cin.wait_event(g0)
+                cout.wait_event(g0)
+                if ins:
+                    with torch.cuda.stream(cin):
+                        d_in[0].copy_(h_adc, non_blocking=True)
+                if outs:
+                    with torch.cuda.stream(cout):
+                        h_out[0].copy_(d_out[0], non_blocking=True)
+                gi, go = torch.cuda.Event(), torch.cuda.Event()
+                gi.record(cin)
+                go.record(cout)
+                stream.wait_event(gi)
+                stream.wait_event(go)
+                g1.record(stream)
+                torch.cuda.synchronize()
+                t_ = g0.elapsed_time(g1)
+                best = t_ if best is None else min(best, t_)
+            lk[name + "_ms"] = best
         e2e = {"value": world * N * T * M / (e2e_ms * 1e-3) / 1e9, "unit": "Gsample/s",
                "h2d_bytes_per_step": N * S, "d2h_bytes_per_step": C * N * T, "ms_per_step": e2e_ms,
-               "steps": ke, "pipeline": "step k's ADC copy-in and step k-1's code copy-out overlap "
-               "step k's channelisation"}
-        del h_adc, h_out
+               "steps": ke, "pipeline": "copy-in, channelisation and copy-out on three streams, the "
+               "host %d step(s) ahead of the oldest copy-out" % depth,
+               "link": dict(lk, h2d_gbs=N * S / lk["h2d_ms"] / 1e6, d2h_gbs=C * N * T / lk["d2h_ms"] / 1e6)}
+        del h_adc, h_out, d_in, d_out
     f.close()
     if rank != 0:
         return 0
@@ -1373,41 +1406,50 @@ def run_fx(args, w, world, rank, local):
     if not args.no_e2e:
         h_adc = torch.empty((N, S), dtype=torch.int8, pin_memory=True)
         h_adc.copy_(blocks[0])
-        hv = [torch.empty((C, nb, 2), dtype=torch.int64, pin_memory=True) for _ in range(2)]
+        depth = max(1, min(args.e2e_depth, 3))   # at most 4 dumps outstanding
+        ns = depth + 1
+        hv = [torch.empty((C, nb, 2), dtype=torch.int64, pin_memory=True) for _ in range(ns)]
+        d_in = blocks + [torch.empty_like(blocks[0]) for _ in range(ns - len(blocks))]
         cin = torch.cuda.Stream(dev)
-        ev_in = [torch.cuda.Event() for _ in range(2)]
-        ev_used = [torch.cuda.Event() for _ in range(2)]
+        ev_in = [torch.cuda.Event() for _ in range(ns)]
+        ev_used = [torch.cuda.Event() for _ in range(ns)]
 
+        # the host runs `depth` steps ahead of the oldest outstanding dump
         def step_host(k):
-            s_ = k % 2
+            s_ = k % ns
             cin.wait_event(ev_used[s_])
             with torch.cuda.stream(cin):
-                blocks[s_].copy_(h_adc, non_blocking=True)
+                d_in[s_].copy_(h_adc, non_blocking=True)
             ev_in[s_].record(cin)
             stream.wait_event(ev_in[s_])
-            f.channelise(blocks[s_], T, out=codes)
+            f.channelise(d_in[s_], T, out=codes)
             ev_used[s_].record(stream)
             cor.push(codes)
             cor.dump_async(hv[s_], reset=True)
-            if k > 0:
+            if k >= depth:
                 cor.dump_wait()
 
-        for k in range(3):
+        def drain_host(n_steps):
+            for _ in range(min(n_steps, depth)):
+                cor.dump_wait()
+
+        for k in range(ns + 1):
             step_host(k)
-        cor.dump_wait()
+        drain_host(ns + 1)
         torch.cuda.synchronize()
         ke = max(3, min(args.steps, args.e2e_steps))
         barrier(world)
         t0 = time.perf_counter()
         for k in range(ke):
             step_host(k)
-        cor.dump_wait()
+        drain_host(ke)
         e2e_ms = max_over_ranks(1e3 * (time.perf_counter() - t0) / ke, world)
         e2e = {"value": world * ops_per_block(w) / (e2e_ms * 1e-3) / 1e12, "unit": "Tops/s",
                "h2d_bytes_per_step": N * S, "d2h_bytes_per_step": C * nb * 16,
                "ms_per_step": e2e_ms, "steps": ke,
-               "pipeline": "ADC copy-in on its own stream, overlapped dumps (corr_dump_async)"}
-        del h_adc, hv
+               "pipeline": "ADC copy-in on its own stream, overlapped dumps (corr_dump_async), the "
+               "host %d step(s) ahead of the oldest dump" % depth}
+        del h_adc, hv, d_in
     f.close()
     cor.close()
     if rank != 0:
