@@ -352,12 +352,20 @@ def run_gpu(args, w, world, rank, local):
     # default each integration is bound to its output buffer (corr_bind), so
     # the visibilities are written there directly and the dump copies nothing;
     # --dump-copy integrates in the context's accumulator and copies out.
-    def step(k):
+    # Several blocks per dump go to one corr_push_many: one persistent
+    # cross-multiply over all their tasks (per-block pushes with
+    # --per-block-push, and where the library needs a corner turn).
+    many = per_dump > 1 and not args.per_block_push
+
+    def step(k, many=many):
         out = vis if k % 2 == 0 else vis2
         if not args.dump_copy:
             cor.bind(out)   # free: its last dump (step k-2) was waited for in step k-1
-        for p in range(per_dump):
-            cor.push(blocks[(k * per_dump + p) % nalt])
+        if many:
+            cor.push_many([blocks[(k * per_dump + p) % nalt] for p in range(per_dump)])
+        else:
+            for p in range(per_dump):
+                cor.push(blocks[(k * per_dump + p) % nalt])
         cor.dump_async(out, reset=True)
         if k > 0:
             cor.dump_wait()
@@ -432,6 +440,27 @@ def run_gpu(args, w, world, rank, local):
     ms_max = max_over_ranks(ms, world)
     s1 = cor.stats()
     cor.set_timing(False)
+
+    # the same steps with one push (and one cross-multiply launch) per block,
+    # for comparison
+    per_block = None
+    if many:
+        nk = max(10, min(50, args.steps))
+        for k in range(3):
+            step(k, many=False)
+        drain()
+        torch.cuda.synchronize()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        for k in range(nk):
+            step(k, many=False)
+        drain()
+        g1.record(stream)
+        torch.cuda.synchronize()
+        pb_ms = max_over_ranks(g0.elapsed_time(g1) / nk, world)
+        per_block = {"ms_per_step": pb_ms, "steps": nk,
+                     "value": world * ops_per_step(w) / (pb_ms * 1e-3) / 1e12,
+                     "note": "one corr_push (one cross-multiply launch) per block"}
 
     # end to end through the public API with host buffers: pinned input
     # blocks copied in and the visibilities read back every step
@@ -523,7 +552,10 @@ def run_gpu(args, w, world, rank, local):
     d = {k: s1[k] - s0[k] for k in s1}
     herk_avg = d["herk_ms"] / max(1, d["timed_herk"])
     turn_avg = d["turn_ms"] / max(1, d["timed_turn"])
-    herk_ops = ops_per_block(w)  # one herk launch per block at T <= 65536
+    # blocks per cross-multiply launch: one at T <= 65536, or a dump's blocks
+    # together (corr_push_many)
+    bpl = d["blocks"] / max(1, d["herk_launches"])
+    herk_ops = ops_per_block(w) * bpl
     # fp8 dense = 2 x bf16 (the nominal ratio).  The kernel runs in launches of
     # about a millisecond, so the burst figure applies; the fraction of the
     # sustained figure is reported beside it.
@@ -539,7 +571,7 @@ def run_gpu(args, w, world, rank, local):
     herk["frac_of_sustained"] = herk["achieved"] / (2 * pk["bf16_sus"])
     # what the tensor pipe actually executes (diagonal blocks in full): reported
     # beside the algorithmic rate, never in place of it
-    exe = executed_flops_per_block(w) / (herk_avg * 1e-3) / 1e12
+    exe = executed_flops_per_block(w) * bpl / (herk_avg * 1e-3) / 1e12
     herk["executed_tflops"] = exe
     herk["executed_frac"] = exe / herk["peak"]
     herk["algorithmic_over_executed"] = ops_per_block(w) / executed_flops_per_block(w)
@@ -561,7 +593,7 @@ def run_gpu(args, w, world, rank, local):
         # cross-multiply reads the payload-order block itself, so its roofline is
         # the block's bytes (plus the int64 visibilities it writes or adds) over
         # its launch time, against the measured copy bandwidth
-        herk_bytes = N * C * T + (2 if per_dump > 1 else 1) * nb * C * 16 / per_dump
+        herk_bytes = (N * C * T + (2 if per_dump > 1 else 1) * nb * C * 16 / per_dump) * bpl
         herk.update({"bound": "hbm", "unit": "GB/s", "achieved": herk_bytes / (herk_avg * 1e-3) / 1e9,
                      "peak": pk["hbm"], "peak_note": "%s HBM copy" % pk["src"],
                      "tensor_tflops": herk["achieved"], "tensor_frac": herk["frac"],
@@ -607,6 +639,8 @@ def run_gpu(args, w, world, rank, local):
                    "l2": "inputs larger than L2 (%d distinct blocks of %.0f MB cycled)" % (
                        nalt, N * C * T / 1e6),
                    "blocks_per_dump": per_dump,
+                   "pushes": ("corr_push_many: the dump's %d blocks in one cross-multiply launch"
+                              % per_dump if many else "one corr_push per block"),
                    "dump": ("copied out of the context's accumulator" if args.dump_copy else
                             "in place: each integration bound to its device output buffer "
                             "(corr_bind), the dump copies nothing"),
@@ -620,7 +654,8 @@ def run_gpu(args, w, world, rank, local):
         "step_ms_distribution": step_dist,
         "wall_ms_per_step": 1e3 * wall / args.steps,
         "gpu_launches": (d["herk_launches"] + d["turn_launches"] + d["norm_launches"]),
-        "roofline": roof, "kernels": kernels,
+        "roofline": roof, "kernels": kernels, "blocks_per_launch": bpl,
+        "per_block_pushes": per_block,
         "phase_ms_per_step": {"turn": d["turn_ms"] / args.steps, "herk": d["herk_ms"] / args.steps,
                               "dump_copy": d["dump_ms"] / args.steps,
                               "overlapped": bool(pipe)},
@@ -1510,6 +1545,8 @@ def main():
                     help="X-engine workloads: copy each dump out of the context's accumulator "
                          "instead of integrating in place in the output buffer")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--per-block-push", action="store_true",
+                    help="one corr_push per block instead of corr_push_many per dump")
     ap.add_argument("--service-requests", type=int, default=0,
                     help="requests of the service workload (default: its configured count)")
     args = ap.parse_args()

@@ -118,6 +118,33 @@ int corr_create(int n_inputs, int n_chans, int n_time, int bits, int layout, uns
 int corr_push(corr_ctx* ctx, const void* block, size_t nbytes, uint64_t seq);
 
 /*
+ * corr_push_many -- add n_blocks blocks of T spectra each to the running
+ * integration: the accumulation of Sec. 2.2 over the spectra of several
+ * blocks, the same result as n_blocks corr_push calls in order.
+ *   blocks   : n_blocks pointers to packed blocks in the context's layout.
+ *   n_blocks : 1 <= n_blocks <= CORR_MAX_PUSH_MANY, else CORR_EINVAL.
+ *   nbytes   : bytes of ONE block, N * C * T * bits / 4, else CORR_EINVAL.
+ *   seq      : sequence number of the first block (the others follow it), or
+ *              CORR_SEQ_ANY; checked as for corr_push, and a gap returns
+ *              CORR_ESEQ with no block integrated.
+ * When every block is device memory with 16-byte aligned rows and needs no
+ * corner turn (CORR_L_CIT, or CORR_L_TCI where the cross-multiply reads the
+ * payload order itself), and the context is not pipelined, all blocks run
+ * as ONE persistent cross-multiply launch: the tasks of all blocks are spread
+ * over the SMs together, so the last, partly filled wave of tasks is paid
+ * once instead of once per block.  Every block then adds its partial sums
+ * with reductions at L2 into an accumulator that a new integration zeroes
+ * first.  Otherwise the call pushes the blocks one by one, and on an error
+ * the blocks before the failing one stay integrated.  Stream order and the
+ * lifetime of the blocks are as for corr_push.  The context keeps two small
+ * device tables of the blocks' parameters; a call with the same blocks and
+ * integration buffer as one of the last two reuses its table.
+ */
+#define CORR_MAX_PUSH_MANY 4096
+int corr_push_many(corr_ctx* ctx, const void* const* blocks, int n_blocks, size_t nbytes,
+                   uint64_t seq);
+
+/*
  * corr_set_pipeline -- overlap the corner turn of each block with the
  * cross-multiply of the block pushed before it.
  *   turn_sms : > 0 -> each push's corner turn runs as turn_sms persistent

@@ -178,6 +178,23 @@ struct corr_ctx {
     CUtensorMap map;
   } map_cache[2];
   int map_next = 0;
+  // corr_push_many: the per-block instances and tensor maps of one launch
+  // over several blocks (device tables, filled from pinned staging).  Two
+  // tables alternate, so that a call can fill one while the cross-multiply
+  // of the call before still reads the other; a table whose blocks and
+  // accumulator match the call is reused without a copy.
+  struct ManyTable {
+    HerkInst* d_insts = nullptr;
+    CUtensorMap* d_maps = nullptr;
+    HerkInst* h_insts = nullptr;
+    CUtensorMap* h_maps = nullptr;
+    int cap = 0;
+    std::vector<const void*> key;  // the blocks whose instances the table holds
+    int64_t* key_acc = nullptr;    // ... and their accumulator
+    cudaEvent_t done = nullptr;    // after the last launch that read the table
+    bool used = false;
+  } many[2];
+  int many_next = 0;
   int rows_per_chan = 0;
   int smem_bytes = 0;
   int* d_status = nullptr;
@@ -298,6 +315,13 @@ void free_ctx(corr_ctx* x) {
     cudaFree(x->stage[i]);
     if (x->stage_free[i]) cudaEventDestroy(x->stage_free[i]);
     if (x->stage_ready[i]) cudaEventDestroy(x->stage_ready[i]);
+  }
+  for (auto& t : x->many) {
+    cudaFree(t.d_insts);
+    cudaFree(t.d_maps);
+    if (t.h_insts) cudaFreeHost(t.h_insts);
+    if (t.h_maps) cudaFreeHost(t.h_maps);
+    if (t.done) cudaEventDestroy(t.done);
   }
   cudaFree(x->turned);
   cudaFree(x->tasks);
@@ -596,6 +620,136 @@ int corr_push(corr_ctx* x, const void* block, size_t nbytes, uint64_t seq) {
     x->herk_pending = true;
   } else if (slot >= 0 && cudaEventRecord(x->stage_free[slot], x->stream) != cudaSuccess) {
     return CORR_ECUDA;
+  }
+  return CORR_OK;
+}
+
+int corr_push_many(corr_ctx* x, const void* const* blocks, int n_blocks, size_t nbytes,
+                   uint64_t seq) {
+  TraceRange trace_("corr_push_many");
+  if (!x || !blocks || n_blocks < 1 || n_blocks > CORR_MAX_PUSH_MANY) return CORR_EINVAL;
+  if (nbytes != x->block_bytes) return CORR_EINVAL;
+  for (int i = 0; i < n_blocks; ++i)
+    if (!blocks[i]) return CORR_EINVAL;
+  const int N = x->n_inputs, C = x->n_chans, T = x->n_time;
+  const bool eight = x->bits == 8;
+  const int chunk = eight ? kMaxChunk8 : kMaxChunk4;
+  const int n_chunks = (T + chunk - 1) / chunk;
+  const int n_inst = n_blocks * n_chunks;
+  const bool tci = tci_direct(x->layout, x->bits, N);
+  // One launch needs blocks the cross-multiply reads in place through TMA:
+  // no corner turn, device memory, 16-byte aligned rows.
+  bool one = n_blocks > 1 && x->pipe_sms == 0 && (tci || !needs_turn(x->layout, x->bits)) &&
+             (tci || T % 16 == 0) && n_inst <= CORR_MAX_PUSH_MANY &&
+             (long long)x->n_tasks * n_inst <= 0x7fffffffLL;
+  int reuse = -1;
+  for (int k = 0; k < 2 && one; ++k) {
+    const corr_ctx::ManyTable& t = x->many[k];
+    if (t.key_acc == x->acc && (int)t.key.size() == n_blocks &&
+        std::equal(t.key.begin(), t.key.end(), blocks))
+      reuse = k;  // its blocks were checked when it was filled
+  }
+  for (int i = 0; i < n_blocks && one && reuse < 0; ++i)
+    one = reinterpret_cast<uintptr_t>(blocks[i]) % 16 == 0 && is_device_ptr(blocks[i]);
+  if (!one) {  // one push per block: same result, one launch (or more) each
+    for (int i = 0; i < n_blocks; ++i) {
+      const int st = corr_push(x, blocks[i], nbytes, seq == CORR_SEQ_ANY ? seq : seq + i);
+      if (st != CORR_OK) return st;
+    }
+    return CORR_OK;
+  }
+  if (seq != CORR_SEQ_ANY && x->seq_started && seq != x->next_seq) {
+    ++x->stats.seq_rejects;
+    return CORR_ESEQ;
+  }
+  cudaStream_t hs = x->stream;
+  if (int g = guard_acc_write(x, hs)) return g;
+  const int R = eight ? 2 * N : N;
+  const long long row_stride = T;
+  corr_ctx::ManyTable* tb = reuse >= 0 ? &x->many[reuse] : &x->many[x->many_next];
+  if (reuse < 0) {
+    x->many_next ^= 1;
+    // the launch that last read this table must be done before it changes
+    if (tb->used && cudaEventSynchronize(tb->done) != cudaSuccess) return CORR_ECUDA;
+    tb->key.clear();
+    tb->key_acc = nullptr;
+    if (tb->cap < n_inst) {
+      cudaFree(tb->d_insts);
+      cudaFree(tb->d_maps);
+      if (tb->h_insts) cudaFreeHost(tb->h_insts);
+      if (tb->h_maps) cudaFreeHost(tb->h_maps);
+      tb->d_insts = nullptr, tb->d_maps = nullptr, tb->h_insts = nullptr, tb->h_maps = nullptr;
+      tb->cap = 0;
+      if (cudaMalloc(&tb->d_insts, (size_t)n_inst * sizeof(HerkInst)) != cudaSuccess ||
+          cudaMalloc(&tb->d_maps, (size_t)n_inst * sizeof(CUtensorMap)) != cudaSuccess ||
+          cudaMallocHost(&tb->h_insts, (size_t)n_inst * sizeof(HerkInst)) != cudaSuccess ||
+          cudaMallocHost(&tb->h_maps, (size_t)n_inst * sizeof(CUtensorMap)) != cudaSuccess)
+        return CORR_ENOMEM;
+      tb->cap = n_inst;
+    }
+    if (!tb->done && cudaEventCreateWithFlags(&tb->done, cudaEventDisableTiming) != cudaSuccess) {
+      tb->done = nullptr;
+      return CORR_ECUDA;
+    }
+    for (int b = 0; b < n_blocks; ++b) {
+      const uint8_t* src = static_cast<const uint8_t*>(blocks[b]);
+      CUtensorMap map;
+      if (!make_herk_tmap(&map, src, tci, x->bits, R, C, T, row_stride, x->rows_per_chan))
+        return CORR_ECUDA;
+      for (int c = 0; c < n_chunks; ++c) {
+        HerkInst& in = tb->h_insts[b * n_chunks + c];
+        memset(&in, 0, sizeof(in));
+        in.x = src;
+        in.acc = x->acc;
+        in.chan_stride = (long long)R * row_stride;
+        in.row_stride = row_stride;
+        in.n_inputs = N;
+        in.n_chans = C;
+        in.t0 = c * chunk;
+        in.tn = std::min(chunk, T - c * chunk);
+        in.rows_per_chan = x->rows_per_chan;
+        in.accumulate = 1;  // every block adds (reductions at L2): blocks run concurrently
+        in.vec_ok = 1;
+        tb->h_maps[b * n_chunks + c] = map;
+      }
+    }
+    if (cudaMemcpyAsync(tb->d_insts, tb->h_insts, (size_t)n_inst * sizeof(HerkInst),
+                        cudaMemcpyHostToDevice, hs) != cudaSuccess ||
+        cudaMemcpyAsync(tb->d_maps, tb->h_maps, (size_t)n_inst * sizeof(CUtensorMap),
+                        cudaMemcpyHostToDevice, hs) != cudaSuccess)
+      return CORR_ECUDA;
+    tb->key.assign(blocks, blocks + n_blocks);
+    tb->key_acc = x->acc;
+  }
+  // a new integration starts from zero, since no block stores
+  if (!x->acc_live && cudaMemsetAsync(x->acc, 0, x->acc_bytes, hs) != cudaSuccess)
+    return CORR_ECUDA;
+  HerkArgs a;
+  memset(&a, 0, sizeof(a));
+  a.in = tb->h_insts[0];
+  a.insts = tb->d_insts;
+  a.tmaps = tb->d_maps;
+  a.tasks = x->tasks;
+  a.tasks_per_inst = x->n_tasks;
+  a.n_tasks = x->n_tasks * n_inst;
+  a.status = x->d_status;
+  a.lo_is_real = (x->flags & CORR_F_LO_IS_REAL) ? 1 : 0;
+  a.smem_bytes = x->smem_bytes;
+  a.bits = x->bits;
+  a.scratch = x->scratch;
+  a.scratch_ctas = x->scratch_ctas;
+  cudaEvent_t th = phase_begin(x, hs);
+  cudaError_t e = herk4_launch(a, nullptr, a.n_tasks, hs, tci);
+  if (e != cudaSuccess) return cuda_fail(e);
+  phase_end(x, kHerk, th, hs);
+  if (cudaEventRecord(tb->done, hs) != cudaSuccess) return CORR_ECUDA;
+  tb->used = true;
+  ++x->stats.herk_launches;
+  x->stats.blocks += (uint64_t)n_blocks;
+  x->acc_live = true;
+  if (seq != CORR_SEQ_ANY) {
+    x->seq_started = true;
+    x->next_seq = seq + (uint64_t)n_blocks;
   }
   return CORR_OK;
 }

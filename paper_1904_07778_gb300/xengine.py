@@ -85,6 +85,10 @@ _lib.corr_correlate_noalloc.argtypes = [_P, _I, _I, _I, _I, _U, _P, _P, _P]
 _lib.corr_correlate_noalloc.restype = _I
 CORR_NOALLOC_SCRATCH_BYTES = 16 << 20
 _lib.corr_get_stats.argtypes = [_P, ctypes.POINTER(CorrStats)]
+_lib.corr_push_many.argtypes = [_P, ctypes.POINTER(_P), _I, _SZ, _U64]
+_lib.corr_push_many.restype = _I
+EXPORTS.append("corr_push_many")
+CORR_MAX_PUSH_MANY = 4096
 for _f in ("corr_create", "corr_push", "corr_dump", "corr_normalise", "corr_sync", "corr_destroy",
            "corr_set_timing", "corr_get_stats"):
     getattr(_lib, _f).restype = _I
@@ -188,6 +192,25 @@ class Correlator:
         st = corr_push(self._ctx, p, n, seq)
         if check and st != CORR_OK:
             raise CorrError(st, "corr_push")
+        return st
+
+    def push_many(self, blocks, seq=CORR_SEQ_ANY, check=True):
+        """Integrate several blocks of one shape (corr_push_many): one
+        cross-multiply launch over all of them where they are device blocks
+        read in place."""
+        ptrs, size = [], None
+        for blk in blocks:
+            p, n = _ptr_and_size(blk)
+            if size is not None and n != size:
+                raise ValueError("every block must have the same size")
+            ptrs.append(p)
+            size = n
+        if not ptrs:
+            raise ValueError("no blocks")
+        arr = (_P * len(ptrs))(*ptrs)
+        st = _lib.corr_push_many(self._ctx, arr, len(ptrs), size, seq)
+        if check and st != CORR_OK:
+            raise CorrError(st, "corr_push_many")
         return st
 
     def dump_into(self, vis, reset=True, check=True):
