@@ -58,6 +58,11 @@ WORKLOADS = {
              "32 blocks integrated per dump into int64, 4-bit complex, [time][channel][input] "
              "order, sky+noise model (4 distinct 134 MB blocks cycled)",
         N=32, C=1024, T=4096, layout=0, kind="sky", alt_blocks=4, per_dump=32),
+    "dish_stream4": dict(
+        desc="dish array, streaming integration, small case: 32 inputs x 1024 channels, blocks of "
+             "4096 spectra, 4 blocks integrated per dump into int64, 4-bit complex, "
+             "[time][channel][input] order, sky+noise model (4 distinct 134 MB blocks)",
+        N=32, C=1024, T=4096, layout=0, kind="sky", alt_blocks=4, per_dump=4),
 }
 # Mixed arrays correlated as one batch (one persistent launch per run, from a
 # CUDA graph) against one launch per array: Gaussian samples as the 32-input
@@ -564,9 +569,10 @@ def run_gpu(args, w, world, rank, local):
             "achieved": herk_ops / (herk_avg * 1e-3) / 1e12, "peak": fp8,
             "avg_launch_ms": herk_avg, "launches": d["timed_herk"], "sms": n_sm - pipe,
             "peak_note": "fp8 dense = 2 x %s bf16 burst (%.1f TF/s)" % (pk["src"], pk["bf16"]),
-            "traffic": kernel_traffic("herk4_kernel", C, n_inputs=N, n_time=T),
+            "traffic": kernel_traffic("herk4_kernel", C * bpl, n_inputs=N, n_time=T,
+                                      multi_block=bpl > 1),
             "tensor_pipe_active_pct": kernel_metric("herk4_kernel", "tensor_pipe_active_pct",
-                                                    n_inputs=N, n_time=T)}
+                                                    n_inputs=N, n_time=T, multi_block=bpl > 1)}
     herk["frac"] = herk["achieved"] / herk["peak"]
     herk["frac_of_sustained"] = herk["achieved"] / (2 * pk["bf16_sus"])
     # what the tensor pipe actually executes (diagonal blocks in full): reported

@@ -531,16 +531,9 @@ struct RingCtrl {
   int32_t usum[2][kMaxBlocks * 128];
 };
 
-// Task j of this CTA: its explicit list, or round robin over the CTAs; in
-// a launch over several blocks, the block's share of one base task list.
+// Task j of this CTA: its explicit list, or round robin over the CTAs.
 __device__ __forceinline__ HerkTask my_task(const HerkArgs& a, int j) {
-  const int i = a.cta_first ? a.cta_first[blockIdx.x] + j : (int)blockIdx.x + j * (int)gridDim.x;
-  if (a.tasks_per_inst > 0) {
-    HerkTask t = a.tasks[i % a.tasks_per_inst];
-    t.inst = i / a.tasks_per_inst;
-    return t;
-  }
-  return a.tasks[i];
+  return a.cta_first ? a.tasks[a.cta_first[blockIdx.x] + j] : a.tasks[blockIdx.x + j * gridDim.x];
 }
 __device__ __forceinline__ int my_task_count(const HerkArgs& a) {
   if (a.cta_first) return a.cta_first[blockIdx.x + 1] - a.cta_first[blockIdx.x];

@@ -80,10 +80,7 @@ struct HerkArgs {
   int2* scratch;
   int scratch_ctas;
   int smem_bytes;            // dynamic shared memory of the launch
-  int n_tasks;               // tasks of the launch
-  // > 0: a launch over several blocks of one array (corr_push_many): task i
-  // is tasks[i % tasks_per_inst] of instance i / tasks_per_inst
-  int tasks_per_inst;
+  int n_tasks;               // tasks in `tasks`
   int grid;                  // CTAs of a launch with cta_first; otherwise, if > 0,
                              // the most CTAs (SMs) a single-array launch may use
 };

@@ -195,6 +195,12 @@ struct corr_ctx {
     bool used = false;
   } many[2];
   int many_next = 0;
+  // the task list of a launch over k blocks: the base list repeated with
+  // the instance index, task i = base[i % n_tasks] of block i / n_tasks; any
+  // prefix is the list of fewer blocks, so one array serves every call
+  HerkTask* many_tasks = nullptr;
+  int many_tasks_inst = 0;  // instances the array covers
+  std::vector<HerkTask> host_tasks;  // the base list
   int rows_per_chan = 0;
   int smem_bytes = 0;
   int* d_status = nullptr;
@@ -316,6 +322,7 @@ void free_ctx(corr_ctx* x) {
     if (x->stage_free[i]) cudaEventDestroy(x->stage_free[i]);
     if (x->stage_ready[i]) cudaEventDestroy(x->stage_ready[i]);
   }
+  cudaFree(x->many_tasks);
   for (auto& t : x->many) {
     cudaFree(t.d_insts);
     cudaFree(t.d_maps);
@@ -472,6 +479,7 @@ int corr_create(int n_inputs, int n_chans, int n_time, int bits, int layout, uns
     if (st != CORR_OK) break;
     std::vector<HerkTask> tasks = plan_tasks(n_inputs, n_chans, &x->rows_per_chan);
     x->n_tasks = (int)tasks.size();
+    x->host_tasks = tasks;
     if (bits == 8 && herk_scratch_alloc(&x->scratch, &x->scratch_ctas) != cudaSuccess) { st = CORR_ENOMEM; break; }
     if (cudaMalloc(&x->tasks, tasks.size() * sizeof(HerkTask)) != cudaSuccess) { st = CORR_ENOMEM; break; }
     if (cudaMemcpy(x->tasks, tasks.data(), tasks.size() * sizeof(HerkTask), cudaMemcpyHostToDevice) != cudaSuccess) { st = CORR_ECUDA; break; }
@@ -639,9 +647,10 @@ int corr_push_many(corr_ctx* x, const void* const* blocks, int n_blocks, size_t 
   const bool tci = tci_direct(x->layout, x->bits, N);
   // One launch needs blocks the cross-multiply reads in place through TMA:
   // no corner turn, device memory, 16-byte aligned rows.
+  // (the task list of the launch stays below 256 MB)
   bool one = n_blocks > 1 && x->pipe_sms == 0 && (tci || !needs_turn(x->layout, x->bits)) &&
              (tci || T % 16 == 0) && n_inst <= CORR_MAX_PUSH_MANY &&
-             (long long)x->n_tasks * n_inst <= 0x7fffffffLL;
+             (long long)x->n_tasks * n_inst * (long long)sizeof(HerkTask) <= (256LL << 20);
   int reuse = -1;
   for (int k = 0; k < 2 && one; ++k) {
     const corr_ctx::ManyTable& t = x->many[k];
@@ -664,6 +673,22 @@ int corr_push_many(corr_ctx* x, const void* const* blocks, int n_blocks, size_t 
   }
   cudaStream_t hs = x->stream;
   if (int g = guard_acc_write(x, hs)) return g;
+  if (x->many_tasks_inst < n_inst) {  // grow the task list (rare: a larger call)
+    if (x->many_tasks && (cudaStreamSynchronize(hs) != cudaSuccess || cudaFree(x->many_tasks) != cudaSuccess))
+      return CORR_ECUDA;
+    x->many_tasks = nullptr;
+    x->many_tasks_inst = 0;
+    std::vector<HerkTask> all((size_t)n_inst * x->n_tasks);
+    for (size_t i = 0; i < all.size(); ++i) {
+      all[i] = x->host_tasks[i % x->n_tasks];
+      all[i].inst = (int)(i / x->n_tasks);
+    }
+    if (cudaMalloc(&x->many_tasks, all.size() * sizeof(HerkTask)) != cudaSuccess) return CORR_ENOMEM;
+    if (cudaMemcpy(x->many_tasks, all.data(), all.size() * sizeof(HerkTask), cudaMemcpyHostToDevice) !=
+        cudaSuccess)
+      return CORR_ECUDA;
+    x->many_tasks_inst = n_inst;
+  }
   const int R = eight ? 2 * N : N;
   const long long row_stride = T;
   corr_ctx::ManyTable* tb = reuse >= 0 ? &x->many[reuse] : &x->many[x->many_next];
@@ -729,8 +754,7 @@ int corr_push_many(corr_ctx* x, const void* const* blocks, int n_blocks, size_t 
   a.in = tb->h_insts[0];
   a.insts = tb->d_insts;
   a.tmaps = tb->d_maps;
-  a.tasks = x->tasks;
-  a.tasks_per_inst = x->n_tasks;
+  a.tasks = x->many_tasks;
   a.n_tasks = x->n_tasks * n_inst;
   a.status = x->d_status;
   a.lo_is_real = (x->flags & CORR_F_LO_IS_REAL) ? 1 : 0;

@@ -76,8 +76,8 @@ def test_one_launch_bit_exact(xe, bits, layout, N, C, T, nblk):
 
 
 def test_many_small_blocks(xe):
-    """Forty 32-input blocks: 1280 tasks over the SMs, each task's block
-    taken from its index."""
+    """Forty 32-input blocks: one launch of 1280 tasks over the SMs (the
+    context's task list grows to forty blocks)."""
     N, C, T, nblk = 32, 64, 128, 40
     blks = _blocks(4, nblk, N, C, T, 900)
     got, launches, _ = _many(xe, blks, N, C, T, 4, 0)
