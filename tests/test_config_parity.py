@@ -63,10 +63,12 @@ def _quadratic_form(vis, w):
 
 
 def test_dish_streaming_integration_full(xe):
-    """32 inputs x 1024 channels, 32 blocks of 4096 spectra per dump, in the
-    benchmark's launch configuration (turn of block k+1 on 48 SMs beside the
-    cross-multiply of block k, integration bound to its device buffer, the
-    dump overlapped); every channel against the oracle."""
+    """32 inputs x 1024 channels, 32 blocks of 4096 spectra per dump, one push
+    per block with the corner turn pipelined (turn of block k+1 on 48 SMs
+    beside the cross-multiply of block k), integration bound to its device
+    buffer, the dump overlapped; every channel against the oracle.  (The
+    benchmark reads these blocks in place, all 32 in one corr_push_many:
+    tests/test_push_many.py checks that form at this size.)"""
     N, C, T, nblk = 32, 1024, 4096, 32
     nb = N * (N + 1) // 2
     dev = torch.device("cuda")
