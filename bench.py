@@ -401,11 +401,12 @@ def run_gpu(args, w, world, rank, local):
 
         for cand in cands:
             try_split(cand)
-        if args.pipeline_sms < 0:  # refine around the best split
-            best = min(sweep, key=sweep.get)
-            for cand in (best - 2, best + 2):
-                if best > 0 and 0 < cand < n_sm and cand not in sweep:
-                    try_split(cand)
+        if args.pipeline_sms < 0:  # refine around the best split, by 2 SMs and then by 1
+            for d_ in (2, 1):
+                best = min(sweep, key=sweep.get)
+                for cand in (best - d_, best + d_):
+                    if best > 0 and 0 < cand < n_sm and cand not in sweep:
+                        try_split(cand)
         pipe = min(sweep, key=sweep.get)
         cor.set_pipeline(pipe)
 

@@ -75,6 +75,17 @@ def test_one_launch_bit_exact(xe, bits, layout, N, C, T, nblk):
     assert np.array_equal(got, _want(blks, N, C, T, bits, layout))
 
 
+@pytest.mark.parametrize("bits,N,C,T", [(4, 16, 2, 70000), (8, 8, 2, 33000)])
+def test_blocks_longer_than_one_accumulation(xe, bits, N, C, T):
+    """Blocks longer than one exact FP32 accumulation (65536 spectra at 4
+    bits, 32768 at 8): each block is two instances with their own time
+    ranges, all in one launch."""
+    blks = _blocks(bits, 2, N, C, T, 950 + bits)
+    got, launches, blocks = _many(xe, blks, N, C, T, bits, 0)
+    assert launches == 1 and blocks == 2
+    assert np.array_equal(got, _want(blks, N, C, T, bits, 0))
+
+
 def test_many_small_blocks(xe):
     """Forty 32-input blocks: one launch of 1280 tasks over the SMs (the
     context's task list grows to forty blocks)."""
