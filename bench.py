@@ -52,7 +52,7 @@ WORKLOADS = {
         desc="dish array, plain: 32 inputs x 256 channels x 1024 spectra/block, 4-bit complex, "
              "[time][channel][input] payload order, i.i.d. Gaussian sigma 2.5 (40 distinct blocks "
              "cycled: 335 MB, larger than L2)",
-        N=32, C=256, T=1024, layout=0, kind="gauss", alt_blocks=40),
+        N=32, C=256, T=1024, layout=0, kind="gauss", alt_blocks=40, batch_instances=40),
     "dish_stream": dict(
         desc="dish array, streaming integration: 32 inputs x 1024 channels, blocks of 4096 spectra, "
              "32 blocks integrated per dump into int64, 4-bit complex, [time][channel][input] "
@@ -543,6 +543,40 @@ def run_gpu(args, w, world, rank, local):
                    blocks[0].numel() * per_dump / link["h2d_gbs"] / 1e6,
                    vis.numel() * 8 / link["d2h_gbs"] / 1e6))}
 
+    # A block this small is bound by launch latency; the same blocks as
+    # independent arrays of one batch (one persistent cross-multiply launch
+    # per run, replayed from a CUDA graph) measure the kernel's throughput.
+    inst = None
+    if w.get("batch_instances"):
+        from paper_1904_07778_gb300.xengine import Batch
+        ni = w["batch_instances"]
+        with torch.cuda.stream(stream):
+            bt = Batch([(N, C, T, 4, w["layout"])] * ni, stream=stream.cuda_stream)
+            for k in range(ni):
+                bt.set_input(k, blocks[k % nalt])
+            for _ in range(3):
+                bt.run()
+            bt.sync()
+            nk = max(20, min(200, args.steps))
+            h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            h0.record(stream)
+            for _ in range(nk):
+                bt.run()
+            h1.record(stream)
+            bt.sync()
+        b_ms = max_over_ranks(h0.elapsed_time(h1) / nk, world)
+        b_bytes = ni * (N * C * T + nb * C * 16)
+        inst = {"instances": ni, "runs": nk, "ms_per_run": b_ms,
+                "value": world * ni * ops_per_block(w) / (b_ms * 1e-3) / 1e12, "unit": "Tops/s",
+                "hbm_gbs": b_bytes / (b_ms * 1e-3) / 1e9,
+                "hbm_frac": b_bytes / (b_ms * 1e-3) / 1e9 / peaks()["hbm"],
+                "bytes_per_run": b_bytes,
+                "launches_per_run": bt.info()["launches_per_run"],
+                "note": "%d independent arrays of this shape, distinct blocks (%.0f MB, larger than "
+                        "L2), one persistent cross-multiply launch per run (corr_batch, CUDA graph); "
+                        "bytes = blocks in + int64 visibilities out" % (ni, ni * N * C * T / 1e6)}
+        bt.close()
+
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         blk, nch, ts, cores = cpu_oracle_run(w, args.cpu_seconds)
@@ -662,7 +696,7 @@ def run_gpu(args, w, world, rank, local):
         "wall_ms_per_step": 1e3 * wall / args.steps,
         "gpu_launches": (d["herk_launches"] + d["turn_launches"] + d["norm_launches"]),
         "roofline": roof, "kernels": kernels, "blocks_per_launch": bpl,
-        "per_block_pushes": per_block,
+        "per_block_pushes": per_block, "batch_of_instances": inst,
         "phase_ms_per_step": {"turn": d["turn_ms"] / args.steps, "herk": d["herk_ms"] / args.steps,
                               "dump_copy": d["dump_ms"] / args.steps,
                               "overlapped": bool(pipe)},

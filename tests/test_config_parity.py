@@ -87,6 +87,24 @@ def test_dish_streaming_integration_full(xe):
     assert np.array_equal(out.cpu().numpy(), want)
 
 
+def test_dish_plain_as_batch_of_instances(xe):
+    """The plain dish block (32 x 256 x 1024) as twelve independent arrays of
+    one batch, the form in which the benchmark measures its throughput (one
+    persistent launch per run): every instance in full."""
+    N, C, T, n = 32, 256, 1024, 12
+    dev = torch.device("cuda")
+    blocks = [synth.block_device("gauss", 60 + k, N, C, T, 0, dev) for k in range(n)]
+    with xe.Batch([(N, C, T, 4, 0)] * n) as b:
+        for k, blk in enumerate(blocks):
+            b.set_input(k, blk)
+        b.run()
+        b.run()                                          # outputs are overwritten, not added
+        assert b.sync() == xe.CORR_OK
+        outs = [b.output(k) for k in range(n)]
+    for k in range(n):
+        assert np.array_equal(outs[k], oracle.correlate(blocks[k].cpu().numpy(), N, C, T, layout=0)), k
+
+
 def test_batched_mixed_arrays_full_size(xe):
     """The three arrays of the batched workload in one batch run (one
     persistent cross-multiply over all their tasks), Gaussian samples in the
