@@ -296,10 +296,13 @@ __device__ __forceinline__ void epilogue(const HerkInst& a, const HerkTask& task
   const int n = a.n_inputs;
   int ch, i, plane;
   bool row_ok;
+  // A stacked tile has a power of two (2 .. 64) of rows per channel, so its
+  // channel and row splits are masks and shifts (the drain warps share their
+  // SMSPs with the busy unpack warps: every instruction of theirs counts).
   if (stacked) {
     const int rpc = a.rows_per_chan;
-    ch = task.chan0 + p / rpc;
-    const int rr = p % rpc;
+    ch = task.chan0 + (p >> (31 - __clz(rpc)));
+    const int rr = p & (rpc - 1);
     i = rr >> 1;
     plane = rr & 1;
     row_ok = i < n && ch < a.n_chans;
@@ -359,9 +362,11 @@ __device__ __forceinline__ void epilogue(const HerkInst& a, const HerkTask& task
       int b;
       bool ok;
       if (stacked) {
+        // column q and row p of the tile share a channel when they agree
+        // above the rows-per-channel bits
         const int rpc = a.rows_per_chan;
-        const int j = (q % rpc) >> 1;
-        ok = row_ok && task.chan0 + q / rpc == ch && j <= i;
+        const int j = (q & (rpc - 1)) >> 1;
+        ok = row_ok && (q ^ p) < rpc && j <= i;
         b = tri_i + j;
       } else {
         const int j = (128 * cblk + q) >> 1;
