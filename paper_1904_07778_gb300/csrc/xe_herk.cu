@@ -326,8 +326,8 @@ __device__ __forceinline__ void epilogue(const HerkInst& a, const HerkTask& task
   int c0 = 0, c1 = g.nb * 8;
   if (stacked) {
     const int rpc = a.rows_per_chan;
-    c0 = rpc >= 32 ? (quad * 32 / rpc) * (rpc / 16) : 2 * quad;
-    c1 = c0 + (rpc >= 32 ? rpc / 16 : 2);
+    c0 = rpc >= 32 ? (rpc == 32 ? quad : quad >> 1) * (rpc >> 4) : 2 * quad;  // rpc <= 64
+    c1 = c0 + (rpc >= 32 ? rpc >> 4 : 2);
   }
   const int per = (c1 - c0 + nparts - 1) / nparts;
   const int cbeg = c0 + part * per, cend = min(c1, cbeg + per);
@@ -340,11 +340,23 @@ __device__ __forceinline__ void epilogue(const HerkInst& a, const HerkTask& task
     }
     uint32_t r[16];
     tmem_load16(trow + (uint32_t)(cc * 16), r);
+    int cs[16];  // 4-bit: the chunk's 16 column sums, in four 16-byte loads
+    if constexpr (!F16) {
+      const int4* u4 = reinterpret_cast<const int4*>(usum + cc * 16);
+#pragma unroll
+      for (int w = 0; w < 4; ++w) {
+        const int4 v = u4[w];
+        cs[4 * w] = v.x, cs[4 * w + 1] = v.y, cs[4 * w + 2] = v.z, cs[4 * w + 3] = v.w;
+      }
+    }
     int gv[16];
 #pragma unroll
-    for (int k = 0; k < 16; ++k)
-      gv[k] = F16 ? __float2int_rn(__uint_as_float(r[k]))
-                  : __float2int_rn(__uint_as_float(r[k]) * 262144.0f) + base_term - 8 * usum[cc * 16 + k];
+    for (int k = 0; k < 16; ++k) {
+      if constexpr (F16)
+        gv[k] = __float2int_rn(__uint_as_float(r[k]));
+      else
+        gv[k] = __float2int_rn(__uint_as_float(r[k]) * 262144.0f) + base_term - 8 * cs[k];
+    }
     const int cblk = slot_block(g, cc >> 3);
     const bool upper = !stacked && cblk > task.rb;
     int vre[4], vim[4];
@@ -416,7 +428,7 @@ struct Ctrl {
   uint64_t done;
   uint32_t tmem_base;
   int abort;
-  int32_t usum[kMaxBlocks * 128];
+  alignas(16) int32_t usum[kMaxBlocks * 128];  // read by the drain in 16-byte loads
 };
 
 __device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
@@ -533,7 +545,7 @@ struct RingCtrl {
   uint64_t done;                 // every MMA finished (before freeing tensor memory)
   uint32_t tmem_base;
   int abort;
-  int32_t usum[2][kMaxBlocks * 128];
+  alignas(16) int32_t usum[2][kMaxBlocks * 128];  // read by the drain in 16-byte loads
 };
 
 // Task j of this CTA: its explicit list, or round robin over the CTAs.
