@@ -1030,20 +1030,37 @@ def run_fengine(args, w, world, rank, local):
         ev_used = [torch.cuda.Event() for _ in range(ns)]
         ev_out = [torch.cuda.Event() for _ in range(ns)]
 
-        def step(k):
+        # per-step timing events on each stream (start and end of its work)
+        tev = []
+
+        def step(k, timed=False):
             s_ = k % ns
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)] if timed else None
             cin.wait_event(ev_used[s_])
+            if timed:
+                ev[0].record(cin)
             with torch.cuda.stream(cin):
                 d_in[s_].copy_(h_adc, non_blocking=True)
             ev_in[s_].record(cin)
+            if timed:
+                ev[1].record(cin)
             stream.wait_event(ev_in[s_])
             stream.wait_event(ev_out[s_])
+            if timed:
+                ev[2].record(stream)
             f.channelise(d_in[s_], T, out=d_out[s_])
             ev_used[s_].record(stream)
+            if timed:
+                ev[3].record(stream)
             cout.wait_event(ev_used[s_])
+            if timed:
+                ev[4].record(cout)
             with torch.cuda.stream(cout):
                 h_out[s_].copy_(d_out[s_], non_blocking=True)
             ev_out[s_].record(cout)
+            if timed:
+                ev[5].record(cout)
+                tev.append(ev)
             if k >= depth:
                 ev_out[(k - depth) % ns].synchronize()
 
@@ -1054,9 +1071,16 @@ def run_fengine(args, w, world, rank, local):
         barrier(world)
         t0 = time.perf_counter()
         for k in range(ke):
-            step(k)
+            step(k, timed=True)
         ev_out[(ke - 1) % ns].synchronize()
         e2e_ms = max_over_ranks(1e3 * (time.perf_counter() - t0) / ke, world)
+        torch.cuda.synchronize()
+        med = lambda xs: sorted(xs)[len(xs) // 2]
+        phases = {"copy_in_ms": med([e[0].elapsed_time(e[1]) for e in tev]),
+                  "channelise_ms": med([e[2].elapsed_time(e[3]) for e in tev]),
+                  "copy_out_ms": med([e[4].elapsed_time(e[5]) for e in tev]),
+                  "pinned": bool(h_adc.is_pinned() and all(h.is_pinned() for h in h_out)),
+                  "note": "medians over the timed steps, CUDA events on each stream"}
         # the host link, one block each way alone and both ways at once
         # (events on the copy streams; the floor of a step is the slower)
         lk = {}
@@ -1088,7 +1112,8 @@ def run_fengine(args, w, world, rank, local):
                "h2d_bytes_per_step": N * S, "d2h_bytes_per_step": C * N * T, "ms_per_step": e2e_ms,
                "steps": ke, "pipeline": "copy-in, channelisation and copy-out on three streams, the "
                "host %d step(s) ahead of the oldest copy-out" % depth,
-               "link": dict(lk, h2d_gbs=N * S / lk["h2d_ms"] / 1e6, d2h_gbs=C * N * T / lk["d2h_ms"] / 1e6)}
+               "link": dict(lk, h2d_gbs=N * S / lk["h2d_ms"] / 1e6, d2h_gbs=C * N * T / lk["d2h_ms"] / 1e6),
+               "phases": phases}
         del h_adc, h_out, d_in, d_out
     f.close()
     if rank != 0:
