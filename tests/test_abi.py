@@ -63,6 +63,12 @@ def test_pure_host_calls(lib_path):
     assert lib.corr_create(4, 1, 1, 4, 0, 0, None, None) == xe.CORR_EINVAL
     lib.corr_destroy.argtypes = [ctypes.c_void_p]
     assert lib.corr_destroy(None) == 0
+    # corr_push_many checks its context and block list before any device work
+    lib.corr_push_many.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t,
+                                   ctypes.c_uint64]
+    blocks = (ctypes.c_void_p * 2)(None, None)
+    assert lib.corr_push_many(None, blocks, 2, 64, xe.CORR_SEQ_ANY) == xe.CORR_EINVAL
+    assert lib.corr_push_many(None, None, 2, 64, xe.CORR_SEQ_ANY) == xe.CORR_EINVAL
 
 
 def test_binding_has_no_cpu_fallback():
