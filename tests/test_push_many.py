@@ -64,6 +64,8 @@ ONE_LAUNCH = [
     (4, 0, 32, 64, 1024, 5), (4, 0, 16, 40, 300, 3), (4, 0, 64, 16, 1000, 4),
     (4, 0, 192, 4, 256, 3), (4, 2, 48, 8, 512, 3), (4, 2, 192, 6, 272, 2),
     (8, 0, 32, 16, 2100, 3), (8, 0, 8, 20, 640, 4), (8, 0, 192, 2, 1100, 2), (8, 0, 64, 6, 1500, 2),
+    # large arrays: paired and single column-block tasks of many row blocks in one launch
+    (4, 0, 384, 3, 512, 2), (8, 0, 512, 2, 300, 2),
 ]
 
 
