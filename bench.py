@@ -623,7 +623,7 @@ def run_gpu(args, w, world, rank, local):
                 "unit": "GB/s", "sms": pipe or n_sm,
                 "achieved": tb / (turn_avg * 1e-3) / 1e9, "peak": pk["hbm"], "avg_launch_ms": turn_avg,
                 "launches": d["timed_turn"], "peak_note": "%s HBM copy" % pk["src"],
-                "traffic": None if pipe else kernel_traffic("turn_kernel", N * C * T)}
+                "traffic": kernel_traffic("turn_persist_kernel" if pipe else "turn_kernel", N * C * T)}
         turn["frac"] = turn["achieved"] / turn["peak"]
         kernels.append(turn)
     # a tensor-bound kernel confined to part of the GPU, also against that
