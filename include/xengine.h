@@ -330,19 +330,24 @@ int corr_get_stats(corr_ctx* ctx, corr_stats* out);
  * library, for the life of the process.  The call itself allocates nothing
  * and frees nothing, on host or device.
  *   block   : device pointer on the current device, N * C * T * bits / 4
- *             bytes in `layout` (4-bit).
+ *             bytes in `layout` (4-bit; corr_correlate_noalloc_bits below
+ *             takes 8-bit blocks too).
  *   vis     : device pointer on the current device, int64 [C][N(N+1)/2][2];
  *             overwritten with this block's visibilities (not added to).
  *   status  : optional device int on the current device; receives the device
  *             status bits of this call (0 ok, 1 a bounded device-side wait ran
- *             out).  The call returns before the GPU has run the work, so a
+ *             out, 2 an 8-bit sample equal to -128 was integrated).  The call returns before the GPU has run the work, so a
  *             device-side failure is reported only here: a caller that passes
  *             NULL does not learn of it.
  *   stream  : cudaStream_t to run on (NULL: the legacy default stream).
- * Limits: 256 + 20 * tasks (rounded up to 256) + (layout != CORR_L_CIT ?
- * N * C * ceil32(T) : 0) bytes must fit the scratch, where tasks is C / (128 /
- * 2^ceil(log2 2N)) rounded up for 2N <= 64, else C times the tasks of one
- * channel; larger requests return CORR_EINVAL.  Host pointers, and device
+ * Limits: 256 + 20 * tasks (rounded up to 256) + (8-bit: 65536 * SMs) +
+ * (turned ? R * C * ceil32(T) : 0) bytes must fit the scratch, where tasks is
+ * C / (128 / 2^ceil(log2 2N)) rounded up for 2N <= 64, else C times the tasks
+ * of one channel, R = N (4-bit) or 2N (8-bit) byte rows, and a block is
+ * turned unless it is 4-bit CORR_L_CIT or a payload-order (CORR_L_TCI) block
+ * whose rows the cross-multiply reads in place (R a multiple of 16 and at
+ * least 64 (4-bit) or 128 (8-bit) byte rows, or R = 16 or 32, or R = 64 at
+ * 8 bits; 16-byte aligned); larger requests return CORR_EINVAL.  Host pointers, and device
  * pointers of another GPU, return CORR_EINVAL.  CORR_ECUDA if the device
  * lacks the shared memory the cross-multiply needs.  Asynchronous: returns
  * once the work is queued.
@@ -357,6 +362,18 @@ int corr_get_stats(corr_ctx* ctx, corr_stats* out);
 #define CORR_NOALLOC_SCRATCH_BYTES (16u << 20)
 int corr_correlate_noalloc(const void* block, int n_inputs, int n_chans, int n_time, int layout,
                            unsigned flags, int64_t* vis, int* status, void* stream);
+
+/*
+ * corr_correlate_noalloc_bits -- corr_correlate_noalloc with the sample width
+ * of corr_create: bits = 4 (the call above) or 8 (two int8 bytes, re and im,
+ * per complex sample, symmetric range -127..127; a -128 is integrated exactly
+ * and reported as status bit 2; CORR_F_LO_IS_REAL is invalid with 8 bits).
+ * The 8-bit cross-multiply keeps per-SM partial sums in the scratch (64 KB a
+ * streaming multiprocessor), which leaves less room for a turned block.
+ * Everything else is as for corr_correlate_noalloc.
+ */
+int corr_correlate_noalloc_bits(const void* block, int n_inputs, int n_chans, int n_time, int bits,
+                                int layout, unsigned flags, int64_t* vis, int* status, void* stream);
 
 /*
  * Batches: several arrays correlated in one persistent launch.

@@ -128,16 +128,19 @@ bool is_device(const void* p) {
 
 using namespace xe;
 
-extern "C" int corr_correlate_noalloc(const void* block, int n_inputs, int n_chans, int n_time,
-                                      int layout, unsigned flags, int64_t* vis, int* status,
-                                      void* stream) {
+extern "C" int corr_correlate_noalloc_bits(const void* block, int n_inputs, int n_chans,
+                                           int n_time, int bits, int layout, unsigned flags,
+                                           int64_t* vis, int* status, void* stream) {
   TraceRange trace_("corr_correlate_noalloc");
   if (!block || !vis || n_inputs < 1 || n_inputs > 1024 || n_chans < 1 || n_time < 1 ||
-      layout < CORR_L_TCI || layout > CORR_L_CIT || (flags & ~CORR_F_LO_IS_REAL))
+      (bits != 4 && bits != 8) || layout < CORR_L_TCI || layout > CORR_L_CIT ||
+      (flags & ~CORR_F_LO_IS_REAL) || (bits == 8 && (flags & CORR_F_LO_IS_REAL)))
     return CORR_EINVAL;
   if (!is_device(block) || !is_device(vis) || (status && !is_device(status))) return CORR_EINVAL;
   const int N = n_inputs, C = n_chans, T = n_time;
-  // scratch layout: [status (256 B)] [tasks] [corner-turned block]
+  const bool eight = bits == 8;
+  const int R = eight ? 2 * N : N;  // byte rows per channel
+  // scratch layout: [status (256 B)] [tasks] [8-bit partial sums] [corner-turned block]
   int rpc = 0, pairs = 0, singles = 0, nrb = 0;
   long long n_tasks;
   if (2 * N <= 64) {
@@ -154,10 +157,16 @@ extern "C" int corr_correlate_noalloc(const void* block, int n_inputs, int n_cha
     n_tasks = (long long)(pairs + singles) * C;
   }
   const long long task_bytes = (n_tasks * (long long)sizeof(HerkTask) + 255) / 256 * 256;
+  // payload-order blocks whose rows suit TMA are read in place; other
+  // layouts (and 8-bit [c][i][t], whose byte pairs split into rows) are turned
+  const bool tci = tci_direct(layout, bits, N) && reinterpret_cast<uintptr_t>(block) % 16 == 0;
+  const bool turn = !tci && needs_turn(layout, bits);
   // turned rows padded to 32 bytes: the corner turn's fast path, as in corr_create
-  const long long row_stride = ((long long)T + 31) / 32 * 32;
-  const long long turned_bytes = layout == CORR_L_CIT ? 0 : row_stride * N * C;
-  if (256 + task_bytes + turned_bytes > (long long)kNoAllocScratchBytes) return CORR_EINVAL;
+  const long long row_stride = turn ? ((long long)T + 31) / 32 * 32 : T;
+  const long long turned_bytes = turn ? row_stride * R * C : 0;
+  const int n_sm = device_sm_count();
+  const long long scr_bytes = eight ? (long long)n_sm * kHerkScratchInt2 * (long long)sizeof(int2) : 0;
+  if (256 + task_bytes + scr_bytes + turned_bytes > (long long)kNoAllocScratchBytes) return CORR_EINVAL;
   // the cross-multiply needs four ring slots of its largest stage (as corr_create checks)
   const int smem = herk4_max_smem();
   if (smem < 4 * 2 * (16384 + 8192) + 1024) return CORR_ECUDA;
@@ -165,9 +174,11 @@ extern "C" int corr_correlate_noalloc(const void* block, int n_inputs, int n_cha
   int st = scratch_address(&base);
   if (st != CORR_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
-  int* d_status = static_cast<int*>(base);
-  HerkTask* tasks = reinterpret_cast<HerkTask*>(static_cast<uint8_t*>(base) + 256);
-  uint8_t* turned = static_cast<uint8_t*>(base) + 256 + task_bytes;
+  uint8_t* b8 = static_cast<uint8_t*>(base);
+  int* d_status = reinterpret_cast<int*>(b8);
+  HerkTask* tasks = reinterpret_cast<HerkTask*>(b8 + 256);
+  int2* scr = reinterpret_cast<int2*>(b8 + 256 + task_bytes);
+  uint8_t* turned = b8 + 256 + task_bytes + scr_bytes;
 
   // the scratch keeps the previous call's contents: clear the status word
   if (cudaMemsetAsync(d_status, 0, sizeof(int), s) != cudaSuccess) return CORR_ECUDA;
@@ -176,37 +187,38 @@ extern "C" int corr_correlate_noalloc(const void* block, int n_inputs, int n_cha
   if (cudaGetLastError() != cudaSuccess) return CORR_ECUDA;
 
   const uint8_t* src = static_cast<const uint8_t*>(block);
-  long long stride = T;
-  if (layout != CORR_L_CIT) {
-    cudaError_t e = layout == CORR_L_TCI ? turn_launch(src, turned, T, 1, C * N, row_stride, s)
-                                         : turn_launch(src, turned, T, N, C, row_stride, s);
-    if (e != cudaSuccess) return CORR_ECUDA;
+  if (turn) {
+    if (turn_rows(src, turned, layout, bits, N, C, T, row_stride, s) != cudaSuccess) return CORR_ECUDA;
     src = turned;
-    stride = row_stride;
   }
   HerkArgs a{};
   a.in.x = src;
   a.in.acc = vis;
   a.tasks = tasks;
   a.status = d_status;
-  a.in.chan_stride = (long long)N * stride;
-  a.in.row_stride = stride;
+  a.in.chan_stride = (long long)R * row_stride;
+  a.in.row_stride = row_stride;
   a.in.n_inputs = N;
   a.in.n_chans = C;
   a.in.rows_per_chan = rpc;
   a.lo_is_real = (flags & CORR_F_LO_IS_REAL) ? 1 : 0;
   a.smem_bytes = smem;
   a.n_tasks = (int)n_tasks;
-  a.bits = 4;
+  a.bits = bits;
+  a.scratch = eight ? scr : nullptr;
+  a.scratch_ctas = eight ? n_sm : 0;
   CUtensorMap tmap;
-  const bool aligned = stride % 16 == 0 && reinterpret_cast<uintptr_t>(src) % 16 == 0;
-  const bool use_tma = aligned && make_herk_tmap(&tmap, src, false, 4, N, C, T, stride, rpc);
-  for (int t0 = 0; t0 < T; t0 += kMaxChunk4) {
+  const bool aligned = row_stride % 16 == 0 && reinterpret_cast<uintptr_t>(src) % 16 == 0;
+  const bool use_tma =
+      (tci || aligned) && make_herk_tmap(&tmap, src, tci, bits, R, C, T, row_stride, rpc);
+  if ((eight || tci) && !use_tma) return CORR_ECUDA;  // these read through TMA only
+  const int chunk = eight ? kMaxChunk8 : kMaxChunk4;
+  for (int t0 = 0; t0 < T; t0 += chunk) {
     a.in.t0 = t0;
-    a.in.tn = std::min(kMaxChunk4, T - t0);
+    a.in.tn = std::min(chunk, T - t0);
     a.in.accumulate = t0 > 0 ? 1 : 0;
     a.in.vec_ok = aligned ? 1 : 0;
-    if (herk4_launch(a, use_tma ? &tmap : nullptr, (int)n_tasks, s) != cudaSuccess)
+    if (herk4_launch(a, use_tma ? &tmap : nullptr, (int)n_tasks, s, tci) != cudaSuccess)
       return CORR_ECUDA;
   }
   if (status) {
@@ -214,4 +226,11 @@ extern "C" int corr_correlate_noalloc(const void* block, int n_inputs, int n_cha
     if (cudaGetLastError() != cudaSuccess) return CORR_ECUDA;
   }
   return CORR_OK;
+}
+
+extern "C" int corr_correlate_noalloc(const void* block, int n_inputs, int n_chans, int n_time,
+                                      int layout, unsigned flags, int64_t* vis, int* status,
+                                      void* stream) {
+  return corr_correlate_noalloc_bits(block, n_inputs, n_chans, n_time, 4, layout, flags, vis,
+                                     status, stream);
 }

@@ -83,6 +83,9 @@ EXPORTS += ["corr_dump_async", "corr_dump_wait", "corr_bind"]
 CORR_MAX_ASYNC_DUMPS = 4
 _lib.corr_correlate_noalloc.argtypes = [_P, _I, _I, _I, _I, _U, _P, _P, _P]
 _lib.corr_correlate_noalloc.restype = _I
+_lib.corr_correlate_noalloc_bits.argtypes = [_P, _I, _I, _I, _I, _I, _U, _P, _P, _P]
+_lib.corr_correlate_noalloc_bits.restype = _I
+EXPORTS.append("corr_correlate_noalloc_bits")
 CORR_NOALLOC_SCRATCH_BYTES = 16 << 20
 _lib.corr_get_stats.argtypes = [_P, ctypes.POINTER(CorrStats)]
 _lib.corr_push_many.argtypes = [_P, ctypes.POINTER(_P), _I, _SZ, _U64]
@@ -147,6 +150,15 @@ def corr_correlate_noalloc(block_ptr: int, n_inputs: int, n_chans: int, n_time: 
     return _lib.corr_correlate_noalloc(_P(block_ptr), n_inputs, n_chans, n_time, layout, flags,
                                        _P(vis_ptr), _P(status_ptr) if status_ptr else None,
                                        _P(stream) if stream else None)
+
+
+def corr_correlate_noalloc_bits(block_ptr: int, n_inputs: int, n_chans: int, n_time: int, bits: int,
+                                layout: int, flags: int, vis_ptr: int, status_ptr: int = 0,
+                                stream: int = 0) -> int:
+    """corr_correlate_noalloc for 4- or 8-bit samples."""
+    return _lib.corr_correlate_noalloc_bits(_P(block_ptr), n_inputs, n_chans, n_time, bits, layout,
+                                            flags, _P(vis_ptr), _P(status_ptr) if status_ptr else None,
+                                            _P(stream) if stream else None)
 
 
 def corr_set_timing(ctx, on: int) -> int:
