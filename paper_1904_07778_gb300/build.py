@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libxengine.so")
 SOURCES = ["xe_herk.cu", "xe_turn.cu", "xe_runtime.cu", "xe_noalloc.cu", "xe_batch.cu", "xe_service.cu",
-           "xe_fengine.cu", "xe_ingest.cu"]
+           "xe_fengine.cu", "xe_ingest.cu", "xe_crc.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -50,7 +50,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
     jobs = []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
-        o = os.path.join(OUT_DIR, src.replace(".cu", ".o"))
+        o = os.path.join(OUT_DIR, os.path.splitext(src)[0] + ".o")
         if force or _stale(o, [s] + headers):
             jobs.append([nvcc] + flags + ["-c", s, "-o", o])
 
@@ -63,7 +63,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         list(ex.map(run, jobs))
-    objs = [os.path.join(OUT_DIR, s.replace(".cu", ".o")) for s in SOURCES]
+    objs = [os.path.join(OUT_DIR, os.path.splitext(s)[0] + ".o") for s in SOURCES]
     if force or jobs or _stale(LIB, objs):
         tmp = LIB + ".tmp%d" % os.getpid()
         run([nvcc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs +

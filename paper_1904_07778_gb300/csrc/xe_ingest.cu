@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include "ingest.h"
+#include "xe_crc.h"
 #include "xe_internal.h"
 #include "xengine.h"
 
@@ -78,7 +79,10 @@ uint32_t x8n_mod(uint64_t n) {
 }
 
 uint32_t crc32(const uint8_t* p, size_t n) {
-  std::call_once(g_crc_once, crc_tables);
+  // on CPUs with CRC instructions (xe_crc.cpp) those advance the registers;
+  // the segments and their join are the same
+  static const bool hw = xe::crc32_hw_available();
+  if (!hw) std::call_once(g_crc_once, crc_tables);
   uint32_t c = 0xFFFFFFFFu;
   if (n >= 256) {
     const size_t L = (n / 4) & ~(size_t)7;  // bytes per segment, whole steps
@@ -91,17 +95,24 @@ uint32_t crc32(const uint8_t* p, size_t n) {
     }
     const uint8_t *p1 = p + L, *p2 = p1 + L, *p3 = p2 + L;
     uint32_t c1 = 0, c2 = 0, c3 = 0;
-    for (size_t k = 0; k < L; k += 8) {
-      c = crc_step8(c, p + k);
-      c1 = crc_step8(c1, p1 + k);
-      c2 = crc_step8(c2, p2 + k);
-      c3 = crc_step8(c3, p3 + k);
+    if (hw) {
+      uint32_t r[4] = {c, 0u, 0u, 0u};
+      xe::crc32_raw4_hw(p, L, r);
+      c = r[0], c1 = r[1], c2 = r[2], c3 = r[3];
+    } else {
+      for (size_t k = 0; k < L; k += 8) {
+        c = crc_step8(c, p + k);
+        c1 = crc_step8(c1, p1 + k);
+        c2 = crc_step8(c2, p2 + k);
+        c3 = crc_step8(c3, p3 + k);
+      }
     }
     const uint32_t X = cached_X;
     c = gf2_mulmod(gf2_mulmod(gf2_mulmod(c, X) ^ c1, X) ^ c2, X) ^ c3;
     p += 4 * L;
     n -= 4 * L;
   }
+  if (hw) return xe::crc32_raw_hw(c, p, n) ^ 0xFFFFFFFFu;
   for (; n >= 8; p += 8, n -= 8) c = crc_step8(c, p);
   for (; n; --n, ++p) c = (c >> 8) ^ g_crc[0][(c ^ *p) & 0xFFu];
   return c ^ 0xFFFFFFFFu;

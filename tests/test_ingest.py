@@ -85,6 +85,24 @@ def test_crc_random_lengths_and_offsets():
         assert pk_crc32(d) == zlib.crc32(d) & 0xFFFFFFFF, (off, n)
 
 
+@pytest.mark.gpu
+def test_crc_on_the_gpu_hosts_cpu():
+    """The CRC-32 on the host of a GPU machine, where the ARMv8 CRC
+    instructions replace the tables when the CPU has them: the lengths of
+    the two tests above, and every start address of a packet-sized message."""
+    import zlib
+    rng = np.random.default_rng(3)
+    for n in (0, 1, 7, 8, 9, 63, 255, 256, 257, 263, 264, 287, 288, 289, 1000, 4101, 8191,
+              8200, 8208, 65536 + 37, (1 << 20) + 3):
+        d = rng.integers(0, 256, n, dtype=np.uint8).tobytes()
+        assert pk_crc32(d) == zlib.crc32(d) & 0xFFFFFFFF, n
+    buf = rng.integers(0, 256, 40000, dtype=np.uint8).tobytes()
+    for off in range(16):
+        for n in (8204, 8208, 30000):
+            d = buf[off:off + n]
+            assert pk_crc32(d) == zlib.crc32(d) & 0xFFFFFFFF, (off, n)
+
+
 def test_clean_stream_round_trips():
     blocks = _blocks(4)
     with _ring() as ring:
